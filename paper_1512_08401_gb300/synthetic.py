@@ -1,0 +1,163 @@
+"""Seeded synthetic inputs: clean images, PSFs and blurred noisy observations.
+
+This module is the one place both the FP64 oracle tests and the CUDA path draw inputs
+from. It holds none of the deblurring method's arithmetic (no wavelet transform, no Theta,
+no solver). It simulates the acquisition model of Sec. 1.1, u0 = H u + b with
+b ~ N(0, sigma^2 I), using a numpy FFT circular convolution, which is data synthesis and is
+independent of both the oracle's direct convolution and the library's cuFFT path.
+
+Stand-ins for the paper's images (the book and confocal photographs of Sec. 5 and the
+phantom of Sec. 5.6 are not available): random axis-aligned rectangles with intensities
+U[0,1] painted over a linear gradient, on the torus.
+
+Generator recipe (seeded numpy PCG64):
+  1. background 0.25 + 0.5 ((i/n_rows) cos phi + (j/n_cols) sin phi)/sqrt(2), phi ~ U[0, 2pi)
+  2. R = min(256, 16 * max(1, n/128)) rectangles (n = min side); corner uniform integer,
+     sides uniform integers in [n/16, n/4], wrapped periodically, painted in order with an
+     intensity U[0,1] (replacing what was there)
+  3. blur with the periodic PSF (centre of the odd-sized array at the origin)
+  4. add N(0, noise^2) noise, no clipping
+PSFs:
+  * gaussian(sigma, k): exp(-(a^2+b^2)/(2 sigma^2)) on a k x k support, sum 1
+  * motion_line(length, angle): points t (cos a, sin a), t in [-(L-1)/2, (L-1)/2] in steps
+    of 1/8 px, bilinearly splatted into an L x L grid, sum 1
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+def rng_for(config_id: int, instance: int = 0) -> np.random.Generator:
+    """PCG64 seeded with 1000 * config_id + instance."""
+    return np.random.Generator(np.random.PCG64(1000 * config_id + instance))
+
+
+def gaussian_psf(sigma: float, k: int) -> np.ndarray:
+    if k % 2 == 0:
+        raise ValueError("PSF side must be odd")
+    c = k // 2
+    a = np.arange(-c, c + 1, dtype=np.float64)
+    h = np.exp(-(a[:, None] ** 2 + a[None, :] ** 2) / (2.0 * sigma * sigma))
+    return h / h.sum()
+
+
+def motion_line_psf(length: int, angle: float) -> np.ndarray:
+    """Straight motion blur of `length` px at `angle` (radians), bilinear splat."""
+    if length % 2 == 0:
+        raise ValueError("PSF side must be odd")
+    c = length // 2
+    h = np.zeros((length, length))
+    half = (length - 1) / 2.0
+    t = np.arange(-half, half + 1e-9, 1.0 / 8.0)
+    ys = c + t * np.sin(angle)
+    xs = c + t * np.cos(angle)
+    for y, x in zip(ys, xs):
+        y0, x0 = int(np.floor(y)), int(np.floor(x))
+        fy, fx = y - y0, x - x0
+        for dy, wy in ((0, 1 - fy), (1, fy)):
+            for dx, wx in ((0, 1 - fx), (1, fx)):
+                yy, xx = y0 + dy, x0 + dx
+                if 0 <= yy < length and 0 <= xx < length and wy * wx > 0:
+                    h[yy, xx] += wy * wx
+    return h / h.sum()
+
+
+def clean_image(n_rows: int, n_cols: int, rng: np.random.Generator) -> np.ndarray:
+    i = np.arange(n_rows, dtype=np.float64)[:, None] / n_rows
+    j = np.arange(n_cols, dtype=np.float64)[None, :] / n_cols
+    phi = rng.uniform(0.0, 2.0 * np.pi)
+    u = 0.25 + 0.5 * (i * np.cos(phi) + j * np.sin(phi)) / np.sqrt(2.0)
+    u = np.broadcast_to(u, (n_rows, n_cols)).copy()
+    n = min(n_rows, n_cols)
+    R = min(256, 16 * max(1, n // 128))
+    lo, hi = max(1, n // 16), max(1, n // 4)
+    for _ in range(R):
+        y0 = int(rng.integers(0, n_rows))
+        x0 = int(rng.integers(0, n_cols))
+        hh = int(rng.integers(lo, hi + 1))
+        ww = int(rng.integers(lo, hi + 1))
+        val = rng.uniform(0.0, 1.0)
+        rows = (y0 + np.arange(hh)) % n_rows
+        cols = (x0 + np.arange(ww)) % n_cols
+        u[np.ix_(rows, cols)] = val
+    return u
+
+
+def blur_fft(u: np.ndarray, psf: np.ndarray) -> np.ndarray:
+    """Circular convolution by FFT (data synthesis only)."""
+    n_rows, n_cols = u.shape
+    kh, kw = psf.shape
+    pad = np.zeros((n_rows, n_cols))
+    ch, cw = kh // 2, kw // 2
+    for a in range(kh):
+        for b in range(kw):
+            pad[(a - ch) % n_rows, (b - cw) % n_cols] += psf[a, b]
+    return np.real(np.fft.ifft2(np.fft.fft2(u) * np.fft.fft2(pad)))
+
+
+@dataclass
+class Problem:
+    u_clean: np.ndarray     # float64 (n_rows, n_cols)
+    u0: np.ndarray          # float64 observation
+    psf: np.ndarray         # float64 odd-sized PSF
+    lam: float
+    name: str
+
+
+def make_problem(n: int, psf: np.ndarray, lam: float, config_id: int, instance: int = 0,
+                 noise: float = 0.01, n_cols: int | None = None, name: str = "") -> Problem:
+    rng = rng_for(config_id, instance)
+    n_cols = n if n_cols is None else n_cols
+    u = clean_image(n, n_cols, rng)
+    u0 = blur_fft(u, psf) + noise * rng.standard_normal((n, n_cols))
+    return Problem(u, u0, psf, lam, name)
+
+
+# ---------------------------------------------------------------------------------------
+# The workloads
+# ---------------------------------------------------------------------------------------
+
+def small_problem() -> Problem:
+    """128 x 128, Gaussian sigma = 2 on 15 x 15, lambda = 1e-3 (db4, J = 4, K = 30 N)."""
+    return make_problem(128, gaussian_psf(2.0, 15), 1e-3, config_id=0, name="128^2 gaussian s2")
+
+
+def headline_problem(blur: str = "gaussian", instance: int = 0) -> Problem:
+    """1024 x 1024: Gaussian sigma = 3 on 31 x 31, or a 21 px motion line at a seeded angle
+    (db4, J = 5, lambda = 1e-3)."""
+    if blur == "gaussian":
+        psf = gaussian_psf(3.0, 31)
+    elif blur == "motion":
+        angle = rng_for(1, 100 + instance).uniform(0.0, np.pi)
+        psf = motion_line_psf(21, angle)
+    else:
+        raise ValueError(blur)
+    return make_problem(1024, psf, 1e-3, config_id=1, instance=instance, name=f"1024^2 {blur}")
+
+
+def large_problem() -> Problem:
+    """4096 x 4096, Gaussian sigma = 4 on 41 x 41 (db4, J = 6, K = 30 N)."""
+    return make_problem(4096, gaussian_psf(4.0, 41), 1e-3, config_id=2, name="4096^2 gaussian s4")
+
+
+def batch_mix(count: int = 256, seed_config: int = 3):
+    """Mixed batch: sizes from {256, 512, 1024}, Gaussian sigma ~ U[1,4] on a
+    (2 ceil(3 sigma)+1)^2 support or a motion line of length U{9..21} (odd) at a random
+    angle (probability 1/2 each), lambda log-uniform in [5e-4, 5e-3]."""
+    rng = rng_for(seed_config, 999)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([256, 512, 1024]))
+        if rng.uniform() < 0.5:
+            s = rng.uniform(1.0, 4.0)
+            psf = gaussian_psf(s, 2 * int(np.ceil(3 * s)) + 1)
+            kind = f"gauss{s:.2f}"
+        else:
+            L = int(rng.choice(np.arange(9, 22, 2)))
+            psf = motion_line_psf(L, rng.uniform(0.0, np.pi))
+            kind = f"motion{L}"
+        lam = float(np.exp(rng.uniform(np.log(5e-4), np.log(5e-3))))
+        out.append(make_problem(n, psf, lam, config_id=seed_config, instance=i, name=f"{n}^2 {kind}"))
+    return out
