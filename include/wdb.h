@@ -1,0 +1,211 @@
+/*
+ * wdb.h — C ABI of libwdb: wavelet-domain l1-l2 deblurring (Escande & Weiss, arXiv 1512.08401)
+ * on one NVIDIA GB300 (sm_103a).
+ *
+ * The library solves
+ *     min_x  E(x) = 1/2 || Theta_K x - x0 ||^2 + sum_i w_i |x_i|          (Eq. l1problemThetaApprox)
+ * with x0 = Psi* u0 the wavelet coefficients of the observed image u0 (Sec. 1.3),
+ * Theta_K the K-sparse approximation of Theta = Psi* H Psi (Eq. matrixH) of a periodic
+ * convolution H, built by Algorithm 2 and thresholded by Eq. cleverthreshold, and the solver
+ * is diagonally preconditioned FISTA (Algorithm 3, Sec. 4.2/4.3). The exact-operator
+ * path (Algorithm 1 with the gradient computed by FFTs and wavelet transforms, Sec. 5.2)
+ * runs on the same GPU for comparison.
+ *
+ * Conventions shared by every entry point
+ *   - Images are row-major float (FP32) arrays of n_rows x n_cols pixels; both sides must be
+ *     divisible by 2^levels. The domain is the torus (periodic boundaries, Sec. 2).
+ *   - Wavelet coefficient vectors hold N = n_rows * n_cols floats in subband-planar order:
+ *     the approximation A_J (n_rows/2^J x n_cols/2^J, row-major), then for s = J, J-1, ..., 1
+ *     the detail subbands with orientation (e_y, e_x) = (0,1), (1,0), (1,1), each
+ *     n_rows/2^s x n_cols/2^s row-major. Subband index 0 is A_J; 3J+1 subbands in all.
+ *   - wavelet names "db1" ... "db10": orthogonal Daubechies filters with p vanishing
+ *     moments (2p taps), minimum phase, periodic separable 2-D transform (Sec. 2).
+ *   - PSF: host FP64 array of kh x kw (odd sizes), row-major; element (kh/2, kw/2) is the
+ *     origin; (H u)[i,j] = sum_{a,b} psf[a+kh/2][b+kw/2] u[i-a][j-b] (indices mod n).
+ *   - Pointers named *_dev are device pointers owned by the caller; they must stay valid
+ *     until the stream has finished the call's work. Pointers named *_host are host memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *   - Every call returns a wdb_status. Nothing is thrown across the ABI and nothing aborts.
+ *     After an error, wdb_last_error() returns a one-line description (thread-local).
+ *     Asynchronous CUDA errors surface as WDB_ECUDA at the next synchronising call.
+ *   - A wdb_theta or wdb_fftop handle may be used by one stream at a time.
+ */
+#ifndef WDB_H
+#define WDB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    WDB_OK = 0,
+    WDB_EINVAL = 1,        /* invalid argument (sizes, names, NULL pointers, ranges) */
+    WDB_ENOMEM = 2,        /* device or host allocation failed */
+    WDB_ECUDA = 3,         /* a CUDA runtime / cuFFT call failed */
+    WDB_ENAN = 4,          /* a NaN or Inf appeared in the objective or the certificate */
+    WDB_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    WDB_EDIVERGED = 6,     /* the objective grew by more than 1e6 x its first value */
+    WDB_EUNSUPPORTED = 7,  /* valid but not supported (e.g. more than 64 subbands) */
+    WDB_EIO = 8            /* file could not be read or written, or has a bad format */
+} wdb_status;
+
+#define WDB_MAX_SUBBANDS 64
+#define WDB_PRECOND_NONE 0
+#define WDB_PRECOND_JACOBI 1   /* Eq. Jacobi_Precond: P = max(diag(Theta_K^T Theta_K), eps) */
+#define WDB_PRECOND_SPAI 2     /* Eq. SPAI_Precond:  P_ii = (M^2)_ii / M_ii, M = Theta_K^T Theta_K */
+#define WDB_RULE_WEIGHTED 0    /* Eq. cleverthreshold: score |2^{s_b} Theta[a,b]| */
+#define WDB_RULE_NAIVE 1       /* Eq. naivethresholding: score |Theta[a,b]| */
+
+typedef struct wdb_theta wdb_theta;   /* Theta_K and its preconditioners, library-owned */
+typedef struct wdb_fftop wdb_fftop;   /* exact operator H Psi for the FFT path, library-owned */
+
+/* Summary of a Theta_K handle. */
+typedef struct {
+    int n_rows, n_cols, levels, n_subbands;
+    int wavelet_taps;           /* 2p */
+    int rule;                   /* WDB_RULE_* used to select taps */
+    long long K_requested;      /* K passed to wdb_build_theta */
+    long long K_eff;            /* nonzero entries of Theta_K (<= K_requested) */
+    long long n_taps;           /* distinct kept taps (one per circulant diagonal) */
+    long long n_candidates;     /* distinct taps of the full Theta before thresholding */
+    double theta_max_abs;       /* max |tap| of the full Theta */
+    int phase_table_len;        /* 4^J: length of the per-phase-class preconditioner tables */
+    double build_ms;            /* wall time of wdb_build_theta (device work included) */
+} wdb_theta_info;
+
+/* Parameters of one solve. Zero-initialise and set what you need. */
+typedef struct {
+    double lambda;              /* w_i = lambda for every coefficient when w_subband == NULL */
+    const double* w_subband_host;  /* optional: n_subbands weights (Eq. def:G, w constant per subband) */
+    int max_iters;              /* iteration cap (>= 1) */
+    double tol;                 /* stop when gap/primal <= tol at a check; 0: run max_iters */
+    int precond;                /* WDB_PRECOND_* */
+    double jacobi_eps;          /* <= 0: 1e-6 * max_i M_ii */
+    int check_every;            /* gap check period m (<= 0: 10) */
+    const float* x_init_dev;    /* N floats or NULL (zero start) */
+    int no_graph;               /* 1: launch kernels one by one instead of CUDA graphs */
+} wdb_solve_params;
+
+typedef struct {
+    int iters;                  /* iterations run (the k of the returned x^(k)) */
+    double objective;           /* E(x) of the returned x, FP64 (Theta_K problem, or exact for the FFT path) */
+    double primal, gap, rel_gap;/* duality-gap certificate of y^(k) at the last check (NaN if none) */
+    long long support;          /* number of nonzero coefficients of x */
+    double tau, L_hat;          /* step and Lipschitz estimate used */
+    double solve_ms;            /* wall time of the call including the final synchronisation */
+    wdb_status status;
+} wdb_solve_result;
+
+/* ---- Theta_K construction (Algorithm 2 + Sec. 3.7), FP64 on the device ----
+ * For every subband b (3J+1 of them) the wavelet at position 0 is blurred with H and H^T
+ * (cuFFT, FP64) and analysed by one forward DWT (the column and row probes of Algorithm 2).
+ * Blocks whose output subband is finer than or as fine as the input take column taps, the
+ * others row taps (Thm 3). Whole taps are kept in the order of decreasing score |sigma_b v|
+ * (sigma_b = 2^{s_b} for WDB_RULE_WEIGHTED, 1 for WDB_RULE_NAIVE; ties by (a, b, oy, ox)
+ * ascending) while the entry count stays <= K; |v| <= 1e-14 max|v| is never kept.
+ * K >= N^2 keeps every tap. The diagonals of Theta_K^T Theta_K and of its square are
+ * computed per phase class for the preconditioners (Sec. 4.2, 4.3).
+ * Returns WDB_EINVAL for sizes not divisible by 2^levels, an even or larger-than-image
+ * PSF, K < 0, an unknown wavelet, or levels < 1. On success *out owns device memory
+ * until wdb_theta_free. The call synchronises `stream`. */
+wdb_status wdb_build_theta(const double* psf_host, int kh, int kw, int n_rows, int n_cols,
+                           const char* wavelet, int levels, long long K, int rule,
+                           void* stream, wdb_theta** out);
+
+/* Build a handle from an explicit tap list (host arrays of length n_taps). Tap t gives the
+ * value v[t] to the circulant diagonal (oy[t], ox[t]) of block (a[t], b[t]) in the
+ * convention of Algorithm 2: if level(a) <= level(b) the entry ((a,p),(b,q)) is v when
+ * p = (oy,ox) + 2^{level(b)-level(a)} q (mod the sides of a); otherwise when
+ * q = (oy,ox) + 2^{level(a)-level(b)} p (mod the sides of b). Used to load an operator
+ * built elsewhere (e.g. from a file). Duplicate taps are WDB_EINVAL. */
+wdb_status wdb_theta_from_taps(int n_rows, int n_cols, const char* wavelet, int levels,
+                               long long n_taps, const int* a_host, const int* b_host,
+                               const int* oy_host, const int* ox_host, const double* v_host,
+                               void* stream, wdb_theta** out);
+
+wdb_status wdb_theta_info_get(const wdb_theta* th, wdb_theta_info* info);
+
+/* Copy the kept taps to host arrays (capacity cap >= info.n_taps), sorted by (a, b, oy, ox). */
+wdb_status wdb_theta_export_taps(const wdb_theta* th, long long cap, int* a_host, int* b_host,
+                                 int* oy_host, int* ox_host, double* v_host);
+
+/* Preconditioner table and step for `precond` (computed on first use and cached):
+ * P_host receives 4^J FP64 values, one per phase class (subband b, qy mod R_b, qx mod R_b),
+ * R_b = 2^{J - level(b)}, subbands in planar order, phases row-major; tau and L_hat are the
+ * step 1/(1.01 L_hat) and the power-iteration estimate of lambda_max(P^-1/2 M P^-1/2)
+ * (Algorithm 3, step size). Md_host / M2d_host (optional, 4^J each) receive diag(M) and
+ * diag(M^2). Any output pointer may be NULL. Synchronises `stream`. */
+wdb_status wdb_theta_precond(wdb_theta* th, int precond, double jacobi_eps, void* stream,
+                             double* P_host, double* Md_host, double* M2d_host,
+                             double* tau_host, double* L_hat_host);
+
+/* Override the preconditioner table (4^J values, > 0) and step used for `precond`. */
+wdb_status wdb_theta_set_precond(wdb_theta* th, int precond, const double* P_host, double tau);
+
+/* Serialise / restore a handle (taps, layout, wavelet; preconditioners are recomputed). */
+wdb_status wdb_theta_save(const wdb_theta* th, const char* path);
+wdb_status wdb_theta_load(const char* path, void* stream, wdb_theta** out);
+void wdb_theta_free(wdb_theta* th);
+
+/* One operator application (Eq. gradientapprox pieces): out = Theta_K in (transpose = 0) or
+ * Theta_K^T in (transpose = 1); N floats each, device. */
+wdb_status wdb_theta_apply(const wdb_theta* th, const float* in_dev, float* out_dev,
+                           int transpose, void* stream);
+
+/* ---- Solvers ----
+ * wdb_solve: Algorithm 3 on Theta_K. x0 = Psi* u0 is computed on the device (FP32), then
+ * for k = 1, 2, ...: r = Theta_K y - x0 (kernel 1), g = Theta_K^T r fused with
+ * x = soft(y - tau g / P, tau w / P) and y = x + (k-1)/(k+2)(x - x_prev) (kernel 2).
+ * Iterates are FP32; the objective and duality-gap reductions are FP64 above the warp level.
+ * u_dev: N floats (image); x_dev: N floats (coefficients, output). Synchronises `stream`.
+ * result->status repeats the return value. */
+wdb_status wdb_solve(wdb_theta* th, const float* u_dev, float* x_dev,
+                     const wdb_solve_params* params, void* stream, wdb_solve_result* result);
+
+/* Same with the data already in the wavelet domain: x0_dev = Psi* u0 (N floats). */
+wdb_status wdb_solve_coeffs(wdb_theta* th, const float* x0_dev, float* x_dev,
+                            const wdb_solve_params* params, void* stream,
+                            wdb_solve_result* result);
+
+/* Objective E(x) = 1/2||Theta_K x - x0||^2 + sum w|x| in FP64 for device x, x0. */
+wdb_status wdb_theta_objective(const wdb_theta* th, const float* x_dev, const float* x0_dev,
+                               double lambda, const double* w_subband_host, void* stream,
+                               double* E_host);
+
+/* Exact operator A = H Psi for the FFT path (Algorithm 1 gradient, Sec. 5.2): cuFFT FP32
+ * R2C/C2R for the solve, FP64 for the preconditioner diagonals (constant per subband, the
+ * full Theta having full translation symmetry) and the power iteration. */
+wdb_status wdb_fftop_create(const double* psf_host, int kh, int kw, int n_rows, int n_cols,
+                            const char* wavelet, int levels, void* stream, wdb_fftop** out);
+void wdb_fftop_free(wdb_fftop* op);
+wdb_status wdb_fftop_precond(wdb_fftop* op, int precond, double jacobi_eps, void* stream,
+                             double* P_host /* 3J+1 */, double* tau_host, double* L_hat_host);
+wdb_status wdb_fftop_set_precond(wdb_fftop* op, int precond, const double* P_host, double tau);
+
+/* FISTA with the exact gradient: per iteration IDWT(y), R2C, r^ = h^ z^ - u0^ with
+ * Parseval reductions, g^ = conj(h^) r^, C2R, DWT, then the same fused step as wdb_solve.
+ * result->objective is the exact objective 1/2||H Psi x - u0||^2 + sum w|x|. */
+wdb_status wdb_solve_fft(wdb_fftop* op, const float* u_dev, float* x_dev,
+                         const wdb_solve_params* params, void* stream, wdb_solve_result* result);
+
+/* ---- Wavelet transforms (Sec. 2), FP32, device ---- */
+wdb_status wdb_dwt(const float* img_dev, float* coef_dev, int n_rows, int n_cols,
+                   const char* wavelet, int levels, void* stream);
+wdb_status wdb_idwt(const float* coef_dev, float* img_dev, int n_rows, int n_cols,
+                    const char* wavelet, int levels, void* stream);
+
+/* Filter taps of a wavelet (host): h (low-pass) and g (high-pass) of length 2p. */
+wdb_status wdb_wavelet_filters(const char* wavelet, int cap, double* h_host, double* g_host,
+                               int* taps);
+
+/* ---- Diagnostics ---- */
+const char* wdb_status_str(wdb_status s);
+const char* wdb_last_error(void);
+/* Number of kernels this library launched (or placed in graphs that were launched) since
+ * load or the last reset; counts graph replays node by node. */
+long long wdb_kernel_launches(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WDB_H */

@@ -1,0 +1,91 @@
+// Device helpers shared by the kernels of libwdb: compensated FP32 accumulation, the
+// deterministic grid-wide FP64 reduction, and subband / phase-class lookups.
+#pragma once
+#include "wdb_internal.h"
+
+namespace wdb {
+
+// Neumaier compensated summation step in FP32.
+__device__ __forceinline__ void neu_add(float& s, float& c, float v) {
+    float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+}
+
+// Reduce NV doubles over the grid. Returns true in every thread of the last CTA to finish,
+// with `tot` holding the grid totals there. Bit i of maxmask selects max instead of sum
+// (values must be >= 0 for max).
+template <int NV>
+__device__ bool grid_reduce(double (&v)[NV], unsigned maxmask, double* part, unsigned int* counter,
+                            double (&tot)[NV]) {
+    __shared__ double s_w[32][NV];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        for (int off = 16; off > 0; off >>= 1) {
+            double o = __shfl_down_sync(0xffffffffu, v[i], off);
+            v[i] = ((maxmask >> i) & 1) ? fmax(v[i], o) : v[i] + o;
+        }
+        if (lane == 0) s_w[warp][i] = v[i];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double x = lane < nw ? s_w[lane][i] : 0.0;
+            for (int off = 16; off > 0; off >>= 1) {
+                double o = __shfl_down_sync(0xffffffffu, x, off);
+                x = ((maxmask >> i) & 1) ? fmax(x, o) : x + o;
+            }
+            if (lane == 0) part[(size_t)blockIdx.x * NV + i] = x;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            double x = __ldcg(part + (size_t)b * NV + i);
+            acc[i] = ((maxmask >> i) & 1) ? fmax(acc[i], x) : acc[i] + x;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        for (int off = 16; off > 0; off >>= 1) {
+            double o = __shfl_down_sync(0xffffffffu, acc[i], off);
+            acc[i] = ((maxmask >> i) & 1) ? fmax(acc[i], o) : acc[i] + o;
+        }
+        if (lane == 0) s_w[warp][i] = acc[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        double x = 0.0;
+        for (int w = 0; w < nw; ++w) x = ((maxmask >> i) & 1) ? fmax(x, s_w[w][i]) : x + s_w[w][i];
+        tot[i] = x;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+__device__ __forceinline__ int find_subband(const int* __restrict__ vb_start, int S, int vb) {
+    int o = 0;
+    while (o + 1 < S && vb >= __ldg(vb_start + o + 1)) ++o;
+    return o;
+}
+
+__device__ __forceinline__ int phase_class(const SubbandDev& so, int py, int px) {
+    const int m = (1 << so.lgR) - 1;
+    return so.tab_off + ((py & m) << so.lgR) + (px & m);
+}
+
+}  // namespace wdb

@@ -1,0 +1,663 @@
+// Construction of Theta_K (Algorithm 2 + Sec. 3.7) and of the preconditioner diagonals
+// (Sec. 4.2, 4.3), FP64 on the device.
+//
+//  1. probes: for every subband b, psi_b = IDWT(e_{b,0}); H psi_b and H^T psi_b by cuFFT
+//     (D2Z, multiply by h^ or conj(h^), Z2D); one forward DWT each (Algorithm 2).
+//  2. candidates: block (a, b) takes column taps col[b] restricted to subband a when
+//     level(a) <= level(b), otherwise row taps row[a] restricted to subband b (Thm 3).
+//  3. selection: keys (score desc, candidate index asc) with score |sigma_b v|; a weighted
+//     radix select over the 128-bit composite key (8-bit digits, histogram weights =
+//     multiplicities) finds the first tap whose entries would exceed K; everything before
+//     it in key order is kept. Numerical zeros (|v| <= 1e-14 max|v|) never enter.
+//  4. packing (host): kept taps -> gather stencils of Theta_K and Theta_K^T.
+//  5. diag(M), diag(M^2), M = Theta_K^T Theta_K, per phase class by comb probes: impulses of
+//     one phase class spaced further apart than the reach of M^2, one Theta_K and one
+//     Theta_K^T application, norms divided by the number of impulses.
+//  6. step: power iteration for lambda_max(P^-1/2 M P^-1/2) from a splitmix64 start vector.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <tuple>
+
+#include "device_util.cuh"
+#include "fftops.cuh"
+#include "stencil.cuh"
+#include "theta_impl.h"
+
+namespace wdb {
+
+namespace {
+
+struct CandPair {
+    const double* src;     // tap array (rows x cols, row-major) inside a probe vector
+    int rows, cols;
+    long long base;        // global candidate index of element 0
+    unsigned long long mult;
+    double sigma;
+};
+
+struct SelState {
+    unsigned long long vmax_bits;
+    unsigned long long K;
+    unsigned long long before;     // weight of keys strictly below the current prefix range
+    unsigned long long prefix_hi, prefix_lo;
+    unsigned long long count;
+    int keep_all;
+    int pad;
+    unsigned long long hist[256];
+};
+
+__device__ __forceinline__ bool cand_key(const CandPair& P, int e, double thr, unsigned long long& hi,
+                                         unsigned long long& lo, double& v) {
+    v = P.src[e];
+    const double av = fabs(v);
+    if (!(av > thr)) return false;
+    const double score = av * P.sigma;
+    hi = ~(unsigned long long)__double_as_longlong(score);
+    lo = (unsigned long long)(P.base + e);
+    return true;
+}
+
+__global__ void vmax_kernel(const CandPair* __restrict__ pairs, SelState* sel) {
+    const CandPair P = pairs[blockIdx.y];
+    const int n = P.rows * P.cols;
+    double m = 0.0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) m = fmax(m, fabs(P.src[e]));
+    for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&sel->vmax_bits, (unsigned long long)__double_as_longlong(m));
+}
+
+// One digit pass of the weighted radix select. Passes 0..7 take 8-bit digits of the score
+// part (high to low), passes 8.. digits of the index part (ibits bits, a multiple of 8).
+__global__ void sel_hist_kernel(const CandPair* __restrict__ pairs, SelState* sel, int pass, int ibits) {
+    __shared__ unsigned long long h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0ull;
+    __syncthreads();
+    const bool skip = sel->keep_all != 0;
+    const CandPair P = pairs[blockIdx.y];
+    const int n = P.rows * P.cols;
+    const double thr = 1e-14 * __longlong_as_double((long long)sel->vmax_bits);
+    const unsigned long long phi = sel->prefix_hi, plo = sel->prefix_lo;
+    if (!skip) {
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+            unsigned long long hi, lo;
+            double v;
+            if (!cand_key(P, e, thr, hi, lo, v)) continue;
+            int d;
+            if (pass < 8) {
+                if (pass > 0 && (hi >> (64 - 8 * pass)) != phi) continue;
+                d = (int)((hi >> (56 - 8 * pass)) & 255ull);
+            } else {
+                const int q = pass - 8;
+                if (hi != phi) continue;
+                if (q > 0 && (lo >> (ibits - 8 * q)) != plo) continue;
+                d = (int)((lo >> (ibits - 8 - 8 * q)) & 255ull);
+            }
+            atomicAdd(&h[d], P.mult);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&sel->hist[i], h[i]);
+}
+
+__global__ void sel_scan_kernel(SelState* sel, int pass) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (!sel->keep_all) {
+        unsigned long long excl = 0;
+        int dsel = -1;
+        for (int d = 0; d < 256; ++d) {
+            const unsigned long long hd = sel->hist[d];
+            if (sel->before + excl + hd > sel->K) {
+                dsel = d;
+                break;
+            }
+            excl += hd;
+        }
+        if (dsel < 0) {
+            sel->keep_all = 1;
+        } else {
+            sel->before += excl;
+            if (pass < 8) sel->prefix_hi = (sel->prefix_hi << 8) | (unsigned long long)dsel;
+            else sel->prefix_lo = (sel->prefix_lo << 8) | (unsigned long long)dsel;
+        }
+    }
+    for (int d = 0; d < 256; ++d) sel->hist[d] = 0ull;
+}
+
+__device__ __forceinline__ bool kept(const SelState& s, unsigned long long hi, unsigned long long lo) {
+    return s.keep_all || hi < s.prefix_hi || (hi == s.prefix_hi && lo < s.prefix_lo);
+}
+
+__global__ void sel_emit_kernel(const CandPair* __restrict__ pairs, SelState* sel, int* out_pair, int* out_e,
+                                double* out_v, unsigned long long cap) {
+    const CandPair P = pairs[blockIdx.y];
+    const int n = P.rows * P.cols;
+    const SelState s = *sel;
+    const double thr = 1e-14 * __longlong_as_double((long long)s.vmax_bits);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        unsigned long long hi, lo;
+        double v;
+        if (!cand_key(P, e, thr, hi, lo, v) || !kept(s, hi, lo)) continue;
+        const unsigned long long slot = atomicAdd(&sel->count, 1ull);
+        if (out_pair && slot < cap) {
+            out_pair[slot] = blockIdx.y;
+            out_e[slot] = e;
+            out_v[slot] = v;
+        }
+    }
+}
+
+__global__ void set_value_kernel(double* p, long long idx, double v) { p[idx] = v; }
+
+// comb of impulses of one phase class (value v) in subband sb
+template <typename T>
+__global__ void comb_kernel(T* __restrict__ vec, long long off, int cols, int phy, int phx, int step, int ty, int tx,
+                            T v) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ty * tx) return;
+    int ky = t / tx, kx = t - ky * tx;
+    vec[off + (size_t)(phy + ky * step) * cols + (phx + kx * step)] = v;
+}
+
+int wrap_signed(int v, int n) {
+    int m = ((v % n) + n) % n;
+    return (m >= n - n / 2) ? m - n : m;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Handle helpers
+// ---------------------------------------------------------------------------------------
+template <typename T>
+wdb_status th_alloc(wdb_theta* th, T** p, size_t n) {
+    void* q = nullptr;
+    WDB_CK(cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T)));
+    th->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return WDB_OK;
+}
+template wdb_status th_alloc<float>(wdb_theta*, float**, size_t);
+template wdb_status th_alloc<double>(wdb_theta*, double**, size_t);
+template wdb_status th_alloc<int>(wdb_theta*, int**, size_t);
+
+template <typename T>
+static wdb_status upload(wdb_theta* th, const std::vector<T>& h, T** d, cudaStream_t st) {
+    WDB_TRY(th_alloc(th, reinterpret_cast<T**>(d), h.size()));
+    if (!h.empty()) WDB_CK(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return WDB_OK;
+}
+
+StencilArgs stencil_args(const wdb_theta* th, bool adj) {
+    StencilArgs A;
+    A.op = adj ? th->adj : th->fwd;
+    A.sb = th->d_sb;
+    A.vb_start = th->d_vb_start;
+    A.S = th->lay.S;
+    A.nvb = th->sched.nvb;
+    return A;
+}
+
+RedTarget th_red(const wdb_theta* th, double* out) { return RedTarget{th->d_counter, th->d_red_part, out}; }
+
+// ---------------------------------------------------------------------------------------
+// Packing kept taps into gather stencils
+// ---------------------------------------------------------------------------------------
+struct PEntry {
+    int out, in, up, lg, phase, dy, dx;
+    double v;
+    bool operator<(const PEntry& o) const {
+        return std::tie(out, in, up, lg, phase, dy, dx) < std::tie(o.out, o.in, o.up, o.lg, o.phase, o.dy, o.dx);
+    }
+};
+
+static void pack_op(const Layout& L, std::vector<PEntry>& E, OpHost& op) {
+    std::sort(E.begin(), E.end());
+    op.pair_start.assign(L.S + 1, 0);
+    op.pairs.clear();
+    op.phase_idx.clear();
+    op.tap_off.clear();
+    op.tap_v.clear();
+    op.tap_v64.clear();
+    size_t i = 0;
+    for (int o = 0; o < L.S; ++o) {
+        op.pair_start[o] = (int)op.pairs.size();
+        while (i < E.size() && E[i].out == o) {
+            const int in = E[i].in, up = E[i].up, lg = E[i].lg;
+            size_t j = i;
+            while (j < E.size() && E[j].out == o && E[j].in == in) ++j;
+            PairDesc d;
+            d.in_sb = in;
+            d.meta = (up << 8) | lg;
+            if (!up) {
+                d.a = (int)op.tap_off.size();
+                for (size_t t = i; t < j; ++t) {
+                    op.tap_off.push_back((E[t].dy << 16) | (E[t].dx & 0xffff));
+                    op.tap_v.push_back((float)E[t].v);
+                    op.tap_v64.push_back(E[t].v);
+                }
+                d.b = (int)op.tap_off.size();
+            } else {
+                const int nph = 1 << (2 * lg);
+                d.a = (int)op.phase_idx.size();
+                d.b = d.a + nph;
+                size_t t = i;
+                for (int ph = 0; ph < nph; ++ph) {
+                    op.phase_idx.push_back((int)op.tap_off.size());
+                    while (t < j && E[t].phase == ph) {
+                        op.tap_off.push_back((E[t].dy << 16) | (E[t].dx & 0xffff));
+                        op.tap_v.push_back((float)E[t].v);
+                        op.tap_v64.push_back(E[t].v);
+                        ++t;
+                    }
+                }
+                op.phase_idx.push_back((int)op.tap_off.size());
+            }
+            op.pairs.push_back(d);
+            i = j;
+        }
+    }
+    op.pair_start[L.S] = (int)op.pairs.size();
+}
+
+static void build_ops(wdb_theta* th) {
+    const Layout& L = th->lay;
+    std::vector<PEntry> F, A;
+    F.reserve(th->taps.size());
+    A.reserve(th->taps.size());
+    for (const Tap& t : th->taps) {
+        const SubbandDev &sa = L.sb[t.a], &sb = L.sb[t.b];
+        if (sa.level <= sb.level) {  // column form: tap array in subband a
+            const int lg = sb.level - sa.level;
+            if (lg == 0) {
+                F.push_back({t.a, t.b, 0, 0, 0, wrap_signed(-t.oy, sb.rows), wrap_signed(-t.ox, sb.cols), t.v});
+            } else {
+                const int m = (1 << lg) - 1;
+                const int ph = ((t.oy & m) << lg) | (t.ox & m);
+                F.push_back({t.a, t.b, 1, lg, ph, wrap_signed(-(t.oy >> lg), sb.rows), wrap_signed(-(t.ox >> lg), sb.cols),
+                             t.v});
+            }
+            A.push_back({t.b, t.a, 0, lg, 0, wrap_signed(t.oy, sa.rows), wrap_signed(t.ox, sa.cols), t.v});
+        } else {  // row form: tap array in subband b
+            const int lg = sa.level - sb.level;
+            F.push_back({t.a, t.b, 0, lg, 0, wrap_signed(t.oy, sb.rows), wrap_signed(t.ox, sb.cols), t.v});
+            const int m = (1 << lg) - 1;
+            const int ph = ((t.oy & m) << lg) | (t.ox & m);
+            A.push_back({t.b, t.a, 1, lg, ph, wrap_signed(-(t.oy >> lg), sa.rows), wrap_signed(-(t.ox >> lg), sa.cols),
+                         t.v});
+        }
+    }
+    pack_op(L, F, th->fwd_h);
+    pack_op(L, A, th->adj_h);
+}
+
+static wdb_status upload_op(wdb_theta* th, const OpHost& h, OpDev& d, cudaStream_t st) {
+    WDB_TRY(upload(th, h.pair_start, const_cast<int**>(&d.pair_start), st));
+    WDB_TRY(upload(th, h.pairs, const_cast<PairDesc**>(&d.pairs), st));
+    WDB_TRY(upload(th, h.phase_idx, const_cast<int**>(&d.phase_idx), st));
+    WDB_TRY(upload(th, h.tap_off, const_cast<int**>(&d.tap_off), st));
+    WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&d.tap_v), st));
+    WDB_TRY(upload(th, h.tap_v64, const_cast<double**>(&d.tap_v64), st));
+    d.n_pairs = (int)h.pairs.size();
+    d.n_taps = (int)h.tap_off.size();
+    d.n_phase = (int)h.phase_idx.size();
+    return WDB_OK;
+}
+
+// max image-space distance between the two coefficients of a kept entry (pixels)
+static long long tap_reach(const wdb_theta* th) {
+    const Layout& L = th->lay;
+    long long D = 0;
+    for (const Tap& t : th->taps) {
+        const SubbandDev &sa = L.sb[t.a], &sb = L.sb[t.b];
+        const SubbandDev& arr = (sa.level <= sb.level) ? sa : sb;
+        long long dy = std::llabs((long long)wrap_signed(t.oy, arr.rows)) << arr.level;
+        long long dx = std::llabs((long long)wrap_signed(t.ox, arr.cols)) << arr.level;
+        D = std::max(D, std::max(dy, dx));
+    }
+    return D;
+}
+
+bool setup_fp64(const wdb_theta* th) { return th->lay.N <= (1LL << 21); }
+
+// diag(M), diag(M^2) per phase class by comb probes
+template <typename T>
+static wdb_status diag_tables(wdb_theta* th, cudaStream_t st) {
+    const Layout& L = th->lay;
+    const long long N = L.N;
+    T *v = nullptr, *u = nullptr, *w = nullptr;
+    WDB_CK(cudaMalloc(&v, sizeof(T) * N));
+    WDB_CK(cudaMalloc(&u, sizeof(T) * N));
+    WDB_CK(cudaMalloc(&w, sizeof(T) * N));
+    double* d_out = nullptr;
+    WDB_CK(cudaMalloc(&d_out, sizeof(double) * 2 * L.tab_len));
+    WDB_CK(cudaMemsetAsync(v, 0, sizeof(T) * N, st));
+    const long long D = tap_reach(th);
+    const long long P2 = 1LL << L.J;
+    const long long Timg = P2 * ((4 * D + 1 + P2 - 1) / P2);
+    const int ty = (int)std::max<long long>(1, L.n_rows / Timg), tx = (int)std::max<long long>(1, L.n_cols / Timg);
+    StencilArgs F = stencil_args(th, false), A = stencil_args(th, true);
+    wdb_status s = WDB_OK;
+    for (int b = 0; b < L.S && s == WDB_OK; ++b) {
+        const SubbandDev& sb = L.sb[b];
+        const int R = 1 << sb.lgR;
+        const int step = (int)(Timg >> sb.level);
+        for (int py = 0; py < R && s == WDB_OK; ++py)
+            for (int px = 0; px < R && s == WDB_OK; ++px) {
+                const int cls = sb.tab_off + py * R + px;
+                comb_kernel<T><<<(ty * tx + 255) / 256, 256, 0, st>>>(v, sb.off, sb.cols, py, px, step, ty, tx, (T)1);
+                count_launch();
+                RedTarget r1 = th_red(th, d_out + 2 * cls), r2 = th_red(th, d_out + 2 * cls + 1);
+                s = launch_apply<T>(F, th->grid, v, u, nullptr, &r1, st);
+                if (s == WDB_OK) s = launch_apply<T>(A, th->grid, u, w, nullptr, &r2, st);
+                comb_kernel<T><<<(ty * tx + 255) / 256, 256, 0, st>>>(v, sb.off, sb.cols, py, px, step, ty, tx, (T)0);
+                count_launch();
+            }
+    }
+    std::vector<double> out(2 * L.tab_len);
+    if (s == WDB_OK) {
+        cudaError_t e = cudaMemcpyAsync(out.data(), d_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = cuda_error(e, "diag tables", __FILE__, __LINE__);
+    }
+    cudaFree(v);
+    cudaFree(u);
+    cudaFree(w);
+    cudaFree(d_out);
+    if (s != WDB_OK) return s;
+    const double teeth = (double)ty * tx;
+    th->Md.resize(L.tab_len);
+    th->M2d.resize(L.tab_len);
+    for (int c = 0; c < L.tab_len; ++c) {
+        th->Md[c] = out[2 * c] / teeth;
+        th->M2d[c] = out[2 * c + 1] / teeth;
+    }
+    th->diag_valid = true;
+    return WDB_OK;
+}
+
+// Upload taps, build stencils, schedule, workspace for reductions, diag tables.
+wdb_status theta_finalize(wdb_theta* th, cudaStream_t st) {
+    const Layout& L = th->lay;
+    th->K_eff = 0;
+    for (const Tap& t : th->taps) {
+        const SubbandDev &sa = L.sb[t.a], &sb = L.sb[t.b];
+        th->K_eff += std::min((long long)sa.rows * sa.cols, (long long)sb.rows * sb.cols);
+    }
+    build_ops(th);
+    WDB_TRY(upload_op(th, th->fwd_h, th->fwd, st));
+    WDB_TRY(upload_op(th, th->adj_h, th->adj, st));
+    std::vector<SubbandDev> sbv(L.sb, L.sb + L.S);
+    WDB_TRY(upload(th, sbv, &th->d_sb, st));
+    th->sched = make_schedule(L);
+    WDB_TRY(upload(th, th->sched.vb_start, &th->d_vb_start, st));
+    th->grid = std::max(1, std::min(th->sched.nvb, stencil_grid_limit()));
+    WDB_TRY(th_alloc(th, &th->d_red_part, (size_t)th->grid * 4));
+    unsigned int* cnt = nullptr;
+    WDB_CK(cudaMalloc(&cnt, sizeof(unsigned int) * 4));
+    th->allocs.push_back(cnt);
+    WDB_CK(cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * 4, st));
+    th->d_counter = cnt;
+    if (setup_fp64(th)) WDB_TRY(diag_tables<double>(th, st));
+    else WDB_TRY(diag_tables<float>(th, st));
+    return WDB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Algorithm 2 + Sec. 3.7 on the device
+// ---------------------------------------------------------------------------------------
+wdb_status theta_build_device(wdb_theta* th, const double* psf_host, int kh, int kw, long long K, int rule,
+                              cudaStream_t st) {
+    const Layout& L = th->lay;
+    const long long N = L.N;
+    const int R = L.n_rows, C = L.n_cols, C2 = C / 2 + 1;
+    const long long NC = (long long)R * C2;
+    // device scratch
+    double *psf = nullptr, *img = nullptr, *coef = nullptr, *scr = nullptr, *probes = nullptr;
+    cufftDoubleComplex *hhat = nullptr, *spec = nullptr, *prod = nullptr;
+    std::vector<void*> tmp;
+    auto dmalloc = [&](void** p, size_t bytes) -> wdb_status {
+        WDB_CK(cudaMalloc(p, std::max<size_t>(bytes, 1)));
+        tmp.push_back(*p);
+        return WDB_OK;
+    };
+    auto cleanup = [&]() {
+        for (void* p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    cufftHandle pf = 0, pi = 0;
+    bool have_pf = false, have_pi = false;
+    wdb_status s = WDB_OK;
+    do {
+        if ((s = dmalloc((void**)&psf, sizeof(double) * kh * kw))) break;
+        if ((s = dmalloc((void**)&img, sizeof(double) * N))) break;
+        if ((s = dmalloc((void**)&coef, sizeof(double) * N))) break;
+        if ((s = dmalloc((void**)&scr, sizeof(double) * (N / 2 + 1)))) break;
+        if ((s = dmalloc((void**)&probes, sizeof(double) * N * 2 * L.S))) break;
+        if ((s = dmalloc((void**)&hhat, sizeof(cufftDoubleComplex) * NC))) break;
+        if ((s = dmalloc((void**)&spec, sizeof(cufftDoubleComplex) * NC))) break;
+        if ((s = dmalloc((void**)&prod, sizeof(cufftDoubleComplex) * NC))) break;
+        cufftResult fr = cufftPlan2d(&pf, R, C, CUFFT_D2Z);
+        if (fr != CUFFT_SUCCESS) { s = cufft_error(fr, "cufftPlan2d D2Z", __FILE__, __LINE__); break; }
+        have_pf = true;
+        fr = cufftPlan2d(&pi, R, C, CUFFT_Z2D);
+        if (fr != CUFFT_SUCCESS) { s = cufft_error(fr, "cufftPlan2d Z2D", __FILE__, __LINE__); break; }
+        have_pi = true;
+        cufftSetStream(pf, st);
+        cufftSetStream(pi, st);
+        cudaError_t ce = cudaMemcpyAsync(psf, psf_host, sizeof(double) * kh * kw, cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) { s = cuda_error(ce, "copy psf", __FILE__, __LINE__); break; }
+        if ((s = launch_pad_psf(psf, kh, kw, img, R, C, st))) break;
+        fr = cufftExecD2Z(pf, img, hhat);
+        if (fr != CUFFT_SUCCESS) { s = cufft_error(fr, "D2Z psf", __FILE__, __LINE__); break; }
+        // probes (Algorithm 2)
+        for (int b = 0; b < L.S && s == WDB_OK; ++b) {
+            cudaMemsetAsync(coef, 0, sizeof(double) * N, st);
+            set_value_kernel<<<1, 1, 0, st>>>(coef, L.sb[b].off, 1.0);
+            count_launch();
+            if ((s = idwt2<double>(coef, img, L, th->filt, scr, st))) break;
+            fr = cufftExecD2Z(pf, img, spec);
+            if (fr != CUFFT_SUCCESS) { s = cufft_error(fr, "D2Z probe", __FILE__, __LINE__); break; }
+            for (int which = 0; which < 2 && s == WDB_OK; ++which) {   // 0: H (column), 1: H^T (row)
+                if ((s = launch_cmul64(spec, hhat, prod, NC, which, 1.0 / (double)N, st))) break;
+                fr = cufftExecZ2D(pi, prod, img);
+                if (fr != CUFFT_SUCCESS) { s = cufft_error(fr, "Z2D probe", __FILE__, __LINE__); break; }
+                double* dst = probes + (size_t)(which * L.S + b) * N;
+                s = dwt2<double>(img, dst, L, th->filt, scr, st);
+            }
+        }
+        if (s) break;
+        // candidate pairs
+        std::vector<CandPair> cp(L.S * L.S);
+        long long base = 0;
+        int maxn = 1;
+        for (int a = 0; a < L.S; ++a)
+            for (int b = 0; b < L.S; ++b) {
+                const SubbandDev &sa = L.sb[a], &sb = L.sb[b];
+                CandPair& c = cp[a * L.S + b];
+                if (sa.level <= sb.level) {
+                    c.src = probes + (size_t)b * N + sa.off;
+                    c.rows = sa.rows;
+                    c.cols = sa.cols;
+                    c.mult = (unsigned long long)sb.rows * sb.cols;
+                } else {
+                    c.src = probes + (size_t)(L.S + a) * N + sb.off;
+                    c.rows = sb.rows;
+                    c.cols = sb.cols;
+                    c.mult = (unsigned long long)sa.rows * sa.cols;
+                }
+                c.sigma = (rule == WDB_RULE_NAIVE) ? 1.0 : std::ldexp(1.0, sb.level);
+                c.base = base;
+                base += (long long)c.rows * c.cols;
+                maxn = std::max(maxn, c.rows * c.cols);
+            }
+        th->n_candidates = base;
+        int ibits = 8;
+        while (ibits < 64 && (base >> ibits) != 0) ibits += 8;
+        CandPair* d_cp = nullptr;
+        SelState* d_sel = nullptr;
+        if ((s = dmalloc((void**)&d_cp, sizeof(CandPair) * cp.size()))) break;
+        if ((s = dmalloc((void**)&d_sel, sizeof(SelState)))) break;
+        SelState h0;
+        std::memset(&h0, 0, sizeof h0);
+        h0.K = (unsigned long long)std::max<long long>(K, 0);
+        cudaMemcpyAsync(d_cp, cp.data(), sizeof(CandPair) * cp.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_sel, &h0, sizeof h0, cudaMemcpyHostToDevice, st);
+        dim3 g((unsigned)std::min(64, (maxn + 255) / 256), (unsigned)cp.size());
+        vmax_kernel<<<g, 256, 0, st>>>(d_cp, d_sel);
+        count_launch();
+        const int passes = 8 + ibits / 8;
+        for (int p = 0; p < passes; ++p) {
+            sel_hist_kernel<<<g, 256, 0, st>>>(d_cp, d_sel, p, ibits);
+            sel_scan_kernel<<<1, 32, 0, st>>>(d_sel, p);
+            count_launch(2);
+        }
+        sel_emit_kernel<<<g, 256, 0, st>>>(d_cp, d_sel, nullptr, nullptr, nullptr, 0);
+        count_launch();
+        SelState hs;
+        ce = cudaMemcpyAsync(&hs, d_sel, sizeof hs, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce == cudaSuccess) ce = cudaGetLastError();
+        if (ce != cudaSuccess) { s = cuda_error(ce, "tap selection", __FILE__, __LINE__); break; }
+        std::memcpy(&th->theta_max_abs, &hs.vmax_bits, sizeof(double));
+        const unsigned long long nk = hs.count;
+        int *d_pair = nullptr, *d_e = nullptr;
+        double* d_v = nullptr;
+        if ((s = dmalloc((void**)&d_pair, sizeof(int) * nk))) break;
+        if ((s = dmalloc((void**)&d_e, sizeof(int) * nk))) break;
+        if ((s = dmalloc((void**)&d_v, sizeof(double) * nk))) break;
+        cudaMemsetAsync(&d_sel->count, 0, sizeof(unsigned long long), st);
+        sel_emit_kernel<<<g, 256, 0, st>>>(d_cp, d_sel, d_pair, d_e, d_v, nk);
+        count_launch();
+        std::vector<int> hp(nk), he(nk);
+        std::vector<double> hv(nk);
+        if (nk) {
+            cudaMemcpyAsync(hp.data(), d_pair, sizeof(int) * nk, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(he.data(), d_e, sizeof(int) * nk, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(hv.data(), d_v, sizeof(double) * nk, cudaMemcpyDeviceToHost, st);
+        }
+        ce = cudaStreamSynchronize(st);
+        if (ce == cudaSuccess) ce = cudaGetLastError();
+        if (ce != cudaSuccess) { s = cuda_error(ce, "tap emit", __FILE__, __LINE__); break; }
+        std::vector<size_t> ord(nk);
+        for (size_t i = 0; i < nk; ++i) ord[i] = i;
+        std::sort(ord.begin(), ord.end(), [&](size_t x, size_t y) {
+            return hp[x] != hp[y] ? hp[x] < hp[y] : he[x] < he[y];
+        });
+        th->taps.resize(nk);
+        for (size_t i = 0; i < nk; ++i) {
+            const size_t k = ord[i];
+            const CandPair& c = cp[hp[k]];
+            Tap& t = th->taps[i];
+            t.a = hp[k] / L.S;
+            t.b = hp[k] % L.S;
+            t.oy = he[k] / c.cols;
+            t.ox = he[k] % c.cols;
+            t.v = hv[k];
+        }
+    } while (false);
+    if (have_pf) cufftDestroy(pf);
+    if (have_pi) cufftDestroy(pi);
+    cudaStreamSynchronize(st);
+    cleanup();
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Preconditioner tables and step (power iteration)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+static wdb_status power_iteration(wdb_theta* th, const std::vector<double>& P, cudaStream_t st, double* L_out) {
+    const Layout& L = th->lay;
+    const long long N = L.N;
+    std::vector<double> sc(P.size());
+    for (size_t i = 0; i < P.size(); ++i) sc[i] = 1.0 / std::sqrt(P[i]);
+    T *v = nullptr, *t = nullptr, *u = nullptr;
+    double *d_sc = nullptr, *d_out = nullptr;
+    WDB_CK(cudaMalloc(&v, sizeof(T) * N));
+    WDB_CK(cudaMalloc(&t, sizeof(T) * N));
+    WDB_CK(cudaMalloc(&u, sizeof(T) * N));
+    WDB_CK(cudaMalloc(&d_sc, sizeof(double) * sc.size()));
+    WDB_CK(cudaMalloc(&d_out, sizeof(double)));
+    WDB_CK(cudaMemcpyAsync(d_sc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
+    StencilArgs F = stencil_args(th, false), A = stencil_args(th, true);
+    wdb_status s = WDB_OK;
+    double lam = 0.0, h_out = 0.0;
+    RedTarget red = th_red(th, d_out);
+    if (s == WDB_OK) s = launch_splitmix<T>(v, N, kPowerSeed, st);
+    if (s == WDB_OK) s = launch_norm2<T>(v, N, red, th->grid, st);
+    cudaMemcpyAsync(&h_out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) s = set_error(WDB_ECUDA, "power iteration start");
+    if (s == WDB_OK) s = launch_scale_const<T>(v, v, N, 1.0 / std::sqrt(h_out), st);
+    for (int it = 1; it <= kPowerIters && s == WDB_OK; ++it) {
+        if ((s = launch_scale<T>(F, th->grid, v, t, d_sc, st))) break;
+        if ((s = launch_apply<T>(F, th->grid, t, u, nullptr, nullptr, st))) break;
+        if ((s = launch_apply<T>(A, th->grid, u, t, d_sc, &red, st))) break;
+        cudaMemcpyAsync(&h_out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = cuda_error(e, "power iteration", __FILE__, __LINE__); break; }
+        const double lam_new = std::sqrt(h_out);
+        if (!(lam_new > 0.0) || !std::isfinite(lam_new)) { lam = lam_new; break; }
+        if ((s = launch_scale_const<T>(t, v, N, 1.0 / lam_new, st))) break;
+        const bool done = std::fabs(lam_new - lam) <= kPowerRtol * lam_new;
+        lam = lam_new;
+        if (done) break;
+    }
+    cudaStreamSynchronize(st);
+    cudaFree(v);
+    cudaFree(t);
+    cudaFree(u);
+    cudaFree(d_sc);
+    cudaFree(d_out);
+    if (s != WDB_OK) return s;
+    if (!std::isfinite(lam)) return set_error(WDB_ENAN, "power iteration produced %g", lam);
+    *L_out = lam;
+    return WDB_OK;
+}
+
+std::vector<double> precond_table(const std::vector<double>& Md, const std::vector<double>& M2d, int kind,
+                                  double eps) {
+    std::vector<double> P(Md.size(), 1.0);
+    if (kind == WDB_PRECOND_JACOBI) {
+        double mx = 0.0;
+        for (double m : Md) mx = std::max(mx, m);
+        const double e = eps > 0.0 ? eps : 1e-6 * mx;
+        for (size_t i = 0; i < P.size(); ++i) P[i] = std::max(Md[i], e);
+        for (double& p : P)
+            if (!(p > 0.0)) p = 1.0;
+    } else if (kind == WDB_PRECOND_SPAI) {
+        for (size_t i = 0; i < P.size(); ++i) P[i] = Md[i] > 0.0 ? M2d[i] / Md[i] : 1.0;
+    }
+    return P;
+}
+
+wdb_status precond_upload(wdb_theta* th, PrecondCache& pc, cudaStream_t st) {
+    const int n = (int)pc.P.size();
+    if (!pc.d_step) WDB_TRY(th_alloc(th, &pc.d_step, n));
+    std::vector<float> stp(n);
+    for (int i = 0; i < n; ++i) stp[i] = (float)(pc.tau / pc.P[i]);
+    WDB_CK(cudaMemcpyAsync(pc.d_step, stp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
+    WDB_CK(cudaStreamSynchronize(st));
+    return WDB_OK;
+}
+
+wdb_status theta_precond(wdb_theta* th, int kind, double eps, cudaStream_t st) {
+    if (kind < 0 || kind > 2) return set_error(WDB_EINVAL, "unknown preconditioner %d", kind);
+    PrecondCache& pc = th->pc[kind];
+    if (pc.valid && (pc.pinned || kind != WDB_PRECOND_JACOBI || pc.eps == eps)) return WDB_OK;
+    if (!th->diag_valid) return set_error(WDB_EINVAL, "diagonal tables missing");
+    pc.P = precond_table(th->Md, th->M2d, kind, eps);
+    double Lh = 0.0;
+    if (setup_fp64(th)) WDB_TRY(power_iteration<double>(th, pc.P, st, &Lh));
+    else WDB_TRY(power_iteration<float>(th, pc.P, st, &Lh));
+    pc.L_hat = Lh;
+    pc.tau = Lh > 0.0 ? 1.0 / (kStepMargin * Lh) : 1.0;
+    pc.eps = eps;
+    WDB_TRY(precond_upload(th, pc, st));
+    pc.valid = true;
+    return WDB_OK;
+}
+
+}  // namespace wdb

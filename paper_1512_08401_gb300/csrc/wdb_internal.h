@@ -1,0 +1,233 @@
+// Internal declarations of libwdb (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/wdb.h"
+
+namespace wdb {
+
+constexpr int kMaxS = WDB_MAX_SUBBANDS;
+constexpr int kMaxL = 20;  // db10
+
+// ---------------------------------------------------------------------------------------
+// Errors
+// ---------------------------------------------------------------------------------------
+wdb_status set_error(wdb_status s, const char* fmt, ...);
+wdb_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define WDB_CK(call)                                                              \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) return ::wdb::cuda_error(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define WDB_TRY(call)                                \
+    do {                                             \
+        wdb_status s_ = (call);                      \
+        if (s_ != WDB_OK) return s_;                 \
+    } while (0)
+
+// Count of kernels launched by the library (graph replays add their node counts).
+void count_launch(long long n = 1);
+
+// ---------------------------------------------------------------------------------------
+// Subband layout (Sec. 2): subband-planar, A_J first, then (0,1),(1,0),(1,1) for s=J..1
+// ---------------------------------------------------------------------------------------
+struct SubbandDev {      // per subband, device-resident copy
+    long long off;       // start in the coefficient vector
+    int rows, cols;
+    int level;           // s (1 = finest)
+    int lgR;             // log2 of the phase period R = 2^{J - s}
+    int tab_off;         // start of this subband in the phase tables (4^J entries in all)
+    int pad;
+};
+
+struct Layout {
+    int n_rows = 0, n_cols = 0, J = 0, S = 0;
+    long long N = 0;
+    SubbandDev sb[kMaxS];
+    int tab_len = 0;     // sum_b R_b^2 = 4^J
+};
+wdb_status make_layout(int n_rows, int n_cols, int J, Layout* out);
+
+// ---------------------------------------------------------------------------------------
+// Daubechies filters (derived on the host by spectral factorisation)
+// ---------------------------------------------------------------------------------------
+struct Filters {
+    int L = 0;
+    double h[kMaxL], g[kMaxL];
+};
+wdb_status wavelet_filters(const char* name, Filters* out);
+
+template <typename T>
+struct FiltT {
+    int L;
+    T h[kMaxL], g[kMaxL];
+};
+template <typename T>
+FiltT<T> filt_cast(const Filters& f) {
+    FiltT<T> o;
+    o.L = f.L;
+    for (int k = 0; k < kMaxL; k++) {
+        o.h[k] = (T)(k < f.L ? f.h[k] : 0.0);
+        o.g[k] = (T)(k < f.L ? f.g[k] : 0.0);
+    }
+    return o;
+}
+
+// ---------------------------------------------------------------------------------------
+// Wavelet transforms (dwt.cu). scratch holds >= N/2 elements.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+wdb_status dwt2(const T* img, T* coef, const Layout& L, const Filters& f, T* scratch,
+                cudaStream_t st);
+template <typename T>
+wdb_status idwt2(const T* coef, T* img, const Layout& L, const Filters& f, T* scratch,
+                 cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
+// Device reduction / solver state
+// ---------------------------------------------------------------------------------------
+struct SolveState {
+    int k;                  // 1-based iteration about to run / running
+    int stop;               // 1: done (converged, max_iters, or error)
+    int max_iters;
+    int check_every;
+    double tol;
+    unsigned int done[4];   // last-CTA counters
+    double rr, x0r;         // from the residual kernel of the current iteration
+    double wy, gmax;        // from the step kernel of the current iteration
+    double primal, dual, gap, rel_gap;  // certificate of the last check
+    int gap_k;              // iteration of the last check
+    int iters_done;         // k of the last computed x
+    int nan_flag;
+    int pad;
+    double first_primal;
+    double scratch[8];      // free slots for one-off reductions
+};
+
+// Reduction slots for one-off launches (power iteration, probes, objective).
+struct RedSlot {
+    unsigned int done;
+    unsigned int pad;
+    double sum[4];
+};
+
+// ---------------------------------------------------------------------------------------
+// Stencil representation of Theta_K / Theta_K^T as gather operators
+//   down pair (input finer or equal, ratio r = 2^lg): out[p] += v * in[r p + d]
+//   up pair   (input coarser, r = 2^lg):  out[r P + phi] += v * in[P + d] for taps of phase phi
+// ---------------------------------------------------------------------------------------
+struct PairDesc {
+    int in_sb;
+    int meta;       // (up << 8) | lg
+    int a, b;       // down: taps [a, b);  up: phase table at phase_idx[a .. a + r*r]
+};
+
+struct OpDev {
+    const int* pair_start;   // [S+1] pairs of output subband o: [pair_start[o], pair_start[o+1])
+    const PairDesc* pairs;
+    const int* phase_idx;
+    const int* tap_off;      // (dy << 16) | (dx & 0xffff)
+    const float* tap_v;
+    const double* tap_v64;
+    int n_pairs, n_taps, n_phase;
+};
+
+struct OpHost {
+    std::vector<int> pair_start;
+    std::vector<PairDesc> pairs;
+    std::vector<int> phase_idx;
+    std::vector<int> tap_off;
+    std::vector<float> tap_v;
+    std::vector<double> tap_v64;
+};
+
+// Virtual-block schedule: blocks of kVB consecutive outputs that stay inside one subband.
+constexpr int kVB = 256;
+struct Schedule {
+    int nvb = 0;                 // number of virtual blocks
+    std::vector<int> vb_start;   // [S+1] first virtual block of each subband
+};
+Schedule make_schedule(const Layout& L);
+
+struct Tap {
+    int a, b, oy, ox;
+    double v;
+};
+
+// ---------------------------------------------------------------------------------------
+// Theta handle internals
+// ---------------------------------------------------------------------------------------
+struct PrecondCache {
+    bool valid = false;
+    bool pinned = false;     // set by the caller (wdb_*_set_precond): never recomputed
+    double eps = 0.0;
+    std::vector<double> P;   // tab_len
+    double tau = 0.0, L_hat = 0.0;
+    float* d_step = nullptr; // tab_len floats: tau / P (device)
+    float* d_Pf = nullptr;   // tab_len floats: P
+};
+
+// A non-blocking library stream joined to the caller's stream with events on entry and
+// exit, so that graph capture works whatever stream the caller uses (including the legacy
+// default stream, which cannot be captured).
+struct WorkStream {
+    cudaStream_t* work;
+    cudaEvent_t* ev_in;
+    cudaEvent_t* ev_out;
+};
+wdb_status work_enter(cudaStream_t* work, cudaEvent_t* ev_in, cudaEvent_t* ev_out, cudaStream_t caller);
+wdb_status work_exit(cudaStream_t work, cudaEvent_t ev_out, cudaStream_t caller);
+
+// Replays chunks of iterations (as a CUDA graph when enabled) until the device state stops.
+struct IterEngine {
+    std::function<wdb_status(int)> enqueue;   // puts `iters` iterations on the stream
+    cudaGraphExec_t graph_exec = nullptr;
+    int graph_m = 0;
+    long long graph_kernels = 0;
+    int key = -1;
+    SolveState* d_state = nullptr;
+    SolveState* h_state = nullptr;
+    void release();
+};
+
+}  // namespace wdb
+
+struct wdb_theta {
+    wdb::Layout lay;
+    wdb::Filters filt;
+    std::string wavelet;
+    int rule = 0;
+    long long K_requested = 0, K_eff = 0, n_candidates = 0;
+    double theta_max_abs = 0.0, build_ms = 0.0;
+    std::vector<wdb::Tap> taps;            // sorted (a, b, oy, ox)
+    wdb::OpHost fwd_h, adj_h;
+    wdb::OpDev fwd{}, adj{};
+    std::vector<void*> allocs;             // device buffers owned by the handle
+    wdb::SubbandDev* d_sb = nullptr;
+    int* d_vb_start = nullptr;
+    wdb::Schedule sched;
+    int grid = 0;                          // CTAs for the persistent-style loops
+    unsigned int* d_counter = nullptr;     // last-CTA counter for one-off reductions
+    double* d_red_part = nullptr;          // per-CTA partials for one-off reductions
+    bool diag_valid = false;
+    std::vector<double> Md, M2d;           // phase tables of diag(M), diag(M^2)
+    wdb::PrecondCache pc[3];
+    // solve workspace (allocated on first solve)
+    float *d_x0 = nullptr, *d_y = nullptr, *d_r = nullptr, *d_scr = nullptr, *d_xs = nullptr;
+    wdb::IterEngine engine[3];             // one captured iteration chunk per preconditioner
+    cudaStream_t work = nullptr;           // library stream the solve runs (and is captured) on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    float* d_w = nullptr;                  // per-subband weights (S floats)
+    double* d_part = nullptr;              // per-CTA partials
+    wdb::SolveState* d_state = nullptr;
+    wdb::SolveState* h_state = nullptr;    // pinned
+    long long ws_N = 0;
+};

@@ -1,0 +1,277 @@
+"""GPU (libwdb through its C ABI) against the FP64 oracle, element by element.
+
+Tolerances (FP32 iterates against an FP64 oracle):
+  * wavelet transforms and single operator applications: max |err| <= 2e-6 * max |ref|
+    (a few FP32 roundings of sums of <= a few hundred terms);
+  * Theta_K taps: built in FP64 on both sides, values within 1e-12 * max|Theta|; the kept
+    sets may differ only by taps whose score lies within 1e-9 (relative) of the selection
+    boundary (the two sides compute the probes with different rounding: FFT vs direct sums);
+  * FISTA trajectories with the same operator, P and tau: ||x_gpu - x_ora|| <= 1e-5 ||x_ora||
+    and |E_gpu - E_ora| <= 1e-5 E_ora, the target the method states for the GPU path.
+"""
+import numpy as np
+import pytest
+
+from oracle import blur, precond, solver, theta, wavelet
+from paper_1512_08401_gb300 import synthetic
+
+from oracle_cases import build_case, fista, precond_and_step, taps_arrays
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wdb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_08401_gb300 import build, wdb as w
+    build.build()
+    w.lib()
+    return w
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32).ravel()).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel_max(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+# ---------------------------------------------------------------------------------------
+# wavelet transforms
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_rows,n_cols,J", [(64, 64, 3), (48, 80, 3), (128, 128, 4), (16, 16, 4), (32, 64, 5)])
+def test_dwt_idwt_parity(wdb, n_rows, n_cols, J):
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal((n_rows, n_cols))
+    c = torch.zeros(n_rows * n_cols, device="cuda")
+    wdb.dwt(dev(u), c, n_rows, n_cols, "db4", J)
+    ref = wavelet.dwt2(u, "db4", J)
+    assert rel_max(host(c), ref) < 2e-6
+    img = torch.zeros_like(c)
+    wdb.idwt(dev(ref), img, n_rows, n_cols, "db4", J)
+    assert rel_max(host(img), wavelet.idwt2(ref, n_rows, n_cols, "db4", J).ravel()) < 2e-6
+
+
+# ---------------------------------------------------------------------------------------
+# Theta_K construction (Algorithm 2 + Sec. 3.7)
+# ---------------------------------------------------------------------------------------
+
+def compare_taps(gpu_taps, ora: theta.ThetaK, rule):
+    """Values agree; kept sets agree away from the selection boundary."""
+    a, b, oy, ox, v = gpu_taps
+    lay = ora.lay
+    key_g = {(int(a[i]), int(b[i]), int(oy[i]), int(ox[i])): v[i] for i in range(len(v))}
+    t = ora.taps
+    key_o = {(int(t.a[i]), int(t.b[i]), int(t.oy[i]), int(t.ox[i])): t.v[i] for i in range(len(t))}
+    vmax = max(np.abs(t.v).max() if len(t) else 0.0, np.abs(v).max() if len(v) else 0.0, 1e-300)
+    common = set(key_g) & set(key_o)
+    for k in common:
+        assert abs(key_g[k] - key_o[k]) <= 1e-12 * vmax, k
+    only = (set(key_g) ^ set(key_o))
+    if only:
+        lev = np.array([s.level for s in lay], dtype=float)
+
+        def score(k, val):
+            return abs(val) * (2.0 ** lev[k[1]] if rule == "weighted" else 1.0)
+        kept_scores = [score(k, key_o[k]) for k in key_o]
+        boundary = min(kept_scores)
+        for k in only:
+            val = key_g.get(k, key_o.get(k))
+            assert abs(score(k, val) - boundary) <= 1e-9 * boundary, (k, score(k, val), boundary)
+    return len(common), len(only)
+
+
+CASES = {
+    "gauss64": (synthetic.gaussian_psf(1.5, 9), 64, 64, 3),
+    "motion64": (synthetic.motion_line_psf(7, 0.9), 64, 64, 3),
+    "ragged48x80": (synthetic.gaussian_psf(1.2, 7), 48, 80, 3),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("rule", ["weighted", "naive"])
+@pytest.mark.parametrize("kn", [3, 30])
+def test_theta_build_parity(wdb, name, rule, kn):
+    psf, nr, nc, J = CASES[name]
+    K = kn * nr * nc
+    g = wdb.Theta.build(psf, nr, nc, "db4", J, K=K, rule=rule)
+    ora = theta.build_theta(psf, nr, nc, "db4", J, K, rule)
+    assert g.info.K_eff <= K
+    assert abs(g.info.K_eff - ora.K_eff) <= 0.01 * K
+    compare_taps(g.export_taps(), ora, rule)
+
+
+def test_theta_keep_all_and_empty(wdb):
+    psf = synthetic.motion_line_psf(5, 0.7)
+    n, J = 16, 2
+    g = wdb.Theta.build(psf, n, n, "db4", J, K=10 ** 12)
+    dense = theta.theta_dense(n, n, psf, "db4", J)
+    # apply to every unit vector: the columns of Theta_K (FP32 apply)
+    cols = np.zeros((n * n, n * n))
+    e = torch.zeros(n * n, device="cuda")
+    out = torch.zeros_like(e)
+    for k in range(n * n):
+        e.zero_()
+        e[k] = 1.0
+        g.apply(e, out)
+        cols[:, k] = host(out)
+    assert np.abs(cols - dense).max() < 1e-6 * np.abs(dense).max()
+    z = wdb.Theta.build(psf, n, n, "db4", J, K=0)
+    assert z.info.K_eff == 0 and z.info.n_taps == 0
+    x = torch.ones(n * n, device="cuda")
+    z.apply(x, out)
+    assert float(host(out).max()) == 0.0
+
+
+# ---------------------------------------------------------------------------------------
+# operator application and preconditioners with the oracle's own taps
+# ---------------------------------------------------------------------------------------
+
+def gpu_from_oracle(wdb, case, nr, nc, J):
+    a, b, oy, ox, v = taps_arrays(case.th)
+    return wdb.Theta.from_taps(nr, nc, "db4", J, a, b, oy, ox, v)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_apply_parity(wdb, name):
+    psf, nr, nc, J = CASES[name]
+    rng = np.random.default_rng(12)
+    u0 = rng.standard_normal((nr, nc))
+    case = build_case(psf, nr, nc, J, 30 * nr * nc, u0)
+    g = gpu_from_oracle(wdb, case, nr, nc, J)
+    assert g.info.K_eff == case.th.K_eff
+    y = rng.standard_normal(nr * nc)
+    out = torch.zeros(nr * nc, device="cuda")
+    g.apply(dev(y), out)
+    assert rel_max(host(out), case.th.mat @ y) < 2e-6
+    g.apply(dev(y), out, transpose=True)
+    assert rel_max(host(out), case.th.matT @ y) < 2e-6
+
+
+@pytest.mark.parametrize("kind", ["none", "jacobi", "spai"])
+def test_precond_and_step_parity(wdb, kind):
+    psf, nr, nc, J = CASES["motion64"]
+    rng = np.random.default_rng(13)
+    case = build_case(psf, nr, nc, J, 30 * nr * nc, rng.standard_normal((nr, nc)))
+    g = gpu_from_oracle(wdb, case, nr, nc, J)
+    res = g.precond(kind)
+    assert np.abs(res["Md"] - case.Md).max() <= 1e-11 * case.Md.max()
+    assert np.abs(res["M2d"] - case.M2d).max() <= 1e-11 * case.M2d.max()
+    Ptab, _, tau, L = precond_and_step(case, kind)
+    assert np.abs(res["P"] - Ptab).max() <= 1e-10 * Ptab.max()
+    assert abs(res["L_hat"] - L) <= 1e-9 * L
+    assert abs(res["tau"] - tau) <= 1e-9 * tau
+
+
+# ---------------------------------------------------------------------------------------
+# FISTA (Algorithm 3)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["none", "spai", "jacobi"])
+def test_fista_trajectory_parity_128(wdb, kind):
+    prob = synthetic.small_problem()
+    n, J, lam = 128, 4, prob.lam
+    case = build_case(prob.psf, n, n, J, 30 * n * n, prob.u0)
+    Ptab, P, tau, _ = precond_and_step(case, kind)
+    ref = fista(case, lam, P, tau, 200)
+    g = gpu_from_oracle(wdb, case, n, n, J)
+    g.set_precond(kind, Ptab, tau)
+    x = torch.zeros(n * n, device="cuda")
+    r = g.solve_coeffs(dev(case.x0), x, lam=lam, max_iters=200, tol=0.0, precond=kind)
+    xg = host(x)
+    assert r["iters"] == 200
+    assert np.linalg.norm(xg - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    assert abs(r["objective"] - ref.objective) <= 1e-5 * ref.objective
+    # objective of the GPU iterate evaluated by the oracle
+    A, _ = solver.theta_ops(case.th)
+    E_ora_of_gpu = solver.objective(A(xg) - case.x0, xg, np.full(n * n, lam))
+    assert abs(r["objective"] - E_ora_of_gpu) <= 1e-6 * E_ora_of_gpu
+
+
+def test_solve_from_image_and_graph_vs_no_graph(wdb):
+    prob = synthetic.small_problem()
+    n, J = 128, 4
+    g = wdb.Theta.build(prob.psf, n, n, "db4", J, K=30 * n * n)
+    u = dev(prob.u0)
+    x1 = torch.zeros(n * n, device="cuda")
+    x2 = torch.zeros(n * n, device="cuda")
+    r1 = g.solve(u, x1, lam=prob.lam, max_iters=60, precond="spai")
+    r2 = g.solve(u, x2, lam=prob.lam, max_iters=60, precond="spai", no_graph=True)
+    assert r1["iters"] == r2["iters"] == 60
+    assert torch.equal(x1, x2)
+
+
+def test_gap_certificate_and_stop(wdb):
+    prob = synthetic.small_problem()
+    n, J, lam = 128, 4, prob.lam
+    case = build_case(prob.psf, n, n, J, 30 * n * n, prob.u0)
+    Ptab, P, tau, _ = precond_and_step(case, "spai")
+    g = gpu_from_oracle(wdb, case, n, n, J)
+    g.set_precond("spai", Ptab, tau)
+    x = torch.zeros(n * n, device="cuda")
+    r = g.solve_coeffs(dev(case.x0), x, lam=lam, max_iters=5000, tol=1e-4, precond="spai", check_every=10)
+    assert r["rel_gap"] <= 1e-4 and r["iters"] % 10 == 0 and r["iters"] < 5000
+    ref = fista(case, lam, P, tau, 5000, tol=1e-4, check_every=10)
+    assert ref.iters == r["iters"]
+    # certified bound on the returned x against a lower bound on E* (dual value of a long run)
+    star = fista(case, lam, P, tau, 20000, tol=1e-9, check_every=50)
+    E_low = star.objective - star.gap
+    assert r["objective"] - E_low <= 1.01e-4 * r["primal"]
+    assert r["objective"] >= E_low
+
+
+def test_end_to_end_gpu_built_operator(wdb):
+    # GPU-built Theta_K, P, tau vs the oracle's, both solved to a 1e-7 certificate
+    psf, nr, nc, J = CASES["gauss64"]
+    rng = np.random.default_rng(14)
+    u0 = synthetic.blur_fft(synthetic.clean_image(nr, nc, rng), psf) + 0.01 * rng.standard_normal((nr, nc))
+    lam = 1e-3
+    case = build_case(psf, nr, nc, J, 30 * nr * nc, u0)
+    Ptab, P, tau, _ = precond_and_step(case, "spai")
+    ref = fista(case, lam, P, tau, 50000, tol=1e-7, check_every=10)
+    g = wdb.Theta.build(psf, nr, nc, "db4", J, K=30 * nr * nc)
+    x = torch.zeros(nr * nc, device="cuda")
+    r = g.solve(dev(u0), x, lam=lam, max_iters=50000, tol=1e-5, precond="spai")
+    assert r["rel_gap"] <= 1e-5
+    # both certified: |E_gpu - E_ora| <= 1e-5 E (+ the oracle's own 1e-7 gap)
+    assert abs(r["objective"] - ref.objective) <= 1.1e-5 * ref.objective
+
+
+# ---------------------------------------------------------------------------------------
+# FFT path (exact operator)
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind", ["none", "spai"])
+def test_fft_path_trajectory_parity(wdb, kind):
+    psf, nr, nc, J = CASES["motion64"]
+    rng = np.random.default_rng(15)
+    u0 = synthetic.blur_fft(synthetic.clean_image(nr, nc, rng), psf) + 0.01 * rng.standard_normal((nr, nc))
+    lam = 1e-3
+    lay = wavelet.layout(nr, nc, J)
+    Md, M2d = solver.exact_diagonal_tables(psf, nr, nc, "db4", J, lay)
+    Psb = precond.preconditioner(Md, M2d, kind)
+    P = precond.expand(Psb, lay, [1] * len(lay))
+    A, At = solver.exact_ops(psf, nr, nc, "db4", J)
+    L, _ = precond.power_iteration(lambda v: At(A(v)), P)
+    tau = precond.step_size(L)
+    ref = solver.fista(A, At, u0.ravel(), np.full(nr * nc, lam), P, tau, 100)
+    op = wdb.FFTOp(psf, nr, nc, "db4", J)
+    got = op.precond(kind)
+    assert np.abs(got["P"] - Psb).max() <= 1e-10 * Psb.max()
+    assert abs(got["L_hat"] - L) <= 1e-8 * L
+    op.set_precond(kind, Psb, tau)
+    x = torch.zeros(nr * nc, device="cuda")
+    r = op.solve(dev(u0), x, lam=lam, max_iters=100, precond=kind)
+    xg = host(x)
+    assert np.linalg.norm(xg - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    assert abs(r["objective"] - ref.objective) <= 1e-5 * ref.objective
