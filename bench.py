@@ -1,0 +1,397 @@
+#!/usr/bin/env python3
+"""Benchmark of wavelet-domain l1-l2 deblurring on GB300 (Escande & Weiss, arXiv 1512.08401).
+
+Metric: milliseconds for one solve to reach a 1e-4 relative objective gap,
+(E(y^(k)) - E*)/E* <= 1e-4, with the compressed operator Theta_K, and FISTA iterations/s;
+the exact-operator FFT path is timed on the same GPU beside it.
+
+Workload (per rank): 1024 x 1024 synthetic image (random rectangles over a gradient, Gaussian
+blur sigma = 3 on 31 x 31, noise 0.01), db4 with J = 5, lambda = 1e-3, K = 30 N (weighted
+rule), SPAI preconditioner, FP32 iterates with FP64 reductions. E* of each path comes from a
+long untimed run of the same path. A step is one whole solve (DWT of u, FISTA to the target,
+final FP64 objective, result copy) with the input resident in HBM; L2 is flushed between
+steps. Operator construction is offline (untimed), as in the paper (Sec. 5.4).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--no-cpu-baseline] [--no-large]
+For N > 1 launch with torch.distributed.run; every rank solves its own instance (replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ms to 1e-4 rel. objective gap & FISTA iters/s, Theta_K vs FFT path, 1024^2"
+N_SIDE, LEVELS, LAM, KN, PRECOND = 1024, 5, 1e-3, 30, "spai"
+REL_GAP = 1e-4
+WORKLOAD = ("1024x1024 synthetic (rectangles over gradient), gaussian sigma=3 31x31, noise 0.01, db4 J=5, "
+            "lambda=1e-3, Theta_K K=30N weighted, SPAI, solve to 1e-4 relative objective gap")
+ORACLE_DATA = os.path.join(ROOT, "oracle", "data", "headline_1024_gauss_k30_spai.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=20)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# distributed helpers (one process per GPU; replicas, no data-path collective)
+# ---------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, torch):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+            self.pg = dist
+
+    def barrier(self, torch):
+        if self.pg:
+            self.pg.barrier()
+        torch.cuda.synchronize()
+
+    def max(self, torch, v: float) -> float:
+        if not self.pg:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "of measured"
+    except Exception:
+        return 6800.0, "of fallback"
+
+
+def traffic_record(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the sources it was
+    measured on are unchanged (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1512_08401_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    entry = rec.get(kernel)
+    if not entry or entry.get("csrc_sha256") != h.hexdigest():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------------------
+# oracle (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------------------
+def oracle_setup(prob, workers: int):
+    """The FP64 oracle's Theta_K, SPAI P and tau for the workload (untimed, offline)."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    from oracle import precond, solver, theta, wavelet
+    ctx = mp.get_context("spawn")
+    with ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as pool:
+        th = theta.build_theta(prob.psf, N_SIDE, N_SIDE, "db4", LEVELS, KN * N_SIDE * N_SIDE, "weighted", pool=pool)
+    per = precond.theta_periods(th.lay, LEVELS)
+    Md, M2d = precond.diagonal_tables(th.mat, th.matT, th.lay, per)
+    P = precond.expand(precond.preconditioner(Md, M2d, PRECOND), th.lay, per)
+    A, At = solver.theta_ops(th)
+    L, _ = precond.power_iteration(lambda v: At(A(v)), P)
+    x0 = wavelet.dwt2(prob.u0, "db4", LEVELS)
+    return th, A, At, x0, P, precond.step_size(L)
+
+
+def oracle_ms_per_iter(setup, iters: int) -> float:
+    from oracle import solver
+    th, A, At, x0, P, tau = setup
+    w = np.full(len(x0), LAM)
+    t0 = time.perf_counter()
+    solver.fista(A, At, x0, w, P, tau, iters)
+    return 1e3 * (time.perf_counter() - t0) / iters
+
+
+def oracle_threads() -> int:
+    # scipy CSR products and numpy elementwise operations run on one thread
+    return 1
+
+
+# ---------------------------------------------------------------------------------------
+# reference arm: the oracle as it stands, timed on the host cores
+# ---------------------------------------------------------------------------------------
+def run_reference(args):
+    d = Dist()
+    if d.rank != 0:
+        return 0
+    from paper_1512_08401_gb300 import synthetic
+    try:
+        with open(ORACLE_DATA) as fh:
+            od = json.load(fh)
+        n_it = int(od["iters_to_rel_1e-4"])
+    except Exception as e:
+        print(json.dumps({"impl": "reference", "unavailable": f"oracle workload data missing: {e}"}))
+        return 0
+    prob = synthetic.headline_problem("gaussian", 0)
+    setup = oracle_setup(prob, workers=min(16, os.cpu_count() or 1))
+    per_step_iters = 3
+    for _ in range(args.warmup):
+        oracle_ms_per_iter(setup, 1)
+    times = [oracle_ms_per_iter(setup, per_step_iters) for _ in range(args.steps)]
+    ms_iter = statistics.mean(times)
+    value = ms_iter * n_it
+    sample = (f"{per_step_iters} FISTA iterations per step of the FP64 oracle (scipy CSR Theta_K, same 1024^2 "
+              f"problem), scaled by the {n_it} iterations the oracle needs to reach the 1e-4 relative gap")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "parallelism": "replicas"},
+           "fista_iters_per_s": 1e3 / ms_iter,
+           "cpu_baseline": {"value": value, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    d = Dist()
+    torch.cuda.set_device(d.local)
+    d.init(torch)
+    from paper_1512_08401_gb300 import build, synthetic, wdb
+    build.build()
+    wdb.lib()
+
+    prob = synthetic.headline_problem("gaussian", d.rank)
+    n, N = N_SIDE, N_SIDE * N_SIDE
+    th = wdb.Theta.build(prob.psf, n, n, "db4", LEVELS, K=KN * N)
+    fop = wdb.FFTOp(prob.psf, n, n, "db4", LEVELS)
+    pc = th.precond(PRECOND)
+    fpc = fop.precond(PRECOND)
+    u_dev = torch.from_numpy(prob.u0.astype(np.float32).ravel()).cuda()
+    x_dev = torch.zeros(N, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
+    # E* of each path: long untimed runs of the same path
+    r_star = th.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND)
+    f_star = fop.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND)
+    E_theta, E_fft = r_star["objective"], f_star["objective"]
+    tgt_theta, tgt_fft = E_theta * (1 + REL_GAP), E_fft * (1 + REL_GAP)
+
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(solve_fn, steps, e2e=False):
+        ms, res = [], []
+        if e2e:
+            u_host = torch.from_numpy(prob.u0.astype(np.float32).ravel()).pin_memory()
+            x_host = torch.empty(N, dtype=torch.float32).pin_memory()
+        for _ in range(steps):
+            flush.fill_(1.0)
+            d.barrier(torch)
+            start.record()
+            if e2e:
+                u_dev.copy_(u_host, non_blocking=True)
+            r = solve_fn()
+            if e2e:
+                x_host.copy_(x_dev, non_blocking=True)
+            end.record()
+            end.synchronize()
+            ms.append(start.elapsed_time(end))
+            res.append(r)
+        return ms, res
+
+    theta_solve = lambda: th.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND,  # noqa: E731
+                                   target_objective=tgt_theta, time_kernels=True)
+    fft_solve = lambda: fop.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND,  # noqa: E731
+                                  target_objective=tgt_fft, time_kernels=True)
+    timed(theta_solve, args.warmup)
+    timed(fft_solve, args.warmup)
+    clocks = Clocks()
+    clocks.start()
+    wdb.kernel_launches(reset=True)
+    d.barrier(torch)
+    t_ms, t_res = timed(theta_solve, args.steps)
+    launches = wdb.kernel_launches()
+    f_ms, f_res = timed(fft_solve, args.steps)
+    clk = clocks.stop()
+    e_ms, _ = timed(theta_solve, args.steps, e2e=True)
+
+    ms_theta = d.max(torch, statistics.mean(t_ms))
+    ms_fft = d.max(torch, statistics.mean(f_ms))
+    ms_e2e = d.max(torch, statistics.mean(e_ms))
+    it_theta = statistics.mean(r["iters"] for r in t_res)
+    it_fft = statistics.mean(r["iters"] for r in f_res)
+    k1 = statistics.mean(r["ms_k1"] for r in t_res)
+    k2 = statistics.mean(r["ms_k2"] for r in t_res)
+
+    # roofline of the dominant kernel (algorithmic bytes: 12N + taps for kernel 1, 20N + taps +
+    # step table for kernel 2; FP32 values, 4-byte tap offsets and values)
+    T_fwd = th.info.n_taps
+    bytes_k1 = 12 * N + 8 * T_fwd
+    bytes_k2 = 20 * N + 8 * T_fwd + 4 * th.info.phase_table_len
+    name, dur, nbytes = ("k2_step", k2, bytes_k2) if k2 >= k1 else ("k1_residual", k1, bytes_k1)
+    peak, peak_src = measured_peaks()
+    achieved = nbytes / (dur * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic_record(name),
+            "bytes_per_launch": nbytes, "launch_ms": dur,
+            "note": "1024^2 working set (~24 MB) stays in L2 across iterations; HBM bound judged at 4096^2"}
+
+    out = {"metric": METRIC, "value": ms_theta, "unit": "ms", "n_gpus": d.world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_theta, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "global_batch": d.world, "parallelism": "replicas",
+                      "l2": "flushed between steps (256 MiB write)", "K_eff": th.info.K_eff,
+                      "n_taps": th.info.n_taps, "tau": pc["tau"], "L_hat": pc["L_hat"]},
+           "iters_to_gap": it_theta, "fista_iters_per_s": it_theta / (ms_theta * 1e-3),
+           "fft_path": {"ms": ms_fft, "iters": it_fft, "iters_per_s": it_fft / (ms_fft * 1e-3),
+                        "ms_gradient": statistics.mean(r["ms_k1"] for r in f_res),
+                        "ms_step": statistics.mean(r["ms_k2"] for r in f_res), "tau": fpc["tau"]},
+           "speedup_theta_vs_fft": ms_fft / ms_theta,
+           "E_star": {"theta_gpu": E_theta, "fft_gpu": E_fft},
+           "kernel_ms": {"k1_residual": k1, "k2_step": k2},
+           "roofline": roof,
+           "e2e": {"value": ms_e2e, "unit": "ms", "h2d_bytes_per_step": 4 * N, "d2h_bytes_per_step": 4 * N},
+           "gpu_launches": launches, "clocks": clk,
+           "build_ms": {"theta": th.info.build_ms}}
+    try:
+        with open(ORACLE_DATA) as fh:
+            od = json.load(fh)
+        out["E_star"]["theta_oracle_upper"] = od["E_star_upper"]
+        out["E_star"]["theta_oracle_lower"] = od["E_star_lower"]
+        out["E_star"]["oracle_iters_to_gap"] = od["iters_to_rel_1e-4"]
+    except Exception:
+        pass
+
+    if not args.no_large and d.rank == 0:
+        out["roofline_large"] = large_study(wdb, torch, peak, peak_src)
+
+    if d.rank == 0 and d.world == 1 and not args.no_cpu_baseline:
+        setup = oracle_setup(prob, workers=min(16, os.cpu_count() or 1))
+        ms_iter = oracle_ms_per_iter(setup, args.cpu_iters)
+        out["cpu_baseline"] = {
+            "value": ms_iter * it_theta, "unit": "ms", "cores": oracle_threads(), "kind": "oracle",
+            "sample": (f"{args.cpu_iters} FISTA iterations of the FP64 oracle (scipy CSR Theta_K built by the "
+                       f"oracle, same 1024^2 problem) = {ms_iter:.1f} ms/iteration, scaled by the "
+                       f"{it_theta:.0f} iterations of the solve")}
+    if d.rank == 0:
+        print(json.dumps(out))
+    d.close()
+    return 0
+
+
+def large_study(wdb, torch, peak, peak_src):
+    """4096 x 4096 (Gaussian sigma = 4 on 41 x 41, J = 6, K = 30 N, SPAI): per-launch time of
+    the two FISTA kernels over 200 iterations, against the HBM roofline."""
+    from paper_1512_08401_gb300 import synthetic
+    prob = synthetic.large_problem()
+    n, N = 4096, 4096 * 4096
+    th = wdb.Theta.build(prob.psf, n, n, "db4", 6, K=30 * N)
+    u = torch.from_numpy(prob.u0.astype(np.float32).ravel()).cuda()
+    x = torch.zeros(N, device="cuda")
+    th.solve(u, x, lam=LAM, max_iters=50, precond=PRECOND)
+    r = th.solve(u, x, lam=LAM, max_iters=200, precond=PRECOND, time_kernels=True)
+    T = th.info.n_taps
+    b1, b2 = 12 * N + 8 * T, 20 * N + 8 * T + 4 * th.info.phase_table_len
+    a1, a2 = b1 / (r["ms_k1"] * 1e-3) / 1e9, b2 / (r["ms_k2"] * 1e-3) / 1e9
+    it_ms = r["solve_ms"] / max(r["iters"], 1)
+    res = {"workload": "4096x4096 gaussian sigma=4 41x41, db4 J=6, K=30N, SPAI, 200 iterations",
+           "k1_residual": {"launch_ms": r["ms_k1"], "achieved": a1, "frac": a1 / peak},
+           "k2_step": {"launch_ms": r["ms_k2"], "achieved": a2, "frac": a2 / peak},
+           "iteration": {"achieved": (b1 + b2) / ((r["ms_k1"] + r["ms_k2"]) * 1e-3) / 1e9,
+                         "frac": (b1 + b2) / ((r["ms_k1"] + r["ms_k2"]) * 1e-3) / 1e9 / peak,
+                         "wall_ms_per_iter": it_ms},
+           "peak": peak, "unit": "GB/s", "peak_source": peak_src, "K_eff": th.info.K_eff,
+           "n_taps": T, "build_ms": th.info.build_ms}
+    th.free()
+    return res
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -84,6 +84,10 @@ typedef struct {
     int check_every;            /* gap check period m (<= 0: 10) */
     const float* x_init_dev;    /* N floats or NULL (zero start) */
     int no_graph;               /* 1: launch kernels one by one instead of CUDA graphs */
+    double target_objective;    /* > 0: also stop at the first k whose primal value at y^(k)
+                                   is <= target (checked on the device every iteration) */
+    int time_kernels;           /* 1: time one residual and one step launch per chunk with
+                                   CUDA events (reported in the result) */
 } wdb_solve_params;
 
 typedef struct {
@@ -93,6 +97,10 @@ typedef struct {
     long long support;          /* number of nonzero coefficients of x */
     double tau, L_hat;          /* step and Lipschitz estimate used */
     double solve_ms;            /* wall time of the call including the final synchronisation */
+    double ms_k1, ms_k2;        /* time_kernels: mean duration of one residual launch (kernel 1;
+                                   FFT path: IDWT+R2C+spectral+C2R+DWT) and one step launch */
+    int timed_chunks;           /* number of chunks those means average over */
+    int first_primal_below;     /* first k with primal(y^(k)) <= target_objective (0: none) */
     wdb_status status;
 } wdb_solve_result;
 

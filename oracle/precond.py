@@ -67,11 +67,11 @@ def diagonal_tables(mat, matT, lay, periods) -> tuple[np.ndarray, np.ndarray]:
         for py in range(R):
             for px in range(R):
                 i = b.offset + py * b.cols + px
-                v = np.asarray(csc[:, i].todense()).ravel()      # Theta_K e_i
-                w = matT @ v                                        # M e_i
+                v = csc[:, [i]]                 # Theta_K e_i (sparse column)
+                w = matT @ v                    # M e_i
                 t = offs[b.index] + py * R + px
-                Md[t] = v @ v
-                M2d[t] = w @ w
+                Md[t] = float(v.multiply(v).sum())
+                M2d[t] = float(w.multiply(w).sum())
     return Md, M2d
 
 

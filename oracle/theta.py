@@ -88,20 +88,27 @@ class Probes:
     row: list        # row[b] = Psi* H^T psi_{b,0} (N-vector)
 
 
+def probe(psf: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels: int, offset: int):
+    """(Psi* H psi, Psi* H^T psi) for psi the wavelet of coefficient `offset` (Algorithm 2)."""
+    e = np.zeros(n_rows * n_cols)
+    e[offset] = 1.0
+    psi = idwt2(e, n_rows, n_cols, wavelet, levels)
+    return (dwt2(conv_periodic(psi, psf), wavelet, levels),
+            dwt2(conv_adjoint(psi, psf), wavelet, levels))
+
+
 def compute_probes(psf: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels: int,
-                   conv=conv_periodic, conv_t=conv_adjoint) -> Probes:
-    """Algorithm 2, probe stage: for every subband b, blur the wavelet psi_{b,0} with H and
-    H^T and take one forward DWT of each."""
+                   pool=None) -> Probes:
+    """Algorithm 2, probe stage: for every subband b, blur the wavelet psi_{b,0} (the
+    coefficient at position (0,0) of b) with H and H^T and take one forward DWT of each.
+    `pool` (an executor) only spreads the independent probes over processes."""
     lay = layout(n_rows, n_cols, levels)
-    N = n_rows * n_cols
-    col, row = [], []
-    for b in lay:
-        e = np.zeros(N)
-        e[b.offset] = 1.0                      # coefficient (b, position (0,0))
-        psi = idwt2(e, n_rows, n_cols, wavelet, levels)
-        col.append(dwt2(conv(psi, psf), wavelet, levels))
-        row.append(dwt2(conv_t(psi, psf), wavelet, levels))
-    return Probes(n_rows, n_cols, wavelet, levels, lay, col, row)
+    args = [(psf, n_rows, n_cols, wavelet, levels, b.offset) for b in lay]
+    if pool is None:
+        res = [probe(*a) for a in args]
+    else:
+        res = list(pool.map(probe, *zip(*args)))
+    return Probes(n_rows, n_cols, wavelet, levels, lay, [c for c, _ in res], [r for _, r in res])
 
 
 def pair_taps(pr: Probes, a: Subband, b: Subband) -> tuple[np.ndarray, int, bool]:
@@ -246,11 +253,11 @@ class ThetaK:
 
 
 def build_theta(psf: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels: int,
-                K: int, rule: str = "weighted") -> ThetaK:
+                K: int, rule: str = "weighted", pool=None) -> ThetaK:
     """Algorithm 2 probes + Sec. 3.7 thresholding -> Theta_K."""
     if K < 0:
         raise ValueError("K must be >= 0")
-    pr = compute_probes(psf, n_rows, n_cols, wavelet, levels)
+    pr = compute_probes(psf, n_rows, n_cols, wavelet, levels, pool=pool)
     t = all_taps(pr)
     keep = select_taps(t, pr.lay, K, rule)
     kt = t.subset(keep)

@@ -60,6 +60,7 @@ SolveState init_state(const wdb_solve_params* p, int m) {
     s.check_every = m;
     s.tol = p->tol;
     s.primal = s.dual = s.gap = s.rel_gap = NAN;
+    s.target = p->target_objective > 0.0 ? p->target_objective : 0.0;
     return s;
 }
 
@@ -67,6 +68,7 @@ wdb_status check_params(const wdb_solve_params* p, int S) {
     if (!p) return set_error(WDB_EINVAL, "params is NULL");
     if (p->max_iters < 1) return set_error(WDB_EINVAL, "max_iters must be >= 1");
     if (!(p->tol >= 0.0) || !std::isfinite(p->tol)) return set_error(WDB_EINVAL, "tol must be finite and >= 0");
+    if (!std::isfinite(p->target_objective)) return set_error(WDB_EINVAL, "target_objective must be finite");
     if (p->precond < 0 || p->precond > 2) return set_error(WDB_EINVAL, "unknown preconditioner %d", p->precond);
     if (!p->w_subband_host && !(p->lambda >= 0.0 && std::isfinite(p->lambda)))
         return set_error(WDB_EINVAL, "lambda must be finite and >= 0");
@@ -94,25 +96,48 @@ double now_ms() {
 // ---------------------------------------------------------------------------------------
 // Runs chunks of m iterations (enqueue(m) puts m iterations on the stream) until the
 // device state says stop. With graphs, the chunk is captured once per (key) and replayed.
-static wdb_status run_loop(IterEngine& E, int m, bool use_graph, long long kernels_per_chunk, cudaStream_t st) {
+static wdb_status run_loop(IterEngine& E, int m, bool use_graph, bool timed, long long kernels_per_chunk,
+                           cudaStream_t st) {
     SolveState* hs = E.h_state;
+    E.sum_k1 = E.sum_k2 = 0.0;
+    E.n_timed = 0;
+    if (timed && !E.ev[0])
+        for (auto& e : E.ev) WDB_CK(cudaEventCreate(&e));
+    auto enqueue_chunk = [&]() -> wdb_status {
+        if (!timed) return E.enqueue(m);
+        if (m > 1) WDB_TRY(E.enqueue(m - 1));
+        return E.enqueue_timed(E.ev);
+    };
+    auto harvest = [&](int chunk) -> wdb_status {
+        // the sample is valid only if the chunk's last iteration ran (no stop before it)
+        if (timed && hs->iters_done >= chunk * m) {
+            float a = 0.f, b = 0.f;
+            WDB_CK(cudaEventElapsedTime(&a, E.ev[0], E.ev[1]));
+            WDB_CK(cudaEventElapsedTime(&b, E.ev[1], E.ev[2]));
+            E.sum_k1 += a;
+            E.sum_k2 += b;
+            E.n_timed++;
+        }
+        return WDB_OK;
+    };
     if (!use_graph) {
-        for (;;) {
-            WDB_TRY(E.enqueue(m));
+        for (int chunk = 1;; ++chunk) {
+            WDB_TRY(enqueue_chunk());
             WDB_CK(cudaMemcpyAsync(hs, E.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, st));
             WDB_CK(cudaStreamSynchronize(st));
+            WDB_TRY(harvest(chunk));
             if (hs->stop) break;
         }
         return WDB_OK;
     }
-    if (!E.graph_exec || E.graph_m != m) {
+    if (!E.graph_exec || E.graph_m != m || E.graph_timed != timed) {
         if (E.graph_exec) {
             cudaGraphExecDestroy(E.graph_exec);
             E.graph_exec = nullptr;
         }
         cudaGraph_t g = nullptr;
         WDB_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        wdb_status s = E.enqueue(m);
+        wdb_status s = enqueue_chunk();
         cudaError_t ce = cudaMemcpyAsync(hs, E.d_state, sizeof(SolveState), cudaMemcpyDeviceToHost, st);
         cudaError_t ee = cudaStreamEndCapture(st, &g);
         if (s != WDB_OK) {
@@ -125,15 +150,25 @@ static wdb_status run_loop(IterEngine& E, int m, bool use_graph, long long kerne
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) return cuda_error(ce, "cudaGraphInstantiate", __FILE__, __LINE__);
         E.graph_m = m;
+        E.graph_timed = timed;
         E.graph_kernels = kernels_per_chunk;
         count_launch(-kernels_per_chunk);   // captured, not launched
     }
-    for (;;) {
+    for (int chunk = 1;; ++chunk) {
         WDB_CK(cudaGraphLaunch(E.graph_exec, st));
         count_launch(E.graph_kernels);
         WDB_CK(cudaStreamSynchronize(st));
+        WDB_TRY(harvest(chunk));
         if (hs->stop) break;
     }
+    return WDB_OK;
+}
+
+static wdb_status record_ev(cudaEvent_t ev, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    WDB_CK(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusActive) WDB_CK(cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal));
+    else WDB_CK(cudaEventRecord(ev, st));
     return WDB_OK;
 }
 
@@ -155,6 +190,11 @@ wdb_status work_exit(cudaStream_t work, cudaEvent_t ev_out, cudaStream_t caller)
 void IterEngine::release() {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
     graph_exec = nullptr;
+    for (auto& e : ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -234,7 +274,15 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
         }
         return WDB_OK;
     };
-    WDB_TRY(run_loop(E, m, !p->no_graph, 2LL * m, st));
+    E.enqueue_timed = [=](cudaEvent_t* ev) -> wdb_status {
+        WDB_TRY(record_ev(ev[0], st));
+        WDB_TRY(launch_k1(F, th->grid, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st));
+        WDB_TRY(record_ev(ev[1], st));
+        WDB_TRY(launch_k2(A, th->grid, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st));
+        WDB_TRY(record_ev(ev[2], st));
+        return WDB_OK;
+    };
+    WDB_TRY(run_loop(E, m, !p->no_graph, p->time_kernels != 0, 2LL * m, st));
     SolveState hs = *th->h_state;
     double Eobj = 0.0;
     long long sup = 0;
@@ -250,6 +298,10 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     res->support = sup;
     res->tau = pc.tau;
     res->L_hat = pc.L_hat;
+    res->ms_k1 = E.n_timed ? E.sum_k1 / E.n_timed : 0.0;
+    res->ms_k2 = E.n_timed ? E.sum_k2 / E.n_timed : 0.0;
+    res->timed_chunks = E.n_timed;
+    res->first_primal_below = hs.hit_k;
     res->status = WDB_OK;
     if (hs.nan_flag || !std::isfinite(Eobj)) res->status = set_error(WDB_ENAN, "NaN/Inf in the objective");
     res->solve_ms = now_ms() - t0;
@@ -602,7 +654,22 @@ wdb_status fft_solve(wdb_fftop* op, const float* u, float* x_out, const wdb_solv
         }
         return WDB_OK;
     };
-    WDB_TRY(run_loop(E, m, !p->no_graph, (long long)m * (2 * L.J + 2), st));
+    E.enqueue_timed = [=](cudaEvent_t* ev) -> wdb_status {
+        WDB_TRY(record_ev(ev[0], st));
+        WDB_TRY(idwt2<float>(op->d_y, op->d_z, L, op->filt, op->d_scr, st));
+        WDB_CKF(cufftExecR2C(op->r2c, op->d_z, op->d_Z));
+        spectral_kernel<<<sgrid, 256, 0, st>>>(op->d_Z, op->d_hhat, op->d_uhat, C2, L.n_cols, NC, invN, 1,
+                                               op->d_part, &op->d_state->done[0], op->d_state, nullptr);
+        WDB_CK(cudaGetLastError());
+        WDB_CKF(cufftExecC2R(op->c2r, op->d_Z, op->d_z));
+        count_launch(1);
+        WDB_TRY(dwt2<float>(op->d_z, op->d_g, L, op->filt, op->d_scr, st));
+        WDB_TRY(record_ev(ev[1], st));
+        WDB_TRY(launch_fft_step(A, op->grid, op->d_g, op->d_y, op->d_xs, step, op->d_w, op->d_part, op->d_state, st));
+        WDB_TRY(record_ev(ev[2], st));
+        return WDB_OK;
+    };
+    WDB_TRY(run_loop(E, m, !p->no_graph, p->time_kernels != 0, (long long)m * (2 * L.J + 2), st));
     SolveState hs = *op->h_state;
     double Eobj = 0.0;
     long long sup = 0;
@@ -618,6 +685,10 @@ wdb_status fft_solve(wdb_fftop* op, const float* u, float* x_out, const wdb_solv
     res->support = sup;
     res->tau = pc.tau;
     res->L_hat = pc.L_hat;
+    res->ms_k1 = E.n_timed ? E.sum_k1 / E.n_timed : 0.0;
+    res->ms_k2 = E.n_timed ? E.sum_k2 / E.n_timed : 0.0;
+    res->timed_chunks = E.n_timed;
+    res->first_primal_below = hs.hit_k;
     res->status = WDB_OK;
     if (hs.nan_flag || !std::isfinite(Eobj)) res->status = set_error(WDB_ENAN, "NaN/Inf in the objective");
     res->solve_ms = now_ms() - t0;

@@ -182,6 +182,10 @@ __device__ void finish_iteration(SolveState* st, double wy, double gmax) {
         st->gap_k = k;
         if (st->tol > 0.0 && (k % st->check_every) == 0 && st->rel_gap <= st->tol) st->stop = 1;
     }
+    if (st->target > 0.0 && primal <= st->target) {
+        if (st->hit_k == 0) st->hit_k = k;
+        st->stop = 1;
+    }
     st->iters_done = k;
     if (k >= st->max_iters) st->stop = 1;
     st->k = k + 1;

@@ -109,6 +109,9 @@ struct SolveState {
     int nan_flag;
     int pad;
     double first_primal;
+    double target;          // > 0: stop once primal(y^(k)) <= target
+    int hit_k;              // first k with primal <= target
+    int pad2;
     double scratch[8];      // free slots for one-off reductions
 };
 
@@ -189,6 +192,13 @@ wdb_status work_exit(cudaStream_t work, cudaEvent_t ev_out, cudaStream_t caller)
 // Replays chunks of iterations (as a CUDA graph when enabled) until the device state stops.
 struct IterEngine {
     std::function<wdb_status(int)> enqueue;   // puts `iters` iterations on the stream
+    // puts one iteration on the stream with ev[0] before, ev[1] between the residual and
+    // the step part, ev[2] after (event record nodes when captured)
+    std::function<wdb_status(cudaEvent_t*)> enqueue_timed;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    bool graph_timed = false;
+    double sum_k1 = 0.0, sum_k2 = 0.0;
+    int n_timed = 0;
     cudaGraphExec_t graph_exec = nullptr;
     int graph_m = 0;
     long long graph_kernels = 0;

@@ -40,13 +40,15 @@ class ThetaInfo(C.Structure):
 class SolveParams(C.Structure):
     _fields_ = [("lam", C.c_double), ("w_subband_host", C.POINTER(C.c_double)), ("max_iters", C.c_int),
                 ("tol", C.c_double), ("precond", C.c_int), ("jacobi_eps", C.c_double),
-                ("check_every", C.c_int), ("x_init_dev", C.c_void_p), ("no_graph", C.c_int)]
+                ("check_every", C.c_int), ("x_init_dev", C.c_void_p), ("no_graph", C.c_int),
+                ("target_objective", C.c_double), ("time_kernels", C.c_int)]
 
 
 class SolveResult(C.Structure):
     _fields_ = [("iters", C.c_int), ("objective", C.c_double), ("primal", C.c_double), ("gap", C.c_double),
                 ("rel_gap", C.c_double), ("support", C.c_longlong), ("tau", C.c_double),
-                ("L_hat", C.c_double), ("solve_ms", C.c_double), ("status", C.c_int)]
+                ("L_hat", C.c_double), ("solve_ms", C.c_double), ("ms_k1", C.c_double), ("ms_k2", C.c_double),
+                ("timed_chunks", C.c_int), ("first_primal_below", C.c_int), ("status", C.c_int)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -150,7 +152,7 @@ def wavelet_filters(name: str = "db4"):
 
 
 def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0, check_every=10, x_init=None,
-                w_subband=None, no_graph=False):
+                w_subband=None, no_graph=False, target_objective=0.0, time_kernels=False):
     p = SolveParams()
     p.lam = float(lam)
     keep = None
@@ -164,6 +166,8 @@ def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0
     p.check_every = int(check_every)
     p.x_init_dev = None if x_init is None else _dev(x_init).value
     p.no_graph = 1 if no_graph else 0
+    p.target_objective = float(target_objective)
+    p.time_kernels = 1 if time_kernels else 0
     return p, keep
 
 
