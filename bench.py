@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--profile", action="store_true",
+                    help="short run for ncu: build Theta_K and the FFT operator, 30 iterations of each path")
     return ap.parse_args()
 
 
@@ -252,15 +254,23 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MiB > L2
 
     # E* of each path: long untimed runs of the same path
-    r_star = th.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND)
-    f_star = fop.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND)
+    if args.profile:
+        th.solve(u_dev, x_dev, lam=LAM, max_iters=30, precond=PRECOND)
+        fop.solve(u_dev, x_dev, lam=LAM, max_iters=30, precond=PRECOND)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "n_taps": th.info.n_taps}))
+        return 0
+    r_star = th.solve(u_dev, x_dev, lam=LAM, max_iters=3000, precond=PRECOND)
+    f_star = fop.solve(u_dev, x_dev, lam=LAM, max_iters=3000, precond=PRECOND)
     E_theta, E_fft = r_star["objective"], f_star["objective"]
     tgt_theta, tgt_fft = E_theta * (1 + REL_GAP), E_fft * (1 + REL_GAP)
 
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-    def timed(solve_fn, steps, e2e=False):
+    def timed(solve_fn, steps, e2e=False, tag=None):
         ms, res = [], []
+        if tag:
+            torch.cuda.nvtx.range_push(tag)
         if e2e:
             u_host = torch.from_numpy(prob.u0.astype(np.float32).ravel()).pin_memory()
             x_host = torch.empty(N, dtype=torch.float32).pin_memory()
@@ -277,6 +287,8 @@ def run_ours(args):
             end.synchronize()
             ms.append(start.elapsed_time(end))
             res.append(r)
+        if tag:
+            torch.cuda.nvtx.range_pop()
         return ms, res
 
     theta_solve = lambda: th.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND,  # noqa: E731
@@ -289,9 +301,9 @@ def run_ours(args):
     clocks.start()
     wdb.kernel_launches(reset=True)
     d.barrier(torch)
-    t_ms, t_res = timed(theta_solve, args.steps)
+    t_ms, t_res = timed(theta_solve, args.steps, tag="timed_theta")
     launches = wdb.kernel_launches()
-    f_ms, f_res = timed(fft_solve, args.steps)
+    f_ms, f_res = timed(fft_solve, args.steps, tag="timed_fft")
     clk = clocks.stop()
     e_ms, _ = timed(theta_solve, args.steps, e2e=True)
 

@@ -284,8 +284,8 @@ void wdb_theta_free(wdb_theta* th) { theta_release(th); }
 
 wdb_status wdb_theta_apply(const wdb_theta* th, const float* in_dev, float* out_dev, int transpose, void* stream) {
     if (!th || !in_dev || !out_dev) return set_error(WDB_EINVAL, "NULL argument");
-    StencilArgs A = stencil_args(th, transpose != 0);
-    return launch_apply<float>(A, th->grid, in_dev, out_dev, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+    return tile_apply<float>(tile_args(th, transpose != 0, false), in_dev, out_dev, nullptr, nullptr, th->d_red_part,
+                             static_cast<cudaStream_t>(stream));
 }
 
 wdb_status wdb_solve(wdb_theta* th, const float* u_dev, float* x_dev, const wdb_solve_params* params, void* stream,

@@ -88,4 +88,40 @@ __device__ __forceinline__ int phase_class(const SubbandDev& so, int py, int px)
     return so.tab_off + ((py & m) << so.lgR) + (px & m);
 }
 
+// ---------------------------------------------------------------------------------------
+// Gap bookkeeping shared by the Theta_K and FFT paths (runs in one thread of the last CTA).
+//   primal = 1/2 rr + wy; s = min(1, 1/max_i |g_i|/w_i); dual = -s x0r - s^2/2 rr
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void finish_iteration(SolveState* st, double wy, double gmax) {
+    const int k = st->k;
+    const double rr = st->rr, x0r = st->x0r;
+    const double primal = 0.5 * rr + wy;
+    const double s = gmax > 0.0 ? fmin(1.0, 1.0 / gmax) : 1.0;
+    const double dual = -s * x0r - 0.5 * s * s * rr;
+    const double gap = primal - dual;
+    st->wy = wy;
+    st->gmax = gmax;
+    if (k == 1) st->first_primal = primal;
+    if (!isfinite(primal) || !isfinite(gap)) {
+        st->nan_flag = 1;
+        st->stop = 1;
+    }
+    const bool check = (k % st->check_every) == 0 || k >= st->max_iters;
+    if (check) {
+        st->primal = primal;
+        st->dual = dual;
+        st->gap = gap;
+        st->rel_gap = primal > 0.0 ? gap / primal : 0.0;
+        st->gap_k = k;
+        if (st->tol > 0.0 && (k % st->check_every) == 0 && st->rel_gap <= st->tol) st->stop = 1;
+    }
+    if (st->target > 0.0 && primal <= st->target) {
+        if (st->hit_k == 0) st->hit_k = k;
+        st->stop = 1;
+    }
+    st->iters_done = k;
+    if (k >= st->max_iters) st->stop = 1;
+    st->k = k + 1;
+}
+
 }  // namespace wdb

@@ -211,7 +211,7 @@ wdb_status theta_workspace_public(wdb_theta* th, cudaStream_t st) {
     WDB_TRY(th_alloc(th, &th->d_xs, N));
     WDB_TRY(th_alloc(th, &th->d_scr, N / 2 + 1));
     WDB_TRY(th_alloc(th, &th->d_w, th->lay.S));
-    WDB_TRY(th_alloc(th, &th->d_part, (size_t)th->grid * 4));
+    WDB_TRY(th_alloc(th, &th->d_part, (size_t)th->part_len * 4));
     void* p = nullptr;
     WDB_CK(cudaMalloc(&p, sizeof(SolveState)));
     th->allocs.push_back(p);
@@ -226,7 +226,7 @@ wdb_status theta_objective_dev(wdb_theta* th, const float* x, const float* x0, c
                                double* E, long long* support) {
     StencilArgs F = stencil_args(th, false);
     double* d_out = reinterpret_cast<double*>(&th->d_state->scratch[0]);
-    WDB_TRY(launch_residual_norm(F, th->grid, x, x0, th->d_r, th_red(th, d_out), st));
+    WDB_TRY(tile_resnorm(tile_args(th, false, false), x, x0, th->d_r, d_out, th->d_red_part, st));
     WDB_TRY(launch_l1_terms(F, th->grid, x, w_dev, th_red(th, d_out + 1), st));
     double h[3];
     WDB_CK(cudaMemcpyAsync(h, d_out, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
@@ -262,23 +262,23 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     }
     SolveState s0 = init_state(p, m);
     WDB_CK(cudaMemcpyAsync(th->d_state, &s0, sizeof s0, cudaMemcpyHostToDevice, st));
-    StencilArgs F = stencil_args(th, false), A = stencil_args(th, true);
+    const TileArgs F = tile_args(th, false, false), A = tile_args(th, true, false);
     IterEngine& E = th->engine[p->precond];
     E.d_state = th->d_state;
     E.h_state = th->h_state;
     const float* step = pc.d_step;
     E.enqueue = [=](int iters) -> wdb_status {
         for (int i = 0; i < iters; ++i) {
-            WDB_TRY(launch_k1(F, th->grid, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st));
-            WDB_TRY(launch_k2(A, th->grid, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st));
+            WDB_TRY(tile_k1(F, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st));
+            WDB_TRY(tile_k2(A, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st));
         }
         return WDB_OK;
     };
     E.enqueue_timed = [=](cudaEvent_t* ev) -> wdb_status {
         WDB_TRY(record_ev(ev[0], st));
-        WDB_TRY(launch_k1(F, th->grid, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st));
+        WDB_TRY(tile_k1(F, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st));
         WDB_TRY(record_ev(ev[1], st));
-        WDB_TRY(launch_k2(A, th->grid, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st));
+        WDB_TRY(tile_k2(A, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st));
         WDB_TRY(record_ev(ev[2], st));
         return WDB_OK;
     };

@@ -291,7 +291,36 @@ static void build_ops(wdb_theta* th) {
     }
     pack_op(L, F, th->fwd_h);
     pack_op(L, A, th->adj_h);
+    for (int op = 0; op < 2; ++op) {
+        const std::vector<PEntry>& src = op ? A : F;
+        std::vector<TileEntry> te(src.size());
+        for (size_t i = 0; i < src.size(); ++i)
+            te[i] = TileEntry{src[i].out, src[i].in, src[i].up, src[i].lg, src[i].phase, src[i].dy, src[i].dx, src[i].v};
+        th->tplan[op][0] = make_tile_plan(L, te, 4, kTileSmemBudget);
+        th->tplan[op][1] = make_tile_plan(L, te, 8, kTileSmemBudget);
+    }
 }
+
+static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a, cudaStream_t st) {
+    WDB_TRY(upload(th, h.pairs, const_cast<TilePair**>(&a.plan.pairs), st));
+    WDB_TRY(upload(th, h.subs, const_cast<TileSub**>(&a.plan.subs), st));
+    WDB_TRY(upload(th, h.items, const_cast<TileItem**>(&a.plan.items), st));
+    WDB_TRY(upload(th, h.tap_off, const_cast<int**>(&a.plan.tap_off), st));
+    WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&a.plan.tap_v), st));
+    WDB_TRY(upload(th, h.tap_v64, const_cast<double**>(&a.plan.tap_v64), st));
+    a.plan.n_items = (int)h.items.size();
+    a.plan.smem_bytes = h.smem_bytes;
+    a.sb = th->d_sb;
+    void* q = nullptr;
+    WDB_CK(cudaMalloc(&q, sizeof(TileQueue)));
+    th->allocs.push_back(q);
+    WDB_CK(cudaMemsetAsync(q, 0, sizeof(TileQueue), st));
+    a.queue = static_cast<TileQueue*>(q);
+    a.grid = std::max(1, std::min(a.plan.n_items, tile_grid(h.smem_bytes)));
+    return WDB_OK;
+}
+
+TileArgs tile_args(const wdb_theta* th, bool adj, bool fp64) { return th->targs[adj ? 1 : 0][fp64 ? 1 : 0]; }
 
 static wdb_status upload_op(wdb_theta* th, const OpHost& h, OpDev& d, cudaStream_t st) {
     WDB_TRY(upload(th, h.pair_start, const_cast<int**>(&d.pair_start), st));
@@ -338,7 +367,8 @@ static wdb_status diag_tables(wdb_theta* th, cudaStream_t st) {
     const long long P2 = 1LL << L.J;
     const long long Timg = P2 * ((4 * D + 1 + P2 - 1) / P2);
     const int ty = (int)std::max<long long>(1, L.n_rows / Timg), tx = (int)std::max<long long>(1, L.n_cols / Timg);
-    StencilArgs F = stencil_args(th, false), A = stencil_args(th, true);
+    const bool f64 = sizeof(T) == 8;
+    TileArgs F = tile_args(th, false, f64), A = tile_args(th, true, f64);
     wdb_status s = WDB_OK;
     for (int b = 0; b < L.S && s == WDB_OK; ++b) {
         const SubbandDev& sb = L.sb[b];
@@ -349,9 +379,8 @@ static wdb_status diag_tables(wdb_theta* th, cudaStream_t st) {
                 const int cls = sb.tab_off + py * R + px;
                 comb_kernel<T><<<(ty * tx + 255) / 256, 256, 0, st>>>(v, sb.off, sb.cols, py, px, step, ty, tx, (T)1);
                 count_launch();
-                RedTarget r1 = th_red(th, d_out + 2 * cls), r2 = th_red(th, d_out + 2 * cls + 1);
-                s = launch_apply<T>(F, th->grid, v, u, nullptr, &r1, st);
-                if (s == WDB_OK) s = launch_apply<T>(A, th->grid, u, w, nullptr, &r2, st);
+                s = tile_apply<T>(F, v, u, nullptr, d_out + 2 * cls, th->d_red_part, st);
+                if (s == WDB_OK) s = tile_apply<T>(A, u, w, nullptr, d_out + 2 * cls + 1, th->d_red_part, st);
                 comb_kernel<T><<<(ty * tx + 255) / 256, 256, 0, st>>>(v, sb.off, sb.cols, py, px, step, ty, tx, (T)0);
                 count_launch();
             }
@@ -394,7 +423,13 @@ wdb_status theta_finalize(wdb_theta* th, cudaStream_t st) {
     th->sched = make_schedule(L);
     WDB_TRY(upload(th, th->sched.vb_start, &th->d_vb_start, st));
     th->grid = std::max(1, std::min(th->sched.nvb, stencil_grid_limit()));
-    WDB_TRY(th_alloc(th, &th->d_red_part, (size_t)th->grid * 4));
+    th->part_len = th->grid;
+    for (int op = 0; op < 2; ++op)
+        for (int pr = 0; pr < 2; ++pr) {
+            WDB_TRY(upload_plan(th, th->tplan[op][pr], th->targs[op][pr], st));
+            th->part_len = std::max(th->part_len, th->targs[op][pr].grid);
+        }
+    WDB_TRY(th_alloc(th, &th->d_red_part, (size_t)th->part_len * 4));
     unsigned int* cnt = nullptr;
     WDB_CK(cudaMalloc(&cnt, sizeof(unsigned int) * 4));
     th->allocs.push_back(cnt);
@@ -582,7 +617,9 @@ static wdb_status power_iteration(wdb_theta* th, const std::vector<double>& P, c
     WDB_CK(cudaMalloc(&d_sc, sizeof(double) * sc.size()));
     WDB_CK(cudaMalloc(&d_out, sizeof(double)));
     WDB_CK(cudaMemcpyAsync(d_sc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
-    StencilArgs F = stencil_args(th, false), A = stencil_args(th, true);
+    StencilArgs F = stencil_args(th, false);
+    const bool f64 = sizeof(T) == 8;
+    TileArgs TF = tile_args(th, false, f64), TA = tile_args(th, true, f64);
     wdb_status s = WDB_OK;
     double lam = 0.0, h_out = 0.0;
     RedTarget red = th_red(th, d_out);
@@ -593,8 +630,8 @@ static wdb_status power_iteration(wdb_theta* th, const std::vector<double>& P, c
     if (s == WDB_OK) s = launch_scale_const<T>(v, v, N, 1.0 / std::sqrt(h_out), st);
     for (int it = 1; it <= kPowerIters && s == WDB_OK; ++it) {
         if ((s = launch_scale<T>(F, th->grid, v, t, d_sc, st))) break;
-        if ((s = launch_apply<T>(F, th->grid, t, u, nullptr, nullptr, st))) break;
-        if ((s = launch_apply<T>(A, th->grid, u, t, d_sc, &red, st))) break;
+        if ((s = tile_apply<T>(TF, t, u, nullptr, nullptr, th->d_red_part, st))) break;
+        if ((s = tile_apply<T>(TA, u, t, d_sc, d_out, th->d_red_part, st))) break;
         cudaMemcpyAsync(&h_out, d_out, sizeof(double), cudaMemcpyDeviceToHost, st);
         cudaError_t e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { s = cuda_error(e, "power iteration", __FILE__, __LINE__); break; }

@@ -12,8 +12,12 @@ constexpr int kPowerIters = 200;
 constexpr double kPowerRtol = 1e-12;
 constexpr double kStepMargin = 1.01;
 
+// shared-memory budget of one CTA of the tiled gather engine (bytes)
+constexpr int kTileSmemBudget = 48 * 1024;
+
 template <typename T>
 wdb_status th_alloc(wdb_theta* th, T** p, size_t n);
+TileArgs tile_args(const wdb_theta* th, bool adj, bool fp64);
 StencilArgs stencil_args(const wdb_theta* th, bool adj);
 RedTarget th_red(const wdb_theta* th, double* out);
 bool setup_fp64(const wdb_theta* th);

@@ -1,0 +1,525 @@
+// Tiled gather engine for Theta_K / Theta_K^T (see tile.cuh) and the fused FISTA kernels
+// built on it: kernel 1 (r = Theta_K y - x0 with FP64 totals of ||r||^2 and <x0, r>) and
+// kernel 2 (g = Theta_K^T r fused with the preconditioned step, soft threshold and momentum
+// of Algorithm 3, with FP64 totals of sum w|y| and max |g|/w).
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+#include "device_util.cuh"
+#include "tile.cuh"
+
+namespace wdb {
+
+// ---------------------------------------------------------------------------------------
+// Host: plan
+// ---------------------------------------------------------------------------------------
+namespace {
+
+struct PairBuild {
+    int out, in, up, lg;
+    int dy0 = 1 << 30, dy1 = -(1 << 30), dx0 = 1 << 30, dx1 = -(1 << 30);
+    std::vector<const TileEntry*> taps;
+};
+
+int next_pow2(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+struct Geometry {
+    int RR, RC, PR, PC;
+    long long bytes;
+};
+
+Geometry geometry(const PairBuild& p, int TS, int esize) {
+    Geometry g;
+    const int r = 1 << p.lg;
+    if (!p.up) {
+        g.RR = r * (TS - 1) + (p.dy1 - p.dy0) + 1;
+        g.RC = r * (TS - 1) + (p.dx1 - p.dx0) + 1;
+        g.PR = (g.RR + r - 1) / r;
+        g.PC = ((g.RC + r - 1) / r) | 1;
+        g.bytes = (long long)r * r * g.PR * g.PC * esize;
+    } else {
+        const int rows = std::max(1, TS >> p.lg);
+        g.RR = rows + (p.dy1 - p.dy0);
+        g.RC = rows + (p.dx1 - p.dx0);
+        g.PR = g.RR;
+        g.PC = g.RC | 1;
+        g.bytes = (long long)g.PR * g.PC * esize;
+    }
+    return g;
+}
+
+}  // namespace
+
+TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int budget) {
+    TilePlanHost plan;
+    std::map<std::pair<int, int>, PairBuild> pairs;
+    for (const TileEntry& e : entries) {
+        PairBuild& p = pairs[{e.out, e.in}];
+        p.out = e.out;
+        p.in = e.in;
+        p.up = e.up;
+        p.lg = e.lg;
+        p.dy0 = std::min(p.dy0, e.dy);
+        p.dy1 = std::max(p.dy1, e.dy);
+        p.dx0 = std::min(p.dx0, e.dx);
+        p.dx1 = std::max(p.dx1, e.dx);
+        p.taps.push_back(&e);
+    }
+    std::vector<std::vector<PairBuild*>> by_out(L.S);
+    for (auto& kv : pairs) by_out[kv.first.first].push_back(&kv.second);
+    plan.subs.resize(L.S);
+    int max_bytes = 0;
+    struct ItemCost {
+        TileItem it;
+        double cost;
+    };
+    std::vector<ItemCost> items;
+    for (int o = 0; o < L.S; ++o) {
+        const SubbandDev& so = L.sb[o];
+        // largest tile (<= 32, <= the subband) whose staged regions fit the budget
+        int TS = std::min(32, next_pow2(std::max(so.rows, so.cols)));
+        std::vector<bool> global(by_out[o].size(), false);
+        for (;; TS >>= 1) {
+            bool fits = true;
+            for (size_t k = 0; k < by_out[o].size(); ++k)
+                if (geometry(*by_out[o][k], TS, esize).bytes > budget) fits = false;
+            if (fits || TS == 1) break;
+        }
+        for (size_t k = 0; k < by_out[o].size(); ++k)
+            if (geometry(*by_out[o][k], TS, esize).bytes > budget) global[k] = true;
+        TileSub& sub = plan.subs[o];
+        sub.TS = TS;
+        sub.pair_begin = (int)plan.pairs.size();
+        double taps_per_out = 0.0, stage_per_tile = 0.0;
+        for (size_t k = 0; k < by_out[o].size(); ++k) {
+            const PairBuild& pb = *by_out[o][k];
+            const Geometry g = geometry(pb, TS, esize);
+            const int r = 1 << pb.lg, m = r - 1;
+            TilePair tp;
+            tp.in_sb = pb.in;
+            tp.lg = pb.lg;
+            tp.mode = pb.up ? (global[k] ? kUpGlobal : kUp) : (global[k] ? kDownGlobal : kDown);
+            tp.RR = g.RR;
+            tp.RC = g.RC;
+            tp.PR = g.PR;
+            tp.PC = g.PC;
+            tp.y0 = pb.dy0;
+            tp.x0 = pb.dx0;
+            tp.tap_begin = (int)plan.tap_off.size();
+            auto offset = [&](const TileEntry& e) -> int {
+                if (global[k]) return (e.dy << 16) | (e.dx & 0xffff);
+                if (!pb.up) {
+                    const int yy = e.dy - pb.dy0, xx = e.dx - pb.dx0;
+                    const int plane = ((yy & m) << pb.lg) + (xx & m);
+                    return plane * g.PR * g.PC + (yy >> pb.lg) * g.PC + (xx >> pb.lg);
+                }
+                return (e.dy - pb.dy0) * g.PC + (e.dx - pb.dx0);
+            };
+            if (!pb.up) {
+                tp.ntap = (int)pb.taps.size();
+                for (const TileEntry* e : pb.taps) {
+                    plan.tap_off.push_back(offset(*e));
+                    plan.tap_v.push_back((float)e->v);
+                    plan.tap_v64.push_back(e->v);
+                }
+            } else {
+                const int nph = r * r;
+                std::vector<std::vector<const TileEntry*>> ph(nph);
+                for (const TileEntry* e : pb.taps) ph[e->phase].push_back(e);
+                int mx = 0;
+                for (auto& v : ph) mx = std::max(mx, (int)v.size());
+                tp.ntap = mx;
+                for (int j = 0; j < mx; ++j)
+                    for (int q = 0; q < nph; ++q) {
+                        if (j < (int)ph[q].size()) {
+                            plan.tap_off.push_back(offset(*ph[q][j]));
+                            plan.tap_v.push_back((float)ph[q][j]->v);
+                            plan.tap_v64.push_back(ph[q][j]->v);
+                        } else {
+                            plan.tap_off.push_back(global[k] ? 0 : 0);
+                            plan.tap_v.push_back(0.f);
+                            plan.tap_v64.push_back(0.0);
+                        }
+                    }
+            }
+            if (!global[k]) max_bytes = std::max<long long>(max_bytes, g.bytes);
+            taps_per_out += tp.ntap;
+            stage_per_tile += global[k] ? 0.0 : (double)g.RR * g.RC;
+            plan.pairs.push_back(tp);
+        }
+        sub.pair_end = (int)plan.pairs.size();
+        sub.pad = 0;
+        const int ty = (so.rows + TS - 1) / TS, tx = (so.cols + TS - 1) / TS;
+        for (int a = 0; a < ty; ++a)
+            for (int b = 0; b < tx; ++b) {
+                const int vy = std::min(TS, so.rows - a * TS), vx = std::min(TS, so.cols - b * TS);
+                const double outs = (double)vy * vx;
+                // MACs per thread-slot plus staging; small tiles leave threads in groups
+                const double cost = outs * taps_per_out + 2.0 * stage_per_tile + 256.0;
+                plan.macs += (long long)(outs * taps_per_out);
+                items.push_back({TileItem{o, a * TS, b * TS, 0}, cost});
+            }
+    }
+    std::stable_sort(items.begin(), items.end(), [](const ItemCost& x, const ItemCost& y) { return x.cost > y.cost; });
+    for (auto& ic : items) plan.items.push_back(ic.it);
+    plan.smem_bytes = std::max(max_bytes, 16);
+    return plan;
+}
+
+// ---------------------------------------------------------------------------------------
+// Device
+// ---------------------------------------------------------------------------------------
+namespace {
+
+enum Epi { kApply = 0, kApplyNorm = 1, kK1 = 2, kK2 = 3, kResNorm = 4 };
+
+struct EpiArgs {
+    const float* x0;          // kK1, kResNorm
+    float* y;                 // kK2 (in place)
+    float* x;                 // kK2 (in place)
+    const float* step_tab;    // kK2: tau / P per phase class
+    const float* w_sb;        // kK2: weights per subband
+    const double* scale;      // kApply*: optional factor per phase class
+    double* part;             // per-CTA partials
+    SolveState* st;           // kK1, kK2
+    double* red_out;          // kApplyNorm, kResNorm
+};
+
+template <typename T>
+__device__ __forceinline__ const T* tvals(const TilePlanDev& p);
+template <>
+__device__ __forceinline__ const float* tvals<float>(const TilePlanDev& p) { return p.tap_v; }
+template <>
+__device__ __forceinline__ const double* tvals<double>(const TilePlanDev& p) { return p.tap_v64; }
+
+__device__ __forceinline__ int wrap1(int v, int n) {
+    v += (v < 0) ? n : 0;
+    return v - ((v >= n) ? n : 0);
+}
+
+__device__ __forceinline__ int pos_mod(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ float gw_ratio(float g, float w) {
+    const float ag = fabsf(g);
+    return w > 0.f ? ag / w : (ag > 0.f ? FLT_MAX : 0.f);
+}
+
+template <typename T, int EPI>
+__global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T* __restrict__ in,
+                                                            T* __restrict__ out, EpiArgs ep) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    __shared__ T red_buf[kTileThreads];
+    __shared__ int s_item;
+    if (EPI == kK1 || EPI == kK2) {
+        if (*(volatile int*)&ep.st->stop) return;
+    }
+    const TilePlanDev& plan = A.plan;
+    const T* __restrict__ vals = tvals<T>(plan);
+    const int t = threadIdx.x;
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, mx = 0.f;
+    double d0 = 0.0;
+    float beta = 0.f;
+    if (EPI == kK2) {
+        const int k = ep.st->k;
+        beta = (float)(k - 1) / (float)(k + 2);
+    }
+    for (;;) {
+        if (t == 0) s_item = (int)atomicAdd(&A.queue->next, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= plan.n_items) break;
+        const TileItem w = plan.items[it];
+        const TileSub sub = plan.subs[w.o];
+        const SubbandDev so = A.sb[w.o];
+        const int TS = sub.TS;
+        const int nout = TS * TS;
+        int E, G, g;
+        int ly[4], lx[4];
+        if (TS == 32) {
+            E = 4;
+            G = 1;
+            g = 0;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                lx[e] = t & 31;
+                ly[e] = (t >> 5) + 8 * e;
+            }
+        } else {
+            E = 1;
+            G = kTileThreads / nout;
+            g = t / nout;
+            const int oi = t - g * nout;
+            lx[0] = oi % TS;
+            ly[0] = oi / TS;
+#pragma unroll
+            for (int e = 1; e < 4; ++e) {
+                lx[e] = lx[0];
+                ly[e] = ly[0];
+            }
+        }
+        T acc[4] = {0, 0, 0, 0};
+        for (int pi = sub.pair_begin; pi < sub.pair_end; ++pi) {
+            const TilePair P = plan.pairs[pi];
+            const SubbandDev si = A.sb[P.in_sb];
+            const T* __restrict__ src = in + si.off;
+            const int lg = P.lg, r = 1 << lg, m = r - 1;
+            if (P.mode == kDown || P.mode == kUp) {
+                const int Y0 = (P.mode == kDown) ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
+                const int X0 = (P.mode == kDown) ? ((w.tx0 << lg) + P.x0) : ((w.tx0 >> lg) + P.x0);
+                const int yb = pos_mod(Y0, si.rows), xb = pos_mod(X0, si.cols);
+                const int n = P.RR * P.RC;
+                const int plane = P.PR * P.PC;
+                for (int q = t; q < n; q += kTileThreads) {
+                    const int yr = q / P.RC, xr = q - yr * P.RC;
+                    int gy = yb + yr, gx = xb + xr;
+                    if (gy >= si.rows) gy %= si.rows;
+                    if (gx >= si.cols) gx %= si.cols;
+                    const T v = src[(size_t)gy * si.cols + gx];
+                    const int idx = (P.mode == kDown)
+                                        ? ((((yr & m) << lg) + (xr & m)) * plane + (yr >> lg) * P.PC + (xr >> lg))
+                                        : (yr * P.PC + xr);
+                    S[idx] = v;
+                }
+                __syncthreads();
+                if (P.mode == kDown) {
+                    int base[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) base[e] = ly[e] * P.PC + lx[e];
+                    const int tb = P.tap_begin;
+                    int j = g;
+                    for (; j + 3 * G < P.ntap; j += 4 * G) {
+                        const int o0 = __ldg(plan.tap_off + tb + j), o1 = __ldg(plan.tap_off + tb + j + G);
+                        const int o2 = __ldg(plan.tap_off + tb + j + 2 * G), o3 = __ldg(plan.tap_off + tb + j + 3 * G);
+                        const T v0 = __ldg(vals + tb + j), v1 = __ldg(vals + tb + j + G);
+                        const T v2 = __ldg(vals + tb + j + 2 * G), v3 = __ldg(vals + tb + j + 3 * G);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            if (e < E) {
+                                acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
+                                acc[e] += v2 * S[o2 + base[e]] + v3 * S[o3 + base[e]];
+                            }
+                        }
+                    }
+                    for (; j < P.ntap; j += G) {
+                        const int o0 = __ldg(plan.tap_off + tb + j);
+                        const T v0 = __ldg(vals + tb + j);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (e < E) acc[e] += v0 * S[o0 + base[e]];
+                    }
+                } else {
+                    const int rr = r * r;
+                    const int py0 = w.ty0 >> lg, px0 = w.tx0 >> lg;
+                    int base[4], ph[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int yy = w.ty0 + ly[e], xx = w.tx0 + lx[e];
+                        base[e] = ((yy >> lg) - py0) * P.PC + ((xx >> lg) - px0);
+                        ph[e] = ((yy & m) << lg) + (xx & m);
+                    }
+                    const int tb = P.tap_begin;
+                    if (E == 1 || r <= 8) {
+                        const int* __restrict__ to = plan.tap_off + tb + ph[0];
+                        const T* __restrict__ tv = vals + tb + ph[0];
+                        int j = g;
+                        for (; j + G < P.ntap; j += 2 * G) {
+                            const int o0 = __ldg(to + j * rr), o1 = __ldg(to + (j + G) * rr);
+                            const T v0 = __ldg(tv + j * rr), v1 = __ldg(tv + (j + G) * rr);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (e < E) acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
+                        }
+                        for (; j < P.ntap; j += G) {
+                            const int o0 = __ldg(to + j * rr);
+                            const T v0 = __ldg(tv + j * rr);
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (e < E) acc[e] += v0 * S[o0 + base[e]];
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int* __restrict__ to = plan.tap_off + tb + ph[e];
+                            const T* __restrict__ tv = vals + tb + ph[e];
+                            for (int j = g; j < P.ntap; j += G) acc[e] += __ldg(tv + j * rr) * S[__ldg(to + j * rr) + base[e]];
+                        }
+                    }
+                }
+                __syncthreads();
+            } else {
+                // gather from global memory (regions larger than the shared-memory budget)
+                const int R = si.rows, C = si.cols;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (e >= E) continue;
+                    const int py = w.ty0 + ly[e], px = w.tx0 + lx[e];
+                    if (py >= so.rows || px >= so.cols) continue;
+                    int by, bx, tb, step;
+                    if (P.mode == kDownGlobal) {
+                        by = py << lg;
+                        bx = px << lg;
+                        tb = P.tap_begin;
+                        step = 1;
+                    } else {
+                        by = py >> lg;
+                        bx = px >> lg;
+                        tb = P.tap_begin + (((py & m) << lg) + (px & m));
+                        step = r * r;
+                    }
+                    T a = 0;
+                    for (int j = g; j < P.ntap; j += G) {
+                        const int pk = __ldg(plan.tap_off + tb + j * step);
+                        const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
+                        a += __ldg(vals + tb + j * step) * src[(size_t)yy * C + xx];
+                    }
+                    acc[e] += a;
+                }
+            }
+        }
+        if (G > 1) {
+            red_buf[t] = acc[0];
+            __syncthreads();
+            if (g == 0)
+                for (int k = 1; k < G; ++k) acc[0] += red_buf[t + k * nout];
+        }
+        if (g == 0) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (e >= E) continue;
+                const int py = w.ty0 + ly[e], px = w.tx0 + lx[e];
+                if (py >= so.rows || px >= so.cols) continue;
+                const size_t i = so.off + (size_t)py * so.cols + px;
+                const int mR = (1 << so.lgR) - 1;
+                const int cls = so.tab_off + ((py & mR) << so.lgR) + (px & mR);
+                if (EPI == kApply || EPI == kApplyNorm) {
+                    T v = acc[e];
+                    if (ep.scale) v = (T)((double)v * ep.scale[cls]);
+                    out[i] = v;
+                    if (EPI == kApplyNorm) {
+                        if (sizeof(T) == 8) d0 += (double)v * (double)v;
+                        else neu_add(s0, c0, (float)v * (float)v);
+                    }
+                } else if (EPI == kK1 || EPI == kResNorm) {
+                    const float xv = ep.x0[i];
+                    const float rv = (float)acc[e] - xv;
+                    out[i] = (T)rv;
+                    neu_add(s0, c0, rv * rv);
+                    if (EPI == kK1) neu_add(s1, c1, xv * rv);
+                } else if (EPI == kK2) {
+                    const float gv = (float)acc[e];
+                    const float stp = ep.step_tab[cls];
+                    const float wv = ep.w_sb[w.o];
+                    const float yv = ep.y[i], xo = ep.x[i];
+                    const float z = yv - stp * gv;
+                    const float xn = copysignf(fmaxf(fabsf(z) - stp * wv, 0.f), z);
+                    ep.x[i] = xn;
+                    ep.y[i] = xn + beta * (xn - xo);
+                    neu_add(s0, c0, wv * fabsf(yv));
+                    mx = fmaxf(mx, gw_ratio(gv, wv));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    // totals (and, in the last CTA, the queue reset)
+    double v[2] = {d0 + (double)s0 + (double)c0, EPI == kK2 ? (double)mx : (double)s1 + (double)c1}, tot[2];
+    const unsigned maxmask = (EPI == kK2) ? 2u : 0u;
+    if (grid_reduce<2>(v, maxmask, ep.part, &A.queue->done, tot)) {
+        if (t == 0) {
+            A.queue->next = 0u;
+            if (EPI == kK1) {
+                ep.st->rr = tot[0];
+                ep.st->x0r = tot[1];
+            } else if (EPI == kK2) {
+                finish_iteration(ep.st, tot[0], tot[1]);
+            } else if (EPI == kApplyNorm || EPI == kResNorm) {
+                ep.red_out[0] = tot[0];
+            }
+        }
+    }
+}
+
+template <typename T, int EPI>
+wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    tile_kernel<T, EPI><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
+}  // namespace
+
+int tile_grid(int smem_bytes) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(tile_kernel<float, kK2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2>, kTileThreads, smem_bytes);
+    if (sms <= 0) sms = 1;
+    if (per <= 0) per = 1;
+    return sms * per;
+}
+
+template <typename T>
+wdb_status tile_apply(const TileArgs& A, const T* in, T* out, const double* scale, double* norm_out, double* part,
+                      cudaStream_t st) {
+    EpiArgs ep{};
+    ep.scale = scale;
+    ep.part = part;
+    ep.red_out = norm_out;
+    if (norm_out) return launch_tile<T, kApplyNorm>(A, in, out, ep, st);
+    return launch_tile<T, kApply>(A, in, out, ep, st);
+}
+
+wdb_status tile_k1(const TileArgs& A, const float* y, const float* x0, float* r, double* part, SolveState* s,
+                   cudaStream_t st) {
+    EpiArgs ep{};
+    ep.x0 = x0;
+    ep.part = part;
+    ep.st = s;
+    return launch_tile<float, kK1>(A, y, r, ep, st);
+}
+
+wdb_status tile_k2(const TileArgs& A, const float* r, float* y, float* x, const float* step_tab, const float* w_sb,
+                   double* part, SolveState* s, cudaStream_t st) {
+    EpiArgs ep{};
+    ep.y = y;
+    ep.x = x;
+    ep.step_tab = step_tab;
+    ep.w_sb = w_sb;
+    ep.part = part;
+    ep.st = s;
+    return launch_tile<float, kK2>(A, r, nullptr, ep, st);
+}
+
+wdb_status tile_resnorm(const TileArgs& A, const float* x, const float* x0, float* r, double* out, double* part,
+                        cudaStream_t st) {
+    EpiArgs ep{};
+    ep.x0 = x0;
+    ep.part = part;
+    ep.red_out = out;
+    return launch_tile<float, kResNorm>(A, x, r, ep, st);
+}
+
+template wdb_status tile_apply<float>(const TileArgs&, const float*, float*, const double*, double*, double*,
+                                      cudaStream_t);
+template wdb_status tile_apply<double>(const TileArgs&, const double*, double*, const double*, double*, double*,
+                                       cudaStream_t);
+
+}  // namespace wdb

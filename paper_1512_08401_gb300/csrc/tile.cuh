@@ -1,0 +1,99 @@
+// Tiled gather engine for Theta_K and Theta_K^T (the hot path of Algorithm 3).
+//
+// A work item is a TS x TS tile of one output subband. For every input subband that feeds
+// it, the CTA stages the input region of the tile (plus the tap halo) in shared memory,
+// with periodic wrap, and accumulates the taps from there:
+//   down pair (input finer or equal, r = 2^lg): out[p] += v_t in[r p + d_t]; the region is
+//     stored as r x r polyphase planes so that neighbouring outputs read neighbouring words;
+//   up pair (input coarser, r = 2^lg): out[r P + phi] += v_t in[P + d_t] over the taps of
+//     phase phi, padded to the same count for every phase;
+//   pairs whose region does not fit even for 1 x 1 tiles gather from global memory.
+// Tiles are processed heaviest first by persistent CTAs that pull items from a device queue.
+#pragma once
+#include <vector>
+
+#include "layout_types.h"
+
+namespace wdb {
+
+constexpr int kTileThreads = 256;
+
+enum TileMode { kDown = 0, kUp = 1, kDownGlobal = 2, kUpGlobal = 3 };
+
+struct TilePair {
+    int in_sb;
+    int mode;         // TileMode
+    int lg;           // log2 of the scale ratio r
+    int RR, RC;       // staged region rows / cols (input units for down, P units for up)
+    int PR, PC;       // plane rows / cols (down: ceil(RR / r), ceil(RC / r) padded; up: RR, RC padded)
+    int y0, x0;       // region origin: down Y0 = (ty0 << lg) + y0; up Y0 = (ty0 >> lg) + y0
+    int tap_begin;    // first tap (up: phase-interleaved, index tap_begin + j r^2 + phase)
+    int ntap;         // down: taps; up: padded taps per phase
+};
+
+struct TileSub {      // per output subband
+    int TS;           // tile side
+    int pair_begin, pair_end;
+    int pad;
+};
+
+struct TileItem {
+    int o;
+    int ty0, tx0;
+    int pad;
+};
+
+struct TilePlanDev {
+    const TilePair* pairs;
+    const TileSub* subs;
+    const TileItem* items;
+    const int* tap_off;       // staged: offset in shared memory; global: (dy << 16) | (dx & 0xffff)
+    const float* tap_v;
+    const double* tap_v64;
+    int n_items;
+    int smem_bytes;           // dynamic shared memory per CTA
+};
+
+struct TilePlanHost {
+    std::vector<TilePair> pairs;
+    std::vector<TileSub> subs;
+    std::vector<TileItem> items;
+    std::vector<int> tap_off;
+    std::vector<float> tap_v;
+    std::vector<double> tap_v64;
+    int smem_bytes = 0;
+    long long macs = 0;        // MACs per application (taps x outputs, padding included)
+};
+
+struct TileEntry {             // one tap of one pair, in gather form
+    int out, in, up, lg, phase, dy, dx;
+    double v;
+};
+
+// Build the plan of one operator for element size `esize` and a shared-memory budget.
+TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget);
+
+struct TileQueue {             // device counters of one operator launch
+    unsigned int next;         // next work item
+    unsigned int done;         // CTAs finished
+};
+
+struct TileArgs {
+    TilePlanDev plan;
+    const SubbandDev* sb;
+    TileQueue* queue;
+    int grid;
+};
+
+template <typename T>
+wdb_status tile_apply(const TileArgs& A, const T* in, T* out, const double* scale, double* norm_out,
+                      double* part, cudaStream_t st);
+wdb_status tile_k1(const TileArgs& A, const float* y, const float* x0, float* r, double* part, SolveState* s,
+                   cudaStream_t st);
+wdb_status tile_k2(const TileArgs& A, const float* r, float* y, float* x, const float* step_tab,
+                   const float* w_sb, double* part, SolveState* s, cudaStream_t st);
+wdb_status tile_resnorm(const TileArgs& A, const float* x, const float* x0, float* r, double* out, double* part,
+                        cudaStream_t st);
+int tile_grid(int smem_bytes);
+
+}  // namespace wdb

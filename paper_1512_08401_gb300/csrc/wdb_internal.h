@@ -9,52 +9,9 @@
 #include <vector>
 
 #include "../../include/wdb.h"
+#include "layout_types.h"
 
 namespace wdb {
-
-constexpr int kMaxS = WDB_MAX_SUBBANDS;
-constexpr int kMaxL = 20;  // db10
-
-// ---------------------------------------------------------------------------------------
-// Errors
-// ---------------------------------------------------------------------------------------
-wdb_status set_error(wdb_status s, const char* fmt, ...);
-wdb_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
-
-#define WDB_CK(call)                                                              \
-    do {                                                                          \
-        cudaError_t e_ = (call);                                                  \
-        if (e_ != cudaSuccess) return ::wdb::cuda_error(e_, #call, __FILE__, __LINE__); \
-    } while (0)
-
-#define WDB_TRY(call)                                \
-    do {                                             \
-        wdb_status s_ = (call);                      \
-        if (s_ != WDB_OK) return s_;                 \
-    } while (0)
-
-// Count of kernels launched by the library (graph replays add their node counts).
-void count_launch(long long n = 1);
-
-// ---------------------------------------------------------------------------------------
-// Subband layout (Sec. 2): subband-planar, A_J first, then (0,1),(1,0),(1,1) for s=J..1
-// ---------------------------------------------------------------------------------------
-struct SubbandDev {      // per subband, device-resident copy
-    long long off;       // start in the coefficient vector
-    int rows, cols;
-    int level;           // s (1 = finest)
-    int lgR;             // log2 of the phase period R = 2^{J - s}
-    int tab_off;         // start of this subband in the phase tables (4^J entries in all)
-    int pad;
-};
-
-struct Layout {
-    int n_rows = 0, n_cols = 0, J = 0, S = 0;
-    long long N = 0;
-    SubbandDev sb[kMaxS];
-    int tab_len = 0;     // sum_b R_b^2 = 4^J
-};
-wdb_status make_layout(int n_rows, int n_cols, int J, Layout* out);
 
 // ---------------------------------------------------------------------------------------
 // Daubechies filters (derived on the host by spectral factorisation)
@@ -90,30 +47,6 @@ wdb_status dwt2(const T* img, T* coef, const Layout& L, const Filters& f, T* scr
 template <typename T>
 wdb_status idwt2(const T* coef, T* img, const Layout& L, const Filters& f, T* scratch,
                  cudaStream_t st);
-
-// ---------------------------------------------------------------------------------------
-// Device reduction / solver state
-// ---------------------------------------------------------------------------------------
-struct SolveState {
-    int k;                  // 1-based iteration about to run / running
-    int stop;               // 1: done (converged, max_iters, or error)
-    int max_iters;
-    int check_every;
-    double tol;
-    unsigned int done[4];   // last-CTA counters
-    double rr, x0r;         // from the residual kernel of the current iteration
-    double wy, gmax;        // from the step kernel of the current iteration
-    double primal, dual, gap, rel_gap;  // certificate of the last check
-    int gap_k;              // iteration of the last check
-    int iters_done;         // k of the last computed x
-    int nan_flag;
-    int pad;
-    double first_primal;
-    double target;          // > 0: stop once primal(y^(k)) <= target
-    int hit_k;              // first k with primal <= target
-    int pad2;
-    double scratch[8];      // free slots for one-off reductions
-};
 
 // Reduction slots for one-off launches (power iteration, probes, objective).
 struct RedSlot {
@@ -210,6 +143,8 @@ struct IterEngine {
 
 }  // namespace wdb
 
+#include "tile.cuh"
+
 struct wdb_theta {
     wdb::Layout lay;
     wdb::Filters filt;
@@ -220,6 +155,9 @@ struct wdb_theta {
     std::vector<wdb::Tap> taps;            // sorted (a, b, oy, ox)
     wdb::OpHost fwd_h, adj_h;
     wdb::OpDev fwd{}, adj{};
+    wdb::TilePlanHost tplan[2][2];         // [0 Theta_K, 1 Theta_K^T][0 FP32, 1 FP64]
+    wdb::TileArgs targs[2][2];
+    int part_len = 0;                      // capacity (CTAs) of the per-CTA partial buffers
     std::vector<void*> allocs;             // device buffers owned by the handle
     wdb::SubbandDev* d_sb = nullptr;
     int* d_vb_start = nullptr;
