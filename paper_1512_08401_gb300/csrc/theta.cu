@@ -309,6 +309,7 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
     WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&a.plan.tap_v), st));
     WDB_TRY(upload(th, h.tap_v64, const_cast<double**>(&a.plan.tap_v64), st));
     a.plan.n_items = (int)h.items.size();
+    a.plan.buf_elems = h.buf_elems;
     a.plan.smem_bytes = h.smem_bytes;
     a.sb = th->d_sb;
     void* q = nullptr;

@@ -83,21 +83,34 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
     std::vector<ItemCost> items;
     for (int o = 0; o < L.S; ++o) {
         const SubbandDev& so = L.sb[o];
-        // largest tile (<= 32, <= the subband) whose staged regions fit the budget
+        // largest tile (<= 32, <= the subband) whose staged regions, all together, fit the
+        // buffer; pairs that do not fit even for 1 x 1 tiles (largest first) gather from
+        // global memory
+        const int np = (int)by_out[o].size();
+        std::vector<bool> global(np, false);
+        auto total = [&](int ts) {
+            long long sum = 0;
+            for (int k = 0; k < np; ++k)
+                if (!global[k]) sum += (geometry(*by_out[o][k], ts, esize).bytes + 15) / 16 * 16;
+            return sum;
+        };
         int TS = std::min(32, next_pow2(std::max(so.rows, so.cols)));
-        std::vector<bool> global(by_out[o].size(), false);
-        for (;; TS >>= 1) {
-            bool fits = true;
-            for (size_t k = 0; k < by_out[o].size(); ++k)
-                if (geometry(*by_out[o][k], TS, esize).bytes > budget) fits = false;
-            if (fits || TS == 1) break;
+        while (TS > 1 && total(TS) > budget) TS >>= 1;
+        while (total(TS) > budget) {
+            int worst = -1;
+            long long wb = -1;
+            for (int k = 0; k < np; ++k)
+                if (!global[k] && geometry(*by_out[o][k], TS, esize).bytes > wb) {
+                    wb = geometry(*by_out[o][k], TS, esize).bytes;
+                    worst = k;
+                }
+            global[worst] = true;
         }
-        for (size_t k = 0; k < by_out[o].size(); ++k)
-            if (geometry(*by_out[o][k], TS, esize).bytes > budget) global[k] = true;
         TileSub& sub = plan.subs[o];
         sub.TS = TS;
         sub.pair_begin = (int)plan.pairs.size();
         double taps_per_out = 0.0, stage_per_tile = 0.0;
+        int soff = 0;
         for (size_t k = 0; k < by_out[o].size(); ++k) {
             const PairBuild& pb = *by_out[o][k];
             const Geometry g = geometry(pb, TS, esize);
@@ -112,6 +125,8 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             tp.PC = g.PC;
             tp.y0 = pb.dy0;
             tp.x0 = pb.dx0;
+            tp.soff = soff;
+            if (!global[k]) soff += (int)((g.bytes + 15) / 16 * 16 / esize);
             tp.tap_begin = (int)plan.tap_off.size();
             auto offset = [&](const TileEntry& e) -> int {
                 if (global[k]) return (e.dy << 16) | (e.dx & 0xffff);
@@ -149,13 +164,13 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                         }
                     }
             }
-            if (!global[k]) max_bytes = std::max<long long>(max_bytes, g.bytes);
             taps_per_out += tp.ntap;
             stage_per_tile += global[k] ? 0.0 : (double)g.RR * g.RC;
             plan.pairs.push_back(tp);
         }
         sub.pair_end = (int)plan.pairs.size();
         sub.pad = 0;
+        max_bytes = std::max(max_bytes, soff * esize);
         const int ty = (so.rows + TS - 1) / TS, tx = (so.cols + TS - 1) / TS;
         for (int a = 0; a < ty; ++a)
             for (int b = 0; b < tx; ++b) {
@@ -169,7 +184,8 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
     }
     std::stable_sort(items.begin(), items.end(), [](const ItemCost& x, const ItemCost& y) { return x.cost > y.cost; });
     for (auto& ic : items) plan.items.push_back(ic.it);
-    plan.smem_bytes = std::max(max_bytes, 16);
+    plan.buf_elems = std::max(max_bytes, 16) / esize;
+    plan.smem_bytes = 2 * plan.buf_elems * esize;
     return plan;
 }
 
@@ -214,13 +230,53 @@ __device__ __forceinline__ float gw_ratio(float g, float w) {
     return w > 0.f ? ag / w : (ag > 0.f ? FLT_MAX : 0.f);
 }
 
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Issue the asynchronous copies of every staged region of item `it` into buffer S.
+template <typename T>
+__device__ __forceinline__ void stage_item(const TileArgs& A, const T* __restrict__ in, int it, T* S) {
+    const TilePlanDev& plan = A.plan;
+    const TileItem w = plan.items[it];
+    const TileSub sub = plan.subs[w.o];
+    for (int pi = sub.pair_begin; pi < sub.pair_end; ++pi) {
+        const TilePair P = plan.pairs[pi];
+        if (P.mode != kDown && P.mode != kUp) continue;
+        const SubbandDev si = A.sb[P.in_sb];
+        const T* __restrict__ src = in + si.off;
+        const int lg = P.lg, m = (1 << lg) - 1;
+        const int Y0 = (P.mode == kDown) ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
+        const int X0 = (P.mode == kDown) ? ((w.tx0 << lg) + P.x0) : ((w.tx0 >> lg) + P.x0);
+        const int yb = pos_mod(Y0, si.rows), xb = pos_mod(X0, si.cols);
+        const int n = P.RR * P.RC;
+        const int plane = P.PR * P.PC;
+        T* dst = S + P.soff;
+        for (int q = threadIdx.x; q < n; q += kTileThreads) {
+            const int yr = q / P.RC, xr = q - yr * P.RC;
+            int gy = yb + yr, gx = xb + xr;
+            if (gy >= si.rows) gy %= si.rows;
+            if (gx >= si.cols) gx %= si.cols;
+            const int idx = (P.mode == kDown) ? ((((yr & m) << lg) + (xr & m)) * plane + (yr >> lg) * P.PC + (xr >> lg))
+                                              : (yr * P.PC + xr);
+            cp_async(dst + idx, src + (size_t)gy * si.cols + gx, (int)sizeof(T));
+        }
+    }
+}
+
 template <typename T, int EPI>
 __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T* __restrict__ in,
                                                             T* __restrict__ out, EpiArgs ep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* S = reinterpret_cast<T*>(smem_raw);
+    T* const buf0 = reinterpret_cast<T*>(smem_raw);
+    T* const buf1 = buf0 + A.plan.buf_elems;
     __shared__ T red_buf[kTileThreads];
-    __shared__ int s_item;
+    __shared__ int s_next;
     if (EPI == kK1 || EPI == kK2) {
         if (*(volatile int*)&ep.st->stop) return;
     }
@@ -234,11 +290,24 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         const int k = ep.st->k;
         beta = (float)(k - 1) / (float)(k + 2);
     }
-    for (;;) {
-        if (t == 0) s_item = (int)atomicAdd(&A.queue->next, 1u);
+    // prologue: first item
+    if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
+    __syncthreads();
+    int it = s_next;
+    T* S = buf0;
+    T* Snext = buf1;
+    if (it < plan.n_items) stage_item<T>(A, in, it, S);
+    cp_async_commit();
+    while (it < plan.n_items) {
+        // fetch and stage the next item while this one computes
         __syncthreads();
-        const int it = s_item;
-        if (it >= plan.n_items) break;
+        if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
+        __syncthreads();
+        const int nx = s_next;
+        if (nx < plan.n_items) stage_item<T>(A, in, nx, Snext);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
         const TileItem w = plan.items[it];
         const TileSub sub = plan.subs[w.o];
         const SubbandDev so = A.sb[w.o];
@@ -271,94 +340,76 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         T acc[4] = {0, 0, 0, 0};
         for (int pi = sub.pair_begin; pi < sub.pair_end; ++pi) {
             const TilePair P = plan.pairs[pi];
-            const SubbandDev si = A.sb[P.in_sb];
-            const T* __restrict__ src = in + si.off;
             const int lg = P.lg, r = 1 << lg, m = r - 1;
-            if (P.mode == kDown || P.mode == kUp) {
-                const int Y0 = (P.mode == kDown) ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
-                const int X0 = (P.mode == kDown) ? ((w.tx0 << lg) + P.x0) : ((w.tx0 >> lg) + P.x0);
-                const int yb = pos_mod(Y0, si.rows), xb = pos_mod(X0, si.cols);
-                const int n = P.RR * P.RC;
-                const int plane = P.PR * P.PC;
-                for (int q = t; q < n; q += kTileThreads) {
-                    const int yr = q / P.RC, xr = q - yr * P.RC;
-                    int gy = yb + yr, gx = xb + xr;
-                    if (gy >= si.rows) gy %= si.rows;
-                    if (gx >= si.cols) gx %= si.cols;
-                    const T v = src[(size_t)gy * si.cols + gx];
-                    const int idx = (P.mode == kDown)
-                                        ? ((((yr & m) << lg) + (xr & m)) * plane + (yr >> lg) * P.PC + (xr >> lg))
-                                        : (yr * P.PC + xr);
-                    S[idx] = v;
-                }
-                __syncthreads();
-                if (P.mode == kDown) {
-                    int base[4];
+            if (P.mode == kDown) {
+                const T* __restrict__ Sp = S + P.soff;
+                int base[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) base[e] = ly[e] * P.PC + lx[e];
-                    const int tb = P.tap_begin;
-                    int j = g;
-                    for (; j + 3 * G < P.ntap; j += 4 * G) {
-                        const int o0 = __ldg(plan.tap_off + tb + j), o1 = __ldg(plan.tap_off + tb + j + G);
-                        const int o2 = __ldg(plan.tap_off + tb + j + 2 * G), o3 = __ldg(plan.tap_off + tb + j + 3 * G);
-                        const T v0 = __ldg(vals + tb + j), v1 = __ldg(vals + tb + j + G);
-                        const T v2 = __ldg(vals + tb + j + 2 * G), v3 = __ldg(vals + tb + j + 3 * G);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            if (e < E) {
-                                acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
-                                acc[e] += v2 * S[o2 + base[e]] + v3 * S[o3 + base[e]];
-                            }
-                        }
-                    }
-                    for (; j < P.ntap; j += G) {
-                        const int o0 = __ldg(plan.tap_off + tb + j);
-                        const T v0 = __ldg(vals + tb + j);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (e < E) acc[e] += v0 * S[o0 + base[e]];
-                    }
-                } else {
-                    const int rr = r * r;
-                    const int py0 = w.ty0 >> lg, px0 = w.tx0 >> lg;
-                    int base[4], ph[4];
+                for (int e = 0; e < 4; ++e) base[e] = ly[e] * P.PC + lx[e];
+                const int tb = P.tap_begin;
+                int j = g;
+                for (; j + 3 * G < P.ntap; j += 4 * G) {
+                    const int o0 = __ldg(plan.tap_off + tb + j), o1 = __ldg(plan.tap_off + tb + j + G);
+                    const int o2 = __ldg(plan.tap_off + tb + j + 2 * G), o3 = __ldg(plan.tap_off + tb + j + 3 * G);
+                    const T v0 = __ldg(vals + tb + j), v1 = __ldg(vals + tb + j + G);
+                    const T v2 = __ldg(vals + tb + j + 2 * G), v3 = __ldg(vals + tb + j + 3 * G);
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int yy = w.ty0 + ly[e], xx = w.tx0 + lx[e];
-                        base[e] = ((yy >> lg) - py0) * P.PC + ((xx >> lg) - px0);
-                        ph[e] = ((yy & m) << lg) + (xx & m);
-                    }
-                    const int tb = P.tap_begin;
-                    if (E == 1 || r <= 8) {
-                        const int* __restrict__ to = plan.tap_off + tb + ph[0];
-                        const T* __restrict__ tv = vals + tb + ph[0];
-                        int j = g;
-                        for (; j + G < P.ntap; j += 2 * G) {
-                            const int o0 = __ldg(to + j * rr), o1 = __ldg(to + (j + G) * rr);
-                            const T v0 = __ldg(tv + j * rr), v1 = __ldg(tv + (j + G) * rr);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (e < E) acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
-                        }
-                        for (; j < P.ntap; j += G) {
-                            const int o0 = __ldg(to + j * rr);
-                            const T v0 = __ldg(tv + j * rr);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e)
-                                if (e < E) acc[e] += v0 * S[o0 + base[e]];
-                        }
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int* __restrict__ to = plan.tap_off + tb + ph[e];
-                            const T* __restrict__ tv = vals + tb + ph[e];
-                            for (int j = g; j < P.ntap; j += G) acc[e] += __ldg(tv + j * rr) * S[__ldg(to + j * rr) + base[e]];
+                        if (e < E) {
+                            acc[e] += v0 * Sp[o0 + base[e]] + v1 * Sp[o1 + base[e]];
+                            acc[e] += v2 * Sp[o2 + base[e]] + v3 * Sp[o3 + base[e]];
                         }
                     }
                 }
-                __syncthreads();
+                for (; j < P.ntap; j += G) {
+                    const int o0 = __ldg(plan.tap_off + tb + j);
+                    const T v0 = __ldg(vals + tb + j);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (e < E) acc[e] += v0 * Sp[o0 + base[e]];
+                }
+            } else if (P.mode == kUp) {
+                const T* __restrict__ Sp = S + P.soff;
+                const int rr = r * r;
+                const int py0 = w.ty0 >> lg, px0 = w.tx0 >> lg;
+                int base[4], ph[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int yy = w.ty0 + ly[e], xx = w.tx0 + lx[e];
+                    base[e] = ((yy >> lg) - py0) * P.PC + ((xx >> lg) - px0);
+                    ph[e] = ((yy & m) << lg) + (xx & m);
+                }
+                const int tb = P.tap_begin;
+                if (E == 1 || r <= 8) {
+                    const int* __restrict__ to = plan.tap_off + tb + ph[0];
+                    const T* __restrict__ tv = vals + tb + ph[0];
+                    int j = g;
+                    for (; j + G < P.ntap; j += 2 * G) {
+                        const int o0 = __ldg(to + j * rr), o1 = __ldg(to + (j + G) * rr);
+                        const T v0 = __ldg(tv + j * rr), v1 = __ldg(tv + (j + G) * rr);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (e < E) acc[e] += v0 * Sp[o0 + base[e]] + v1 * Sp[o1 + base[e]];
+                    }
+                    for (; j < P.ntap; j += G) {
+                        const int o0 = __ldg(to + j * rr);
+                        const T v0 = __ldg(tv + j * rr);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+                            if (e < E) acc[e] += v0 * Sp[o0 + base[e]];
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int* __restrict__ to = plan.tap_off + tb + ph[e];
+                        const T* __restrict__ tv = vals + tb + ph[e];
+                        for (int j = g; j < P.ntap; j += G) acc[e] += __ldg(tv + j * rr) * Sp[__ldg(to + j * rr) + base[e]];
+                    }
+                }
             } else {
                 // gather from global memory (regions larger than the shared-memory budget)
+                const SubbandDev si = A.sb[P.in_sb];
+                const T* __restrict__ src = in + si.off;
                 const int R = si.rows, C = si.cols;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -430,8 +481,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
                 }
             }
         }
-        __syncthreads();
+        it = nx;
+        T* tmp = S;
+        S = Snext;
+        Snext = tmp;
     }
+    cp_async_wait<0>();
+    __syncthreads();
     // totals (and, in the last CTA, the queue reset)
     double v[2] = {d0 + (double)s0 + (double)c0, EPI == kK2 ? (double)mx : (double)s1 + (double)c1}, tot[2];
     const unsigned maxmask = (EPI == kK2) ? 2u : 0u;

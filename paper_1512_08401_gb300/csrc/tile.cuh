@@ -8,7 +8,9 @@
 //   up pair (input coarser, r = 2^lg): out[r P + phi] += v_t in[P + d_t] over the taps of
 //     phase phi, padded to the same count for every phase;
 //   pairs whose region does not fit even for 1 x 1 tiles gather from global memory.
-// Tiles are processed heaviest first by persistent CTAs that pull items from a device queue.
+// Tiles are processed heaviest first by persistent CTAs that pull items from a device queue;
+// all regions of a tile are staged at once with cp.async, double buffered so that the next
+// tile's loads are in flight while the current tile computes.
 #pragma once
 #include <vector>
 
@@ -22,6 +24,7 @@ enum TileMode { kDown = 0, kUp = 1, kDownGlobal = 2, kUpGlobal = 3 };
 
 struct TilePair {
     int in_sb;
+    int soff;         // staged: element offset of this pair's region in the tile's buffer
     int mode;         // TileMode
     int lg;           // log2 of the scale ratio r
     int RR, RC;       // staged region rows / cols (input units for down, P units for up)
@@ -51,6 +54,7 @@ struct TilePlanDev {
     const float* tap_v;
     const double* tap_v64;
     int n_items;
+    int buf_elems;            // elements of one staging buffer (two buffers per CTA)
     int smem_bytes;           // dynamic shared memory per CTA
 };
 
@@ -61,6 +65,7 @@ struct TilePlanHost {
     std::vector<int> tap_off;
     std::vector<float> tap_v;
     std::vector<double> tap_v64;
+    int buf_elems = 0;
     int smem_bytes = 0;
     long long macs = 0;        // MACs per application (taps x outputs, padding included)
 };
@@ -70,7 +75,8 @@ struct TileEntry {             // one tap of one pair, in gather form
     double v;
 };
 
-// Build the plan of one operator for element size `esize` and a shared-memory budget.
+// Build the plan of one operator for element size `esize` and a per-buffer shared-memory
+// budget (all staged regions of one tile share one buffer; a CTA holds two buffers).
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget);
 
 struct TileQueue {             // device counters of one operator launch
