@@ -304,6 +304,7 @@ static void build_ops(wdb_theta* th) {
 static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a, cudaStream_t st) {
     WDB_TRY(upload(th, h.pairs, const_cast<TilePair**>(&a.plan.pairs), st));
     WDB_TRY(upload(th, h.subs, const_cast<TileSub**>(&a.plan.subs), st));
+    WDB_TRY(upload(th, h.batches, const_cast<TileBatch**>(&a.plan.batches), st));
     WDB_TRY(upload(th, h.items, const_cast<TileItem**>(&a.plan.items), st));
     WDB_TRY(upload(th, h.tap_off, const_cast<int**>(&a.plan.tap_off), st));
     WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&a.plan.tap_v), st));

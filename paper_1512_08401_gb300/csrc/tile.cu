@@ -83,35 +83,34 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
     std::vector<ItemCost> items;
     for (int o = 0; o < L.S; ++o) {
         const SubbandDev& so = L.sb[o];
-        // largest tile (<= 32, <= the subband) whose staged regions, all together, fit the
-        // buffer; pairs that do not fit even for 1 x 1 tiles (largest first) gather from
-        // global memory
+        // largest tile (<= 32, <= the subband) whose staged regions each fit one buffer;
+        // a pair that does not fit even for 1 x 1 tiles gathers from global memory
         const int np = (int)by_out[o].size();
         std::vector<bool> global(np, false);
-        auto total = [&](int ts) {
-            long long sum = 0;
+        auto fits = [&](int ts) {
             for (int k = 0; k < np; ++k)
-                if (!global[k]) sum += (geometry(*by_out[o][k], ts, esize).bytes + 15) / 16 * 16;
-            return sum;
+                if (geometry(*by_out[o][k], ts, esize).bytes > budget) return false;
+            return true;
         };
         int TS = std::min(32, next_pow2(std::max(so.rows, so.cols)));
-        while (TS > 1 && total(TS) > budget) TS >>= 1;
-        while (total(TS) > budget) {
-            int worst = -1;
-            long long wb = -1;
-            for (int k = 0; k < np; ++k)
-                if (!global[k] && geometry(*by_out[o][k], TS, esize).bytes > wb) {
-                    wb = geometry(*by_out[o][k], TS, esize).bytes;
-                    worst = k;
-                }
-            global[worst] = true;
-        }
+        while (TS > 1 && !fits(TS)) TS >>= 1;
+        for (int k = 0; k < np; ++k)
+            if (geometry(*by_out[o][k], TS, esize).bytes > budget) global[k] = true;
+        // staged pairs first (in batches that fill a buffer), then the global ones
+        std::vector<int> order;
+        for (int k = 0; k < np; ++k)
+            if (!global[k]) order.push_back(k);
+        for (int k = 0; k < np; ++k)
+            if (global[k]) order.push_back(k);
         TileSub& sub = plan.subs[o];
         sub.TS = TS;
         sub.pair_begin = (int)plan.pairs.size();
+        sub.batch_begin = sub.batch_end = 0;
         double taps_per_out = 0.0, stage_per_tile = 0.0;
         int soff = 0;
-        for (size_t k = 0; k < by_out[o].size(); ++k) {
+        sub.batch_begin = (int)plan.batches.size();
+        plan.batches.push_back(TileBatch{sub.pair_begin, sub.pair_begin});
+        for (int k : order) {
             const PairBuild& pb = *by_out[o][k];
             const Geometry g = geometry(pb, TS, esize);
             const int r = 1 << pb.lg, m = r - 1;
@@ -125,8 +124,18 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             tp.PC = g.PC;
             tp.y0 = pb.dy0;
             tp.x0 = pb.dx0;
-            tp.soff = soff;
-            if (!global[k]) soff += (int)((g.bytes + 15) / 16 * 16 / esize);
+            if (!global[k]) {
+                const int need = (int)((g.bytes + 15) / 16 * 16 / esize);
+                if (soff + need > budget / esize && plan.batches.back().pair_end > plan.batches.back().pair_begin) {
+                    plan.batches.push_back(TileBatch{(int)plan.pairs.size(), (int)plan.pairs.size()});
+                    soff = 0;
+                }
+                tp.soff = soff;
+                soff += need;
+                max_bytes = std::max(max_bytes, soff * esize);
+            } else {
+                tp.soff = 0;
+            }
             tp.tap_begin = (int)plan.tap_off.size();
             auto offset = [&](const TileEntry& e) -> int {
                 if (global[k]) return (e.dy << 16) | (e.dx & 0xffff);
@@ -167,10 +176,11 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             taps_per_out += tp.ntap;
             stage_per_tile += global[k] ? 0.0 : (double)g.RR * g.RC;
             plan.pairs.push_back(tp);
+            plan.batches.back().pair_end = (int)plan.pairs.size();
         }
         sub.pair_end = (int)plan.pairs.size();
-        sub.pad = 0;
-        max_bytes = std::max(max_bytes, soff * esize);
+        sub.batch_end = (int)plan.batches.size();
+        sub.pad[0] = sub.pad[1] = sub.pad[2] = 0;
         const int ty = (so.rows + TS - 1) / TS, tx = (so.cols + TS - 1) / TS;
         for (int a = 0; a < ty; ++a)
             for (int b = 0; b < tx; ++b) {
@@ -239,13 +249,13 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Issue the asynchronous copies of every staged region of item `it` into buffer S.
+// Issue the asynchronous copies of the staged regions of batch `bi` of item `it` into S.
 template <typename T>
-__device__ __forceinline__ void stage_item(const TileArgs& A, const T* __restrict__ in, int it, T* S) {
+__device__ __forceinline__ void stage_batch(const TileArgs& A, const T* __restrict__ in, int it, int bi, T* S) {
     const TilePlanDev& plan = A.plan;
     const TileItem w = plan.items[it];
-    const TileSub sub = plan.subs[w.o];
-    for (int pi = sub.pair_begin; pi < sub.pair_end; ++pi) {
+    const TileBatch bt = plan.batches[bi];
+    for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
         const TilePair P = plan.pairs[pi];
         if (P.mode != kDown && P.mode != kUp) continue;
         const SubbandDev si = A.sb[P.in_sb];
@@ -290,26 +300,32 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         const int k = ep.st->k;
         beta = (float)(k - 1) / (float)(k + 2);
     }
-    // prologue: first item
+    // prologue: first item, first batch
     if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
     __syncthreads();
     int it = s_next;
+    int bi = (it < plan.n_items) ? plan.subs[plan.items[it].o].batch_begin : 0;
     T* S = buf0;
     T* Snext = buf1;
-    if (it < plan.n_items) stage_item<T>(A, in, it, S);
+    if (it < plan.n_items) stage_batch<T>(A, in, it, bi, S);
     cp_async_commit();
+    T acc[4] = {0, 0, 0, 0};
     while (it < plan.n_items) {
-        // fetch and stage the next item while this one computes
+        const TileItem w = plan.items[it];
+        const TileSub sub = plan.subs[w.o];
+        // the next (item, batch): the next batch of this item, or batch 0 of a new item
+        int nit = it, nbi = bi + 1;
         __syncthreads();
-        if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
-        __syncthreads();
-        const int nx = s_next;
-        if (nx < plan.n_items) stage_item<T>(A, in, nx, Snext);
+        if (nbi >= sub.batch_end) {
+            if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
+            __syncthreads();
+            nit = s_next;
+            nbi = (nit < plan.n_items) ? plan.subs[plan.items[nit].o].batch_begin : 0;
+        }
+        if (nit < plan.n_items) stage_batch<T>(A, in, nit, nbi, Snext);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
-        const TileItem w = plan.items[it];
-        const TileSub sub = plan.subs[w.o];
         const SubbandDev so = A.sb[w.o];
         const int TS = sub.TS;
         const int nout = TS * TS;
@@ -337,8 +353,9 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
                 ly[e] = ly[0];
             }
         }
-        T acc[4] = {0, 0, 0, 0};
-        for (int pi = sub.pair_begin; pi < sub.pair_end; ++pi) {
+        const TileBatch bt = plan.batches[bi];
+        const bool last_batch = (bi + 1 == sub.batch_end);
+        for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
             const TilePair P = plan.pairs[pi];
             const int lg = P.lg, r = 1 << lg, m = r - 1;
             if (P.mode == kDown) {
@@ -438,13 +455,13 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
                 }
             }
         }
-        if (G > 1) {
+        if (last_batch && G > 1) {
             red_buf[t] = acc[0];
             __syncthreads();
             if (g == 0)
                 for (int k = 1; k < G; ++k) acc[0] += red_buf[t + k * nout];
         }
-        if (g == 0) {
+        if (last_batch && g == 0) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (e >= E) continue;
@@ -481,7 +498,12 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
                 }
             }
         }
-        it = nx;
+        if (last_batch) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] = 0;
+        }
+        it = nit;
+        bi = nbi;
         T* tmp = S;
         S = Snext;
         Snext = tmp;

@@ -8,9 +8,10 @@
 //   up pair (input coarser, r = 2^lg): out[r P + phi] += v_t in[P + d_t] over the taps of
 //     phase phi, padded to the same count for every phase;
 //   pairs whose region does not fit even for 1 x 1 tiles gather from global memory.
-// Tiles are processed heaviest first by persistent CTAs that pull items from a device queue;
-// all regions of a tile are staged at once with cp.async, double buffered so that the next
-// tile's loads are in flight while the current tile computes.
+// Tiles are processed heaviest first by persistent CTAs that pull items from a device queue.
+// The pairs of a tile are grouped into batches whose regions fit one buffer; each batch is
+// staged with cp.async, double buffered so that the next batch's loads are in flight while
+// the current batch computes.
 #pragma once
 #include <vector>
 
@@ -37,7 +38,12 @@ struct TilePair {
 struct TileSub {      // per output subband
     int TS;           // tile side
     int pair_begin, pair_end;
-    int pad;
+    int batch_begin, batch_end;   // batches of pairs whose staged regions share one buffer
+    int pad[3];
+};
+
+struct TileBatch {    // pairs [pair_begin, pair_end) of one subband, staged together
+    int pair_begin, pair_end;
 };
 
 struct TileItem {
@@ -49,6 +55,7 @@ struct TileItem {
 struct TilePlanDev {
     const TilePair* pairs;
     const TileSub* subs;
+    const TileBatch* batches;
     const TileItem* items;
     const int* tap_off;       // staged: offset in shared memory; global: (dy << 16) | (dx & 0xffff)
     const float* tap_v;
@@ -61,6 +68,7 @@ struct TilePlanDev {
 struct TilePlanHost {
     std::vector<TilePair> pairs;
     std::vector<TileSub> subs;
+    std::vector<TileBatch> batches;
     std::vector<TileItem> items;
     std::vector<int> tap_off;
     std::vector<float> tap_v;
@@ -76,7 +84,7 @@ struct TileEntry {             // one tap of one pair, in gather form
 };
 
 // Build the plan of one operator for element size `esize` and a per-buffer shared-memory
-// budget (all staged regions of one tile share one buffer; a CTA holds two buffers).
+// budget (a batch of staged regions shares one buffer; a CTA holds two buffers).
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget);
 
 struct TileQueue {             // device counters of one operator launch
