@@ -13,7 +13,7 @@ constexpr double kPowerRtol = 1e-12;
 constexpr double kStepMargin = 1.01;
 
 // shared-memory budget of one CTA of the tiled gather engine (bytes)
-constexpr int kTileSmemBudget = 48 * 1024;
+constexpr int kTileSmemBudget = 32 * 1024;
 
 template <typename T>
 wdb_status th_alloc(wdb_theta* th, T** p, size_t n);

@@ -106,14 +106,56 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         sub.TS = TS;
         sub.pair_begin = (int)plan.pairs.size();
         sub.batch_begin = sub.batch_end = 0;
+        // (batches are filled in below)
         double taps_per_out = 0.0, stage_per_tile = 0.0;
-        int soff = 0;
+        // first pass: geometry and batch membership (regions plus their taps must fit)
+        const int ebudget = budget / esize;
+        std::vector<int> batch_of(order.size()), pair_soff(order.size(), 0);
+        std::vector<int> batch_regions(1, 0), batch_taps(1, 0);
+        for (size_t q = 0; q < order.size(); ++q) {
+            const int k = order[q];
+            if (global[k]) {
+                batch_of[q] = (int)batch_regions.size() - 1;
+                continue;
+            }
+            const PairBuild& pb = *by_out[o][k];
+            const Geometry g = geometry(pb, TS, esize);
+            const int need = (int)((g.bytes + 15) / 16 * 16 / esize);
+            const int r = 1 << pb.lg;
+            int nt = (int)pb.taps.size();
+            if (pb.up) {
+                std::vector<int> cnt(r * r, 0);
+                for (const TileEntry* e : pb.taps) cnt[e->phase]++;
+                nt = *std::max_element(cnt.begin(), cnt.end()) * r * r;
+            }
+            // taps: one int offset + one value each, rounded to 16 bytes
+            auto tap_elems = [&](int ntaps) { return (int)(((long long)ntaps * (4 + esize) + 15) / 16 * 16 / esize); };
+            const bool nonempty = batch_regions.back() > 0;
+            if (nonempty && batch_regions.back() + need + tap_elems(batch_taps.back() + nt) > ebudget) {
+                batch_regions.push_back(0);
+                batch_taps.push_back(0);
+            }
+            batch_of[q] = (int)batch_regions.size() - 1;
+            pair_soff[q] = batch_regions.back();
+            batch_regions.back() += need;
+            batch_taps.back() += nt;
+        }
         sub.batch_begin = (int)plan.batches.size();
-        plan.batches.push_back(TileBatch{sub.pair_begin, sub.pair_begin});
-        for (int k : order) {
+        for (size_t bi = 0; bi < batch_regions.size(); ++bi) {
+            TileBatch bt{};
+            bt.pair_begin = bt.pair_end = (int)plan.pairs.size();
+            plan.batches.push_back(bt);
+        }
+        for (size_t q = 0; q < order.size(); ++q) {
+            const int k = order[q];
             const PairBuild& pb = *by_out[o][k];
             const Geometry g = geometry(pb, TS, esize);
             const int r = 1 << pb.lg, m = r - 1;
+            TileBatch& bt = plan.batches[sub.batch_begin + batch_of[q]];
+            if (bt.pair_end == bt.pair_begin) {
+                bt.pair_begin = bt.pair_end = (int)plan.pairs.size();
+                bt.tap_begin = bt.tap_end = (int)plan.tap_off.size();
+            }
             TilePair tp;
             tp.in_sb = pb.in;
             tp.lg = pb.lg;
@@ -124,27 +166,16 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             tp.PC = g.PC;
             tp.y0 = pb.dy0;
             tp.x0 = pb.dx0;
-            if (!global[k]) {
-                const int need = (int)((g.bytes + 15) / 16 * 16 / esize);
-                if (soff + need > budget / esize && plan.batches.back().pair_end > plan.batches.back().pair_begin) {
-                    plan.batches.push_back(TileBatch{(int)plan.pairs.size(), (int)plan.pairs.size()});
-                    soff = 0;
-                }
-                tp.soff = soff;
-                soff += need;
-                max_bytes = std::max(max_bytes, soff * esize);
-            } else {
-                tp.soff = 0;
-            }
+            tp.soff = global[k] ? 0 : pair_soff[q];
             tp.tap_begin = (int)plan.tap_off.size();
             auto offset = [&](const TileEntry& e) -> int {
                 if (global[k]) return (e.dy << 16) | (e.dx & 0xffff);
                 if (!pb.up) {
                     const int yy = e.dy - pb.dy0, xx = e.dx - pb.dx0;
                     const int plane = ((yy & m) << pb.lg) + (xx & m);
-                    return plane * g.PR * g.PC + (yy >> pb.lg) * g.PC + (xx >> pb.lg);
+                    return plane * g.PR * g.PC + (yy >> pb.lg) * g.PC + (xx >> pb.lg) + tp.soff;
                 }
-                return (e.dy - pb.dy0) * g.PC + (e.dx - pb.dx0);
+                return (e.dy - pb.dy0) * g.PC + (e.dx - pb.dx0) + tp.soff;
             };
             if (!pb.up) {
                 tp.ntap = (int)pb.taps.size();
@@ -161,13 +192,13 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 for (auto& v : ph) mx = std::max(mx, (int)v.size());
                 tp.ntap = mx;
                 for (int j = 0; j < mx; ++j)
-                    for (int q = 0; q < nph; ++q) {
-                        if (j < (int)ph[q].size()) {
-                            plan.tap_off.push_back(offset(*ph[q][j]));
-                            plan.tap_v.push_back((float)ph[q][j]->v);
-                            plan.tap_v64.push_back(ph[q][j]->v);
+                    for (int qq = 0; qq < nph; ++qq) {
+                        if (j < (int)ph[qq].size()) {
+                            plan.tap_off.push_back(offset(*ph[qq][j]));
+                            plan.tap_v.push_back((float)ph[qq][j]->v);
+                            plan.tap_v64.push_back(ph[qq][j]->v);
                         } else {
-                            plan.tap_off.push_back(global[k] ? 0 : 0);
+                            plan.tap_off.push_back(global[k] ? 0 : tp.soff);
                             plan.tap_v.push_back(0.f);
                             plan.tap_v64.push_back(0.0);
                         }
@@ -176,11 +207,25 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             taps_per_out += tp.ntap;
             stage_per_tile += global[k] ? 0.0 : (double)g.RR * g.RC;
             plan.pairs.push_back(tp);
-            plan.batches.back().pair_end = (int)plan.pairs.size();
+            bt.pair_end = (int)plan.pairs.size();
+            if (!global[k]) bt.tap_end = (int)plan.tap_off.size();
+        }
+        // tap copies follow the regions of each batch in the buffer
+        for (int bi = sub.batch_begin; bi < (int)plan.batches.size(); ++bi) {
+            TileBatch& bt = plan.batches[bi];
+            if (bt.tap_end < bt.tap_begin) bt.tap_end = bt.tap_begin;
+            const int nt = bt.tap_end - bt.tap_begin;
+            const int reg = batch_regions[bi - sub.batch_begin];
+            bt.tap_soff = reg * esize / 4;                                   // in ints
+            bt.val_soff = (int)(((long long)(bt.tap_soff + nt) * 4 + esize - 1) / esize);   // in T
+            const int total = (bt.val_soff + nt) * esize;
+            max_bytes = std::max(max_bytes, (total + 15) / 16 * 16);
         }
         sub.pair_end = (int)plan.pairs.size();
         sub.batch_end = (int)plan.batches.size();
-        sub.pad[0] = sub.pad[1] = sub.pad[2] = 0;
+        sub.pad[0] = sub.pad[1] = 0;
+        sub.lgTS = 0;
+        while ((1 << sub.lgTS) < TS) ++sub.lgTS;
         const int ty = (so.rows + TS - 1) / TS, tx = (so.cols + TS - 1) / TS;
         for (int a = 0; a < ty; ++a)
             for (int b = 0; b < tx; ++b) {
@@ -249,12 +294,16 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Issue the asynchronous copies of the staged regions of batch `bi` of item `it` into S.
+// Issue the asynchronous copies of batch `bi` of item `it` into buffer S: every staged
+// region (row by row, one warp per row, lanes along the row, periodic wrap) and the batch's
+// tap offsets and values.
 template <typename T>
 __device__ __forceinline__ void stage_batch(const TileArgs& A, const T* __restrict__ in, int it, int bi, T* S) {
     const TilePlanDev& plan = A.plan;
     const TileItem w = plan.items[it];
     const TileBatch bt = plan.batches[bi];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = kTileThreads / 32;
     for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
         const TilePair P = plan.pairs[pi];
         if (P.mode != kDown && P.mode != kUp) continue;
@@ -264,18 +313,30 @@ __device__ __forceinline__ void stage_batch(const TileArgs& A, const T* __restri
         const int Y0 = (P.mode == kDown) ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
         const int X0 = (P.mode == kDown) ? ((w.tx0 << lg) + P.x0) : ((w.tx0 >> lg) + P.x0);
         const int yb = pos_mod(Y0, si.rows), xb = pos_mod(X0, si.cols);
-        const int n = P.RR * P.RC;
         const int plane = P.PR * P.PC;
         T* dst = S + P.soff;
-        for (int q = threadIdx.x; q < n; q += kTileThreads) {
-            const int yr = q / P.RC, xr = q - yr * P.RC;
-            int gy = yb + yr, gx = xb + xr;
-            if (gy >= si.rows) gy %= si.rows;
-            if (gx >= si.cols) gx %= si.cols;
-            const int idx = (P.mode == kDown) ? ((((yr & m) << lg) + (xr & m)) * plane + (yr >> lg) * P.PC + (xr >> lg))
-                                              : (yr * P.PC + xr);
-            cp_async(dst + idx, src + (size_t)gy * si.cols + gx, (int)sizeof(T));
+        for (int yr = warp; yr < P.RR; yr += NW) {
+            int gy = yb + yr;
+            while (gy >= si.rows) gy -= si.rows;
+            const T* __restrict__ row = src + (size_t)gy * si.cols;
+            T* drow = (P.mode == kDown) ? dst + ((yr & m) << lg) * plane + (yr >> lg) * P.PC : dst + yr * P.PC;
+            int gx = xb + lane;
+            while (gx >= si.cols) gx -= si.cols;
+            for (int xr = lane; xr < P.RC; xr += 32) {
+                const int idx = (P.mode == kDown) ? ((xr & m) * plane + (xr >> lg)) : xr;
+                cp_async(drow + idx, row + gx, (int)sizeof(T));
+                gx += 32;
+                while (gx >= si.cols) gx -= si.cols;
+            }
         }
+    }
+    const int nt = bt.tap_end - bt.tap_begin;
+    int* toff = reinterpret_cast<int*>(S) + bt.tap_soff;
+    T* tval = S + bt.val_soff;
+    const T* __restrict__ vals = tvals<T>(plan);
+    for (int j = threadIdx.x; j < nt; j += kTileThreads) {
+        cp_async(toff + j, plan.tap_off + bt.tap_begin + j, 4);
+        cp_async(tval + j, vals + bt.tap_begin + j, (int)sizeof(T));
     }
 }
 
@@ -291,7 +352,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         if (*(volatile int*)&ep.st->stop) return;
     }
     const TilePlanDev& plan = A.plan;
-    const T* __restrict__ vals = tvals<T>(plan);
+    const T* __restrict__ gvals = tvals<T>(plan);
     const int t = threadIdx.x;
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, mx = 0.f;
     double d0 = 0.0;
@@ -313,7 +374,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
     while (it < plan.n_items) {
         const TileItem w = plan.items[it];
         const TileSub sub = plan.subs[w.o];
-        // the next (item, batch): the next batch of this item, or batch 0 of a new item
+        // the next (item, batch): the next batch of this item, or the first batch of a new item
         int nit = it, nbi = bi + 1;
         __syncthreads();
         if (nbi >= sub.batch_end) {
@@ -327,7 +388,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         cp_async_wait<1>();
         __syncthreads();
         const SubbandDev so = A.sb[w.o];
-        const int TS = sub.TS;
+        const int TS = sub.TS, lgTS = sub.lgTS;
         const int nout = TS * TS;
         int E, G, g;
         int ly[4], lx[4];
@@ -342,11 +403,11 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
             }
         } else {
             E = 1;
-            G = kTileThreads / nout;
-            g = t / nout;
-            const int oi = t - g * nout;
-            lx[0] = oi % TS;
-            ly[0] = oi / TS;
+            G = kTileThreads >> (2 * lgTS);
+            g = t >> (2 * lgTS);
+            const int oi = t & (nout - 1);
+            lx[0] = oi & (TS - 1);
+            ly[0] = oi >> lgTS;
 #pragma unroll
             for (int e = 1; e < 4; ++e) {
                 lx[e] = lx[0];
@@ -355,38 +416,42 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         }
         const TileBatch bt = plan.batches[bi];
         const bool last_batch = (bi + 1 == sub.batch_end);
+        const int* __restrict__ soffs = reinterpret_cast<const int*>(S) + bt.tap_soff - bt.tap_begin;
+        const T* __restrict__ svals = S + bt.val_soff - bt.tap_begin;
         for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
             const TilePair P = plan.pairs[pi];
             const int lg = P.lg, r = 1 << lg, m = r - 1;
             if (P.mode == kDown) {
-                const T* __restrict__ Sp = S + P.soff;
                 int base[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) base[e] = ly[e] * P.PC + lx[e];
-                const int tb = P.tap_begin;
+                const int* __restrict__ to = soffs + P.tap_begin;
+                const T* __restrict__ tv = svals + P.tap_begin;
                 int j = g;
-                for (; j + 3 * G < P.ntap; j += 4 * G) {
-                    const int o0 = __ldg(plan.tap_off + tb + j), o1 = __ldg(plan.tap_off + tb + j + G);
-                    const int o2 = __ldg(plan.tap_off + tb + j + 2 * G), o3 = __ldg(plan.tap_off + tb + j + 3 * G);
-                    const T v0 = __ldg(vals + tb + j), v1 = __ldg(vals + tb + j + G);
-                    const T v2 = __ldg(vals + tb + j + 2 * G), v3 = __ldg(vals + tb + j + 3 * G);
+                if (E == 4) {
+                    for (; j + 1 < P.ntap; j += 2) {
+                        const int o0 = to[j], o1 = to[j + 1];
+                        const T v0 = tv[j], v1 = tv[j + 1];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        if (e < E) {
-                            acc[e] += v0 * Sp[o0 + base[e]] + v1 * Sp[o1 + base[e]];
-                            acc[e] += v2 * Sp[o2 + base[e]] + v3 * Sp[o3 + base[e]];
-                        }
+                        for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
                     }
-                }
-                for (; j < P.ntap; j += G) {
-                    const int o0 = __ldg(plan.tap_off + tb + j);
-                    const T v0 = __ldg(vals + tb + j);
+                    for (; j < P.ntap; ++j) {
+                        const int o0 = to[j];
+                        const T v0 = tv[j];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (e < E) acc[e] += v0 * Sp[o0 + base[e]];
+                        for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
+                    }
+                } else {
+                    const T* __restrict__ Sb = S + base[0];
+                    T a0 = 0, a1 = 0;
+                    for (; j + G < P.ntap; j += 2 * G) {
+                        a0 += tv[j] * Sb[to[j]];
+                        a1 += tv[j + G] * Sb[to[j + G]];
+                    }
+                    if (j < P.ntap) a0 += tv[j] * Sb[to[j]];
+                    acc[0] += a0 + a1;
                 }
             } else if (P.mode == kUp) {
-                const T* __restrict__ Sp = S + P.soff;
                 const int rr = r * r;
                 const int py0 = w.ty0 >> lg, px0 = w.tx0 >> lg;
                 int base[4], ph[4];
@@ -396,31 +461,33 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
                     base[e] = ((yy >> lg) - py0) * P.PC + ((xx >> lg) - px0);
                     ph[e] = ((yy & m) << lg) + (xx & m);
                 }
-                const int tb = P.tap_begin;
                 if (E == 1 || r <= 8) {
-                    const int* __restrict__ to = plan.tap_off + tb + ph[0];
-                    const T* __restrict__ tv = vals + tb + ph[0];
-                    int j = g;
-                    for (; j + G < P.ntap; j += 2 * G) {
-                        const int o0 = __ldg(to + j * rr), o1 = __ldg(to + (j + G) * rr);
-                        const T v0 = __ldg(tv + j * rr), v1 = __ldg(tv + (j + G) * rr);
+                    const int* __restrict__ to = soffs + P.tap_begin + ph[0];
+                    const T* __restrict__ tv = svals + P.tap_begin + ph[0];
+                    if (E == 4) {
+                        for (int j = 0; j < P.ntap; ++j) {
+                            const int o0 = to[j * rr];
+                            const T v0 = tv[j * rr];
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (e < E) acc[e] += v0 * Sp[o0 + base[e]] + v1 * Sp[o1 + base[e]];
-                    }
-                    for (; j < P.ntap; j += G) {
-                        const int o0 = __ldg(to + j * rr);
-                        const T v0 = __ldg(tv + j * rr);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            if (e < E) acc[e] += v0 * Sp[o0 + base[e]];
+                            for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
+                        }
+                    } else {
+                        const T* __restrict__ Sb = S + base[0];
+                        T a0 = 0, a1 = 0;
+                        int j = g;
+                        for (; j + G < P.ntap; j += 2 * G) {
+                            a0 += tv[j * rr] * Sb[to[j * rr]];
+                            a1 += tv[(j + G) * rr] * Sb[to[(j + G) * rr]];
+                        }
+                        if (j < P.ntap) a0 += tv[j * rr] * Sb[to[j * rr]];
+                        acc[0] += a0 + a1;
                     }
                 } else {
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
-                        const int* __restrict__ to = plan.tap_off + tb + ph[e];
-                        const T* __restrict__ tv = vals + tb + ph[e];
-                        for (int j = g; j < P.ntap; j += G) acc[e] += __ldg(tv + j * rr) * Sp[__ldg(to + j * rr) + base[e]];
+                        const int* __restrict__ to = soffs + P.tap_begin + ph[e];
+                        const T* __restrict__ tv = svals + P.tap_begin + ph[e];
+                        for (int j = g; j < P.ntap; j += G) acc[e] += tv[j * rr] * S[to[j * rr] + base[e]];
                     }
                 }
             } else {
@@ -449,7 +516,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
                     for (int j = g; j < P.ntap; j += G) {
                         const int pk = __ldg(plan.tap_off + tb + j * step);
                         const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
-                        a += __ldg(vals + tb + j * step) * src[(size_t)yy * C + xx];
+                        a += __ldg(gvals + tb + j * step) * src[(size_t)yy * C + xx];
                     }
                     acc[e] += a;
                 }

@@ -36,14 +36,19 @@ struct TilePair {
 };
 
 struct TileSub {      // per output subband
-    int TS;           // tile side
+    int TS;           // tile side (a power of two)
+    int lgTS;
     int pair_begin, pair_end;
     int batch_begin, batch_end;   // batches of pairs whose staged regions share one buffer
-    int pad[3];
+    int pad[2];
 };
 
 struct TileBatch {    // pairs [pair_begin, pair_end) of one subband, staged together
     int pair_begin, pair_end;
+    int tap_begin, tap_end;       // taps of the staged pairs, copied to shared memory
+    int tap_soff;                 // element offset of the tap offsets (ints) in the buffer
+    int val_soff;                 // element offset of the tap values in the buffer
+    int pad[2];
 };
 
 struct TileItem {
