@@ -202,6 +202,20 @@ wdb_status wdb_dwt(const float* img_dev, float* coef_dev, int n_rows, int n_cols
 wdb_status wdb_idwt(const float* coef_dev, float* img_dev, int n_rows, int n_cols,
                     const char* wavelet, int levels, void* stream);
 
+/* Forward transform that allocates nothing (the paper has no counterpart; this is a service
+ * for callers that cannot allocate device memory: code running inside another framework's
+ * locked-down memory pool, real-time paths where cudaMalloc and the synchronisation it may
+ * imply are not allowed, or callers holding a capture or lock that an allocation would
+ * break). Same result as wdb_dwt, but the intermediate approximations live in a file-scope
+ * device array of 4 Mi floats (16 MiB) that every GPU loading the library keeps until the
+ * process exits; images above 8 Mi - 2 pixels are rejected with WDB_EINVAL. The first call
+ * on each device looks the array's device address up (make that first call before any
+ * stream capture). All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads) race and must be serialised by the caller. No cudaMalloc, cudaFree or
+ * allocating library routine is called. */
+wdb_status wdb_dwt_noalloc(const float* img_dev, float* coef_dev, int n_rows, int n_cols,
+                           const char* wavelet, int levels, void* stream);
+
 /* Filter taps of a wavelet (host): h (low-pass) and g (high-pass) of length 2p. */
 wdb_status wdb_wavelet_filters(const char* wavelet, int cap, double* h_host, double* g_host,
                                int* taps);

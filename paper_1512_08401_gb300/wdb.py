@@ -80,6 +80,7 @@ _SIGS = {
     "wdb_solve_fft": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_dwt": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
     "wdb_idwt": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
+    "wdb_dwt_noalloc": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
     "wdb_wavelet_filters": (i32, [C.c_char_p, i32, pd, pd, pi]),
     "wdb_status_str": (C.c_char_p, [i32]),
     "wdb_last_error": (C.c_char_p, []),
@@ -332,3 +333,10 @@ def idwt(coef, img, n_rows, n_cols, wavelet="db4", levels=4, stream=None):
     _check(lib().wdb_idwt(_dev(coef, n_rows * n_cols), _dev(img, n_rows * n_cols), n_rows, n_cols,
                           wavelet.encode(), levels, _stream(stream)))
     return img
+
+
+def dwt_noalloc(img, coef, n_rows, n_cols, wavelet="db4", levels=4, stream=None):
+    """Forward transform without any device allocation (scratch in a static device array)."""
+    _check(lib().wdb_dwt_noalloc(_dev(img, n_rows * n_cols), _dev(coef, n_rows * n_cols), n_rows, n_cols,
+                                 wavelet.encode(), levels, _stream(stream)))
+    return coef
