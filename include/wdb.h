@@ -175,6 +175,17 @@ wdb_status wdb_solve_coeffs(wdb_theta* th, const float* x0_dev, float* x_dev,
                             const wdb_solve_params* params, void* stream,
                             wdb_solve_result* result);
 
+/* Batched solve (many problems of uneven size, each with its own Theta_K handle, image,
+ * weights and stopping rule): the problems advance together, two launches per iteration
+ * that cover the tiles of every running problem, heaviest first, in chunks of check_every
+ * iterations replayed as a CUDA graph; a problem that meets its own stopping rule drops out.
+ * th[b], u_dev[b], x_dev[b], params[b], results[b] for b < B; every handle distinct; all
+ * problems share check_every. results[b].objective is the exact FP64 objective of x_dev[b];
+ * results[b].support is -1 (not counted); solve_ms is the wall time of the whole call.
+ * Synchronises `stream`. */
+wdb_status wdb_solve_batch(int B, wdb_theta* const* th, const float* const* u_dev, float* const* x_dev,
+                           const wdb_solve_params* params, void* stream, wdb_solve_result* results);
+
 /* Objective E(x) = 1/2||Theta_K x - x0||^2 + sum w|x| in FP64 for device x, x0. */
 wdb_status wdb_theta_objective(const wdb_theta* th, const float* x_dev, const float* x0_dev,
                                double lambda, const double* w_subband_host, void* stream,

@@ -306,6 +306,12 @@ wdb_status wdb_solve_coeffs(wdb_theta* th, const float* x0_dev, float* x_dev, co
     return s;
 }
 
+wdb_status wdb_solve_batch(int B, wdb_theta* const* th, const float* const* u_dev, float* const* x_dev,
+                           const wdb_solve_params* params, void* stream, wdb_solve_result* results) {
+    WDB_TRY(need_device());
+    return solve_batch(B, th, u_dev, x_dev, params, static_cast<cudaStream_t>(stream), results);
+}
+
 wdb_status wdb_theta_objective(const wdb_theta* thc, const float* x_dev, const float* x0_dev, double lambda,
                                const double* w_subband_host, void* stream, double* E_host) {
     wdb_theta* th = const_cast<wdb_theta*>(thc);

@@ -238,7 +238,10 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             }
     }
     std::stable_sort(items.begin(), items.end(), [](const ItemCost& x, const ItemCost& y) { return x.cost > y.cost; });
-    for (auto& ic : items) plan.items.push_back(ic.it);
+    for (auto& ic : items) {
+        plan.items.push_back(ic.it);
+        plan.item_cost.push_back(ic.cost);
+    }
     plan.buf_elems = std::max(max_bytes, 16) / esize;
     plan.smem_bytes = 2 * plan.buf_elems * esize;
     return plan;
@@ -249,14 +252,14 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
 // ---------------------------------------------------------------------------------------
 namespace {
 
-enum Epi { kApply = 0, kApplyNorm = 1, kK1 = 2, kK2 = 3, kResNorm = 4 };
+enum Epi { kApply = 0, kApplyNorm = 1, kK1 = 2, kK2 = 3, kResNorm = 4, kObj = 5 };
 
 struct EpiArgs {
-    const float* x0;          // kK1, kResNorm
+    const float* x0;          // kK1, kResNorm, kObj
     float* y;                 // kK2 (in place)
     float* x;                 // kK2 (in place)
     const float* step_tab;    // kK2: tau / P per phase class
-    const float* w_sb;        // kK2: weights per subband
+    const float* w_sb;        // kK2, kObj: weights per subband
     const double* scale;      // kApply*: optional factor per phase class
     double* part;             // per-CTA partials
     SolveState* st;           // kK1, kK2
@@ -294,20 +297,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Issue the asynchronous copies of batch `bi` of item `it` into buffer S: every staged
-// region (row by row, one warp per row, lanes along the row, periodic wrap) and the batch's
-// tap offsets and values.
+// Issue the asynchronous copies of batch `bi` of tile `w` into buffer S: every staged region
+// (row by row, one warp per row, lanes along the row, periodic wrap) and the batch's taps.
 template <typename T>
-__device__ __forceinline__ void stage_batch(const TileArgs& A, const T* __restrict__ in, int it, int bi, T* S) {
-    const TilePlanDev& plan = A.plan;
-    const TileItem w = plan.items[it];
+__device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const SubbandDev* __restrict__ sb,
+                                            const T* __restrict__ in, const TileItem& w, int bi, T* S) {
     const TileBatch bt = plan.batches[bi];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = kTileThreads / 32;
     for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
         const TilePair P = plan.pairs[pi];
         if (P.mode != kDown && P.mode != kUp) continue;
-        const SubbandDev si = A.sb[P.in_sb];
+        const SubbandDev si = sb[P.in_sb];
         const T* __restrict__ src = in + si.off;
         const int lg = P.lg, m = (1 << lg) - 1;
         const int Y0 = (P.mode == kDown) ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
@@ -340,6 +341,222 @@ __device__ __forceinline__ void stage_batch(const TileArgs& A, const T* __restri
     }
 }
 
+// Outputs of this thread in a TS x TS tile: TS = 32 -> 4 outputs (rows ly + 8e); smaller
+// tiles -> 1 output, with G thread groups splitting the taps.
+struct ThreadMap {
+    int E, G, g, nout;
+    int ly[4], lx[4];
+};
+
+__device__ __forceinline__ ThreadMap thread_map(const TileSub& sub) {
+    ThreadMap tm;
+    const int t = threadIdx.x, TS = sub.TS, lgTS = sub.lgTS;
+    tm.nout = TS * TS;
+    if (TS == 32) {
+        tm.E = 4;
+        tm.G = 1;
+        tm.g = 0;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            tm.lx[e] = t & 31;
+            tm.ly[e] = (t >> 5) + 8 * e;
+        }
+    } else {
+        tm.E = 1;
+        tm.G = kTileThreads >> (2 * lgTS);
+        tm.g = t >> (2 * lgTS);
+        const int oi = t & (tm.nout - 1);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            tm.lx[e] = oi & (TS - 1);
+            tm.ly[e] = oi >> lgTS;
+        }
+    }
+    return tm;
+}
+
+// Accumulate the pairs of batch `bi` of tile `w` (staged in S) into acc.
+template <typename T>
+__device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const SubbandDev* __restrict__ sb,
+                                              const T* __restrict__ in, const TileItem& w, const SubbandDev& so,
+                                              int bi, const T* __restrict__ S, const ThreadMap& tm, T (&acc)[4]) {
+    const TileBatch bt = plan.batches[bi];
+    const int* __restrict__ soffs = reinterpret_cast<const int*>(S) + bt.tap_soff - bt.tap_begin;
+    const T* __restrict__ svals = S + bt.val_soff - bt.tap_begin;
+    const T* __restrict__ gvals = tvals<T>(plan);
+    const int E = tm.E, G = tm.G, g = tm.g;
+    for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
+        const TilePair P = plan.pairs[pi];
+        const int lg = P.lg, r = 1 << lg, m = r - 1;
+        if (P.mode == kDown) {
+            int base[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) base[e] = tm.ly[e] * P.PC + tm.lx[e];
+            const int* __restrict__ to = soffs + P.tap_begin;
+            const T* __restrict__ tv = svals + P.tap_begin;
+            int j = g;
+            if (E == 4) {
+                for (; j + 1 < P.ntap; j += 2) {
+                    const int o0 = to[j], o1 = to[j + 1];
+                    const T v0 = tv[j], v1 = tv[j + 1];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
+                }
+                for (; j < P.ntap; ++j) {
+                    const int o0 = to[j];
+                    const T v0 = tv[j];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
+                }
+            } else {
+                const T* __restrict__ Sb = S + base[0];
+                T a0 = 0, a1 = 0;
+                for (; j + G < P.ntap; j += 2 * G) {
+                    a0 += tv[j] * Sb[to[j]];
+                    a1 += tv[j + G] * Sb[to[j + G]];
+                }
+                if (j < P.ntap) a0 += tv[j] * Sb[to[j]];
+                acc[0] += a0 + a1;
+            }
+        } else if (P.mode == kUp) {
+            const int rr = r * r;
+            const int py0 = w.ty0 >> lg, px0 = w.tx0 >> lg;
+            int base[4], ph[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int yy = w.ty0 + tm.ly[e], xx = w.tx0 + tm.lx[e];
+                base[e] = ((yy >> lg) - py0) * P.PC + ((xx >> lg) - px0);
+                ph[e] = ((yy & m) << lg) + (xx & m);
+            }
+            if (E == 1 || r <= 8) {
+                const int* __restrict__ to = soffs + P.tap_begin + ph[0];
+                const T* __restrict__ tv = svals + P.tap_begin + ph[0];
+                if (E == 4) {
+                    for (int j = 0; j < P.ntap; ++j) {
+                        const int o0 = to[j * rr];
+                        const T v0 = tv[j * rr];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
+                    }
+                } else {
+                    const T* __restrict__ Sb = S + base[0];
+                    T a0 = 0, a1 = 0;
+                    int j = g;
+                    for (; j + G < P.ntap; j += 2 * G) {
+                        a0 += tv[j * rr] * Sb[to[j * rr]];
+                        a1 += tv[(j + G) * rr] * Sb[to[(j + G) * rr]];
+                    }
+                    if (j < P.ntap) a0 += tv[j * rr] * Sb[to[j * rr]];
+                    acc[0] += a0 + a1;
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int* __restrict__ to = soffs + P.tap_begin + ph[e];
+                    const T* __restrict__ tv = svals + P.tap_begin + ph[e];
+                    for (int j = g; j < P.ntap; j += G) acc[e] += tv[j * rr] * S[to[j * rr] + base[e]];
+                }
+            }
+        } else {
+            // gather from global memory (regions larger than the shared-memory budget)
+            const SubbandDev si = sb[P.in_sb];
+            const T* __restrict__ src = in + si.off;
+            const int R = si.rows, C = si.cols;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if (e >= E) continue;
+                const int py = w.ty0 + tm.ly[e], px = w.tx0 + tm.lx[e];
+                if (py >= so.rows || px >= so.cols) continue;
+                int by, bx, tb, step;
+                if (P.mode == kDownGlobal) {
+                    by = py << lg;
+                    bx = px << lg;
+                    tb = P.tap_begin;
+                    step = 1;
+                } else {
+                    by = py >> lg;
+                    bx = px >> lg;
+                    tb = P.tap_begin + (((py & m) << lg) + (px & m));
+                    step = r * r;
+                }
+                T a = 0;
+                for (int j = g; j < P.ntap; j += G) {
+                    const int pk = __ldg(plan.tap_off + tb + j * step);
+                    const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
+                    a += __ldg(gvals + tb + j * step) * src[(size_t)yy * C + xx];
+                }
+                acc[e] += a;
+            }
+        }
+    }
+}
+
+// Sum the G partial accumulators of each output (groups of threads that split the taps).
+template <typename T>
+__device__ __forceinline__ void group_reduce(const ThreadMap& tm, T (&acc)[4], T* red_buf) {
+    if (tm.G > 1) {
+        red_buf[threadIdx.x] = acc[0];
+        __syncthreads();
+        if (tm.g == 0)
+            for (int k = 1; k < tm.G; ++k) acc[0] += red_buf[threadIdx.x + k * tm.nout];
+    }
+}
+
+// Per-thread partial sums of the epilogues.
+struct Partials {
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, mx = 0.f;
+    double d0 = 0.0;
+};
+
+// Epilogue of the outputs of one tile (threads of group 0).
+template <typename T, int EPI>
+__device__ __forceinline__ void epilogue(const TileItem& w, const SubbandDev& so, const ThreadMap& tm, const T (&acc)[4],
+                                         T* __restrict__ out, const EpiArgs& ep, float beta, Partials& pt) {
+    if (tm.g != 0) return;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (e >= tm.E) continue;
+        const int py = w.ty0 + tm.ly[e], px = w.tx0 + tm.lx[e];
+        if (py >= so.rows || px >= so.cols) continue;
+        const size_t i = so.off + (size_t)py * so.cols + px;
+        const int mR = (1 << so.lgR) - 1;
+        const int cls = so.tab_off + ((py & mR) << so.lgR) + (px & mR);
+        if (EPI == kApply || EPI == kApplyNorm) {
+            T v = acc[e];
+            if (ep.scale) v = (T)((double)v * ep.scale[cls]);
+            out[i] = v;
+            if (EPI == kApplyNorm) {
+                if (sizeof(T) == 8) pt.d0 += (double)v * (double)v;
+                else neu_add(pt.s0, pt.c0, (float)v * (float)v);
+            }
+        } else if (EPI == kK1 || EPI == kResNorm || EPI == kObj) {
+            const float xv = ep.x0[i];
+            const float rv = (float)acc[e] - xv;
+            if (EPI != kObj) out[i] = (T)rv;
+            neu_add(pt.s0, pt.c0, rv * rv);
+            if (EPI == kK1) neu_add(pt.s1, pt.c1, xv * rv);
+            if (EPI == kObj) {
+                // kObj applies the operator to x itself: sum w|x| over this tile's outputs
+                neu_add(pt.s1, pt.c1, ep.w_sb[w.o] * fabsf(ep.x[i]));
+            }
+        } else if (EPI == kK2) {
+            const float gv = (float)acc[e];
+            const float stp = ep.step_tab[cls];
+            const float wv = ep.w_sb[w.o];
+            const float yv = ep.y[i], xo = ep.x[i];
+            const float z = yv - stp * gv;
+            const float xn = copysignf(fmaxf(fabsf(z) - stp * wv, 0.f), z);
+            ep.x[i] = xn;
+            ep.y[i] = xn + beta * (xn - xo);
+            neu_add(pt.s0, pt.c0, wv * fabsf(yv));
+            pt.mx = fmaxf(pt.mx, gw_ratio(gv, wv));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Single problem: persistent CTAs, heaviest tiles first, (tile, batch) double buffering
+// ---------------------------------------------------------------------------------------
 template <typename T, int EPI>
 __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T* __restrict__ in,
                                                             T* __restrict__ out, EpiArgs ep) {
@@ -352,29 +569,25 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         if (*(volatile int*)&ep.st->stop) return;
     }
     const TilePlanDev& plan = A.plan;
-    const T* __restrict__ gvals = tvals<T>(plan);
     const int t = threadIdx.x;
-    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, mx = 0.f;
-    double d0 = 0.0;
+    Partials pt;
     float beta = 0.f;
     if (EPI == kK2) {
         const int k = ep.st->k;
         beta = (float)(k - 1) / (float)(k + 2);
     }
-    // prologue: first item, first batch
     if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
     __syncthreads();
     int it = s_next;
     int bi = (it < plan.n_items) ? plan.subs[plan.items[it].o].batch_begin : 0;
     T* S = buf0;
     T* Snext = buf1;
-    if (it < plan.n_items) stage_batch<T>(A, in, it, bi, S);
+    if (it < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[it], bi, S);
     cp_async_commit();
     T acc[4] = {0, 0, 0, 0};
     while (it < plan.n_items) {
         const TileItem w = plan.items[it];
         const TileSub sub = plan.subs[w.o];
-        // the next (item, batch): the next batch of this item, or the first batch of a new item
         int nit = it, nbi = bi + 1;
         __syncthreads();
         if (nbi >= sub.batch_end) {
@@ -383,189 +596,16 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
             nit = s_next;
             nbi = (nit < plan.n_items) ? plan.subs[plan.items[nit].o].batch_begin : 0;
         }
-        if (nit < plan.n_items) stage_batch<T>(A, in, nit, nbi, Snext);
+        if (nit < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[nit], nbi, Snext);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         const SubbandDev so = A.sb[w.o];
-        const int TS = sub.TS, lgTS = sub.lgTS;
-        const int nout = TS * TS;
-        int E, G, g;
-        int ly[4], lx[4];
-        if (TS == 32) {
-            E = 4;
-            G = 1;
-            g = 0;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                lx[e] = t & 31;
-                ly[e] = (t >> 5) + 8 * e;
-            }
-        } else {
-            E = 1;
-            G = kTileThreads >> (2 * lgTS);
-            g = t >> (2 * lgTS);
-            const int oi = t & (nout - 1);
-            lx[0] = oi & (TS - 1);
-            ly[0] = oi >> lgTS;
-#pragma unroll
-            for (int e = 1; e < 4; ++e) {
-                lx[e] = lx[0];
-                ly[e] = ly[0];
-            }
-        }
-        const TileBatch bt = plan.batches[bi];
-        const bool last_batch = (bi + 1 == sub.batch_end);
-        const int* __restrict__ soffs = reinterpret_cast<const int*>(S) + bt.tap_soff - bt.tap_begin;
-        const T* __restrict__ svals = S + bt.val_soff - bt.tap_begin;
-        for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
-            const TilePair P = plan.pairs[pi];
-            const int lg = P.lg, r = 1 << lg, m = r - 1;
-            if (P.mode == kDown) {
-                int base[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) base[e] = ly[e] * P.PC + lx[e];
-                const int* __restrict__ to = soffs + P.tap_begin;
-                const T* __restrict__ tv = svals + P.tap_begin;
-                int j = g;
-                if (E == 4) {
-                    for (; j + 1 < P.ntap; j += 2) {
-                        const int o0 = to[j], o1 = to[j + 1];
-                        const T v0 = tv[j], v1 = tv[j + 1];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
-                    }
-                    for (; j < P.ntap; ++j) {
-                        const int o0 = to[j];
-                        const T v0 = tv[j];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
-                    }
-                } else {
-                    const T* __restrict__ Sb = S + base[0];
-                    T a0 = 0, a1 = 0;
-                    for (; j + G < P.ntap; j += 2 * G) {
-                        a0 += tv[j] * Sb[to[j]];
-                        a1 += tv[j + G] * Sb[to[j + G]];
-                    }
-                    if (j < P.ntap) a0 += tv[j] * Sb[to[j]];
-                    acc[0] += a0 + a1;
-                }
-            } else if (P.mode == kUp) {
-                const int rr = r * r;
-                const int py0 = w.ty0 >> lg, px0 = w.tx0 >> lg;
-                int base[4], ph[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int yy = w.ty0 + ly[e], xx = w.tx0 + lx[e];
-                    base[e] = ((yy >> lg) - py0) * P.PC + ((xx >> lg) - px0);
-                    ph[e] = ((yy & m) << lg) + (xx & m);
-                }
-                if (E == 1 || r <= 8) {
-                    const int* __restrict__ to = soffs + P.tap_begin + ph[0];
-                    const T* __restrict__ tv = svals + P.tap_begin + ph[0];
-                    if (E == 4) {
-                        for (int j = 0; j < P.ntap; ++j) {
-                            const int o0 = to[j * rr];
-                            const T v0 = tv[j * rr];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
-                        }
-                    } else {
-                        const T* __restrict__ Sb = S + base[0];
-                        T a0 = 0, a1 = 0;
-                        int j = g;
-                        for (; j + G < P.ntap; j += 2 * G) {
-                            a0 += tv[j * rr] * Sb[to[j * rr]];
-                            a1 += tv[(j + G) * rr] * Sb[to[(j + G) * rr]];
-                        }
-                        if (j < P.ntap) a0 += tv[j * rr] * Sb[to[j * rr]];
-                        acc[0] += a0 + a1;
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int* __restrict__ to = soffs + P.tap_begin + ph[e];
-                        const T* __restrict__ tv = svals + P.tap_begin + ph[e];
-                        for (int j = g; j < P.ntap; j += G) acc[e] += tv[j * rr] * S[to[j * rr] + base[e]];
-                    }
-                }
-            } else {
-                // gather from global memory (regions larger than the shared-memory budget)
-                const SubbandDev si = A.sb[P.in_sb];
-                const T* __restrict__ src = in + si.off;
-                const int R = si.rows, C = si.cols;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    if (e >= E) continue;
-                    const int py = w.ty0 + ly[e], px = w.tx0 + lx[e];
-                    if (py >= so.rows || px >= so.cols) continue;
-                    int by, bx, tb, step;
-                    if (P.mode == kDownGlobal) {
-                        by = py << lg;
-                        bx = px << lg;
-                        tb = P.tap_begin;
-                        step = 1;
-                    } else {
-                        by = py >> lg;
-                        bx = px >> lg;
-                        tb = P.tap_begin + (((py & m) << lg) + (px & m));
-                        step = r * r;
-                    }
-                    T a = 0;
-                    for (int j = g; j < P.ntap; j += G) {
-                        const int pk = __ldg(plan.tap_off + tb + j * step);
-                        const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
-                        a += __ldg(gvals + tb + j * step) * src[(size_t)yy * C + xx];
-                    }
-                    acc[e] += a;
-                }
-            }
-        }
-        if (last_batch && G > 1) {
-            red_buf[t] = acc[0];
-            __syncthreads();
-            if (g == 0)
-                for (int k = 1; k < G; ++k) acc[0] += red_buf[t + k * nout];
-        }
-        if (last_batch && g == 0) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                if (e >= E) continue;
-                const int py = w.ty0 + ly[e], px = w.tx0 + lx[e];
-                if (py >= so.rows || px >= so.cols) continue;
-                const size_t i = so.off + (size_t)py * so.cols + px;
-                const int mR = (1 << so.lgR) - 1;
-                const int cls = so.tab_off + ((py & mR) << so.lgR) + (px & mR);
-                if (EPI == kApply || EPI == kApplyNorm) {
-                    T v = acc[e];
-                    if (ep.scale) v = (T)((double)v * ep.scale[cls]);
-                    out[i] = v;
-                    if (EPI == kApplyNorm) {
-                        if (sizeof(T) == 8) d0 += (double)v * (double)v;
-                        else neu_add(s0, c0, (float)v * (float)v);
-                    }
-                } else if (EPI == kK1 || EPI == kResNorm) {
-                    const float xv = ep.x0[i];
-                    const float rv = (float)acc[e] - xv;
-                    out[i] = (T)rv;
-                    neu_add(s0, c0, rv * rv);
-                    if (EPI == kK1) neu_add(s1, c1, xv * rv);
-                } else if (EPI == kK2) {
-                    const float gv = (float)acc[e];
-                    const float stp = ep.step_tab[cls];
-                    const float wv = ep.w_sb[w.o];
-                    const float yv = ep.y[i], xo = ep.x[i];
-                    const float z = yv - stp * gv;
-                    const float xn = copysignf(fmaxf(fabsf(z) - stp * wv, 0.f), z);
-                    ep.x[i] = xn;
-                    ep.y[i] = xn + beta * (xn - xo);
-                    neu_add(s0, c0, wv * fabsf(yv));
-                    mx = fmaxf(mx, gw_ratio(gv, wv));
-                }
-            }
-        }
-        if (last_batch) {
+        const ThreadMap tm = thread_map(sub);
+        compute_batch<T>(plan, A.sb, in, w, so, bi, S, tm, acc);
+        if (bi + 1 == sub.batch_end) {
+            group_reduce<T>(tm, acc, red_buf);
+            epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[e] = 0;
         }
@@ -577,8 +617,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
     }
     cp_async_wait<0>();
     __syncthreads();
-    // totals (and, in the last CTA, the queue reset)
-    double v[2] = {d0 + (double)s0 + (double)c0, EPI == kK2 ? (double)mx : (double)s1 + (double)c1}, tot[2];
+    double v[2] = {pt.d0 + (double)pt.s0 + (double)pt.c0, EPI == kK2 ? (double)pt.mx : (double)pt.s1 + (double)pt.c1}, tot[2];
     const unsigned maxmask = (EPI == kK2) ? 2u : 0u;
     if (grid_reduce<2>(v, maxmask, ep.part, &A.queue->done, tot)) {
         if (t == 0) {
@@ -595,6 +634,176 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Batch of problems: one launch covers the tiles of every running problem
+// ---------------------------------------------------------------------------------------
+// Block sum of the per-thread partials of one tile, added to the problem's slots.
+template <int EPI>
+__device__ __forceinline__ void flush_partials(Partials& pt, double* sums, double* red) {
+    double a = (double)pt.s0 + (double)pt.c0;
+    double b = (EPI == kK2) ? (double)pt.mx : (double)pt.s1 + (double)pt.c1;
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        const double o = __shfl_down_sync(0xffffffffu, b, off);
+        b = (EPI == kK2) ? fmax(b, o) : b + o;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[2 * warp] = a;
+        red[2 * warp + 1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int k = 0; k < kTileThreads / 32; ++k) {
+            A += red[2 * k];
+            B = (EPI == kK2) ? fmax(B, red[2 * k + 1]) : B + red[2 * k + 1];
+        }
+        if (EPI == kK1) {
+            atomicAdd(&sums[0], A);
+            atomicAdd(&sums[1], B);
+        } else if (EPI == kK2) {
+            atomicAdd(&sums[2], A);
+            atomicMax(reinterpret_cast<unsigned long long*>(&sums[3]), (unsigned long long)__double_as_longlong(B));
+        } else {
+            atomicAdd(&sums[0], A);
+            atomicAdd(&sums[1], B);
+        }
+    }
+    pt = Partials();
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(kTileThreads) tile_batch_kernel(BatchArgs B) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* const buf0 = reinterpret_cast<float*>(smem_raw);
+    float* const buf1 = buf0 + B.buf_elems;
+    __shared__ float red_buf[kTileThreads];
+    __shared__ double red_d[2 * kTileThreads / 32];
+    __shared__ int s_next;
+    const int t = threadIdx.x;
+    // next item whose problem is still running (thread 0), broadcast through shared memory
+    auto fetch = [&]() {
+        if (t == 0) {
+            int i;
+            for (;;) {
+                i = (int)atomicAdd(&B.queue->next, 1u);
+                if (i >= B.n_items) break;
+                if (EPI == kObj || !*(volatile int*)&B.probs[B.items[i].p].st->stop) break;
+            }
+            s_next = i;
+        }
+        __syncthreads();
+        return s_next;
+    };
+    auto plan_of = [&](int p) -> const TilePlanDev& { return (EPI == kK2) ? B.probs[p].adj : B.probs[p].fwd; };
+    auto in_of = [&](int p) -> const float* {
+        const BatchProblem& P = B.probs[p];
+        return (EPI == kK1) ? P.y : (EPI == kK2) ? P.r : P.x;
+    };
+    int it = fetch();
+    int bi = 0;
+    float* S = buf0;
+    float* Snext = buf1;
+    if (it < B.n_items) {
+        const BatchItem bw = B.items[it];
+        const TilePlanDev& pl = plan_of(bw.p);
+        bi = pl.subs[pl.items[bw.item].o].batch_begin;
+        stage_batch<float>(pl, B.probs[bw.p].sb, in_of(bw.p), pl.items[bw.item], bi, S);
+    }
+    cp_async_commit();
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    Partials pt;
+    while (it < B.n_items) {
+        const BatchItem bw = B.items[it];
+        const BatchProblem& P = B.probs[bw.p];
+        const TilePlanDev& pl = plan_of(bw.p);
+        const TileItem w = pl.items[bw.item];
+        const TileSub sub = pl.subs[w.o];
+        int nit = it, nbi = bi + 1;
+        __syncthreads();
+        if (nbi >= sub.batch_end) {
+            nit = fetch();
+            if (nit < B.n_items) {
+                const BatchItem nb = B.items[nit];
+                const TilePlanDev& npl = plan_of(nb.p);
+                nbi = npl.subs[npl.items[nb.item].o].batch_begin;
+            }
+        }
+        if (nit < B.n_items) {
+            const BatchItem nb = B.items[nit];
+            const TilePlanDev& npl = plan_of(nb.p);
+            stage_batch<float>(npl, B.probs[nb.p].sb, in_of(nb.p), npl.items[nb.item], nbi, Snext);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const SubbandDev so = P.sb[w.o];
+        const ThreadMap tm = thread_map(sub);
+        compute_batch<float>(pl, P.sb, in_of(bw.p), w, so, bi, S, tm, acc);
+        if (bi + 1 == sub.batch_end) {
+            group_reduce<float>(tm, acc, red_buf);
+            EpiArgs ep{};
+            ep.x0 = P.x0;
+            ep.y = P.y;
+            ep.x = P.x;
+            ep.step_tab = P.step_tab;
+            ep.w_sb = P.w_sb;
+            float beta = 0.f;
+            if (EPI == kK2) {
+                const int k = P.st->k;
+                beta = (float)(k - 1) / (float)(k + 2);
+            }
+            epilogue<float, EPI>(w, so, tm, acc, (EPI == kK1) ? P.r : nullptr, ep, beta, pt);
+            flush_partials<EPI>(pt, P.sums, red_d);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[e] = 0.f;
+        }
+        it = nit;
+        bi = nbi;
+        float* tmp = S;
+        S = Snext;
+        Snext = tmp;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    // the last CTA resets the queue; after the step kernel it also finishes the iteration of
+    // every running problem (one thread per problem)
+    __shared__ bool s_last;
+    __threadfence();
+    if (t == 0) s_last = (atomicAdd(&B.queue->done, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (EPI == kK2) {
+        int running = 0;
+        for (int p = t; p < B.B; p += kTileThreads) {
+            const BatchProblem& P = B.probs[p];
+            SolveState* st = P.st;
+            if (!st->stop) {
+                st->rr = __ldcg(&P.sums[0]);
+                st->x0r = __ldcg(&P.sums[1]);
+                finish_iteration(st, __ldcg(&P.sums[2]), __ldcg(&P.sums[3]));
+            }
+            P.sums[0] = P.sums[1] = P.sums[2] = P.sums[3] = 0.0;
+            running += st->stop ? 0 : 1;
+        }
+        for (int off = 16; off > 0; off >>= 1) running += __shfl_down_sync(0xffffffffu, running, off);
+        __shared__ int s_run[kTileThreads / 32];
+        if ((t & 31) == 0) s_run[t >> 5] = running;
+        __syncthreads();
+        if (t == 0) {
+            int tot = 0;
+            for (int k = 0; k < kTileThreads / 32; ++k) tot += s_run[k];
+            *B.running = tot;
+        }
+    }
+    if (t == 0) {
+        B.queue->next = 0u;
+        B.queue->done = 0u;
+    }
+}
+
 template <typename T, int EPI>
 wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st) {
     static bool attr = false;
@@ -608,6 +817,19 @@ wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep
     return WDB_OK;
 }
 
+template <int EPI>
+wdb_status launch_batch(const BatchArgs& B, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        WDB_CK(cudaFuncSetAttribute(tile_batch_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    tile_batch_kernel<EPI><<<B.grid, kTileThreads, B.smem_bytes, st>>>(B);
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
 }  // namespace
 
 int tile_grid(int smem_bytes) {
@@ -616,6 +838,17 @@ int tile_grid(int smem_bytes) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(tile_kernel<float, kK2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2>, kTileThreads, smem_bytes);
+    if (sms <= 0) sms = 1;
+    if (per <= 0) per = 1;
+    return sms * per;
+}
+
+int tile_batch_grid(int smem_bytes) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(tile_batch_kernel<kK2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_batch_kernel<kK2>, kTileThreads, smem_bytes);
     if (sms <= 0) sms = 1;
     if (per <= 0) per = 1;
     return sms * per;
@@ -661,6 +894,10 @@ wdb_status tile_resnorm(const TileArgs& A, const float* x, const float* x0, floa
     ep.red_out = out;
     return launch_tile<float, kResNorm>(A, x, r, ep, st);
 }
+
+wdb_status batch_k1(const BatchArgs& B, cudaStream_t st) { return launch_batch<kK1>(B, st); }
+wdb_status batch_k2(const BatchArgs& B, cudaStream_t st) { return launch_batch<kK2>(B, st); }
+wdb_status batch_objective(const BatchArgs& B, cudaStream_t st) { return launch_batch<kObj>(B, st); }
 
 template wdb_status tile_apply<float>(const TileArgs&, const float*, float*, const double*, double*, double*,
                                       cudaStream_t);

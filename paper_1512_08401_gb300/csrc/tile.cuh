@@ -78,6 +78,7 @@ struct TilePlanHost {
     std::vector<int> tap_off;
     std::vector<float> tap_v;
     std::vector<double> tap_v64;
+    std::vector<double> item_cost;   // estimated cost of every item (items are sorted by it)
     int buf_elems = 0;
     int smem_bytes = 0;
     long long macs = 0;        // MACs per application (taps x outputs, padding included)
@@ -103,6 +104,40 @@ struct TileArgs {
     TileQueue* queue;
     int grid;
 };
+
+// One problem of a batched solve (device-resident descriptor).
+struct BatchProblem {
+    TilePlanDev fwd, adj;          // the problem's plans for Theta_K and Theta_K^T
+    const SubbandDev* sb;
+    float *y, *x, *r;              // iterates and residual (in place)
+    const float* x0;
+    const float* step_tab;         // tau / P per phase class
+    const float* w_sb;             // weights per subband
+    SolveState* st;
+    double* sums;                  // [4] accumulated by the tiles: rr, <x0,r>, sum w|y|, max |g|/w
+};
+
+struct BatchItem {                 // tile `item` of problem p's plan (the plan of the phase)
+    int p, item;
+};
+
+struct BatchArgs {
+    const BatchProblem* probs;
+    int B;
+    const BatchItem* items;        // all problems' tiles of this phase, heaviest first
+    int n_items;
+    TileQueue* queue;
+    int* running;                  // written by the last CTA of the step kernel
+    int grid;
+    int buf_elems;                 // largest staging buffer of any problem's plan
+    int smem_bytes;
+};
+
+int tile_batch_grid(int smem_bytes);
+wdb_status batch_k1(const BatchArgs& B, cudaStream_t st);
+wdb_status batch_k2(const BatchArgs& B, cudaStream_t st);
+// x -> sums[0] = ||Theta_K x - x0||^2, sums[1] = sum w|x| for every problem
+wdb_status batch_objective(const BatchArgs& B, cudaStream_t st);
 
 template <typename T>
 wdb_status tile_apply(const TileArgs& A, const T* in, T* out, const double* scale, double* norm_out,

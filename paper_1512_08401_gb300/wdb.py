@@ -73,6 +73,8 @@ _SIGS = {
     "wdb_solve": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_solve_coeffs": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_theta_objective": (i32, [vp, vp, vp, f64, pd, vp, pd]),
+    "wdb_solve_batch": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveParams), vp,
+                              C.POINTER(SolveResult)]),
     "wdb_fftop_create": (i32, [pd, i32, i32, i32, i32, C.c_char_p, i32, vp, C.POINTER(vp)]),
     "wdb_fftop_free": (None, [vp]),
     "wdb_fftop_precond": (i32, [vp, i32, f64, vp, pd, pd, pd]),
@@ -340,3 +342,21 @@ def dwt_noalloc(img, coef, n_rows, n_cols, wavelet="db4", levels=4, stream=None)
     _check(lib().wdb_dwt_noalloc(_dev(img, n_rows * n_cols), _dev(coef, n_rows * n_cols), n_rows, n_cols,
                                  wavelet.encode(), levels, _stream(stream)))
     return coef
+
+
+def solve_batch(thetas, us, xs, params_list, stream=None):
+    """Solve many problems together (one Theta handle per problem). params_list: dicts of
+    make_params keyword arguments. Returns one result dict per problem."""
+    B = len(thetas)
+    TH = (C.c_void_p * B)(*[t._h.value for t in thetas])
+    U = (C.c_void_p * B)(*[_dev(u, t.N).value for u, t in zip(us, thetas)])
+    X = (C.c_void_p * B)(*[_dev(x, t.N).value for x, t in zip(xs, thetas)])
+    keep = []
+    P = (SolveParams * B)()
+    for i, kw in enumerate(params_list):
+        p, k = make_params(**kw)
+        keep.append(k)
+        P[i] = p
+    R = (SolveResult * B)()
+    _check(lib().wdb_solve_batch(B, TH, U, X, P, _stream(stream), R))
+    return [R[i].as_dict() for i in range(B)]
