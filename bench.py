@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=20)
+    ap.add_argument("--workload", choices=["headline", "batch"], default="headline",
+                    help="batch: 256 problems of mixed size, batched solve vs a per-problem loop")
+    ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
                     help="short run for ncu: build Theta_K and the FFT operator, 30 iterations of each path")
     return ap.parse_args()
@@ -398,10 +401,72 @@ def large_study(wdb, torch, peak, peak_src):
     return res
 
 
+def run_batch(args):
+    """256 problems, sizes from {256, 512, 1024}^2, Gaussian (sigma ~ U[1,4]) or motion blur,
+    lambda log-uniform in [5e-4, 5e-3], db4 J = 5, K = 30 N, SPAI, each solved to a 1e-4
+    relative objective gap: one batched solve against a loop of single solves."""
+    import torch
+    from paper_1512_08401_gb300 import build, synthetic, wdb
+    build.build()
+    wdb.lib()
+    probs = synthetic.batch_mix(args.problems)
+    t0 = time.perf_counter()
+    th = [wdb.Theta.build(p.psf, p.u0.shape[0], p.u0.shape[1], "db4", 5, K=30 * p.u0.size) for p in probs]
+    build_s = time.perf_counter() - t0
+    us = [torch.from_numpy(p.u0.astype(np.float32).ravel()).cuda() for p in probs]
+    xs = [torch.zeros(t.N, device="cuda") for t in th]
+    # E* of every problem (long untimed batched run), targets at 1e-4 relative
+    star = wdb.solve_batch(th, us, xs, [dict(lam=p.lam, max_iters=3000, precond=PRECOND) for p in probs])
+    kw = [dict(lam=p.lam, max_iters=5000, precond=PRECOND, target_objective=r["objective"] * (1 + REL_GAP))
+          for p, r in zip(probs, star)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def timed(fn):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        start.record()
+        out = fn()
+        end.record()
+        end.synchronize()
+        return start.elapsed_time(end), out
+
+    def batched():
+        return wdb.solve_batch(th, us, xs, kw)
+
+    def loop():
+        return [t.solve(u, x, **k) for t, u, x, k in zip(th, us, xs, kw)]
+    for _ in range(args.warmup):
+        batched()
+        loop()
+    bms, bres = zip(*[timed(batched) for _ in range(args.steps)])
+    lms, lres = zip(*[timed(loop) for _ in range(args.steps)])
+    iters = [r["iters"] for r in bres[-1]]
+    bytes_iter = sum(32 * t.N for t in th)   # algorithmic bytes of one iteration of every problem
+    mean_b, mean_l = statistics.mean(bms), statistics.mean(lms)
+    sizes = {}
+    for p in probs:
+        sizes[p.u0.shape[0]] = sizes.get(p.u0.shape[0], 0) + 1
+    out = {"metric": "problems/s, batch of %d mixed-size deblurring problems to 1e-4 rel. objective gap" % len(probs),
+           "value": len(probs) / (mean_b * 1e-3), "unit": "problems/s", "higher_is_better": True, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_b, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch: sizes %s, gaussian sigma~U[1,4] or motion line, lambda log-U[5e-4,5e-3], "
+                                  "db4 J=5, K=30N, SPAI" % sizes, "l2": "flushed before each step"},
+           "loop": {"ms": mean_l, "problems_per_s": len(probs) / (mean_l * 1e-3)},
+           "speedup_batched_vs_loop": mean_l / mean_b,
+           "iters": {"min": min(iters), "max": max(iters), "mean": statistics.mean(iters)},
+           "algorithmic_GBps": sum(32 * t.N * r["iters"] for t, r in zip(th, bres[-1])) / (mean_b * 1e-3) / 1e9,
+           "build_s": build_s}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 
