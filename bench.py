@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=20)
-    ap.add_argument("--workload", choices=["headline", "batch"], default="headline",
+    ap.add_argument("--workload", choices=["headline", "batch", "large", "warm"], default="headline",
                     help="batch: 256 problems of mixed size, batched solve vs a per-problem loop")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
@@ -67,23 +67,35 @@ class Dist:
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.pg = None
+        self.nccl = False
 
     def init(self, torch):
         if self.world > 1:
             import torch.distributed as dist
-            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+            self.nccl = torch.cuda.is_available()
+            dist.init_process_group("nccl" if self.nccl else "gloo")
             self.pg = dist
 
     def barrier(self, torch):
         if self.pg:
             self.pg.barrier()
-        torch.cuda.synchronize()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
 
     def max(self, torch, v: float) -> float:
+        """Maximum of v over the ranks (a timing, so the slowest rank decides)."""
         if not self.pg:
             return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if self.nccl else "cpu")
         self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, torch, v: float) -> float:
+        """Sum of v over the ranks (units processed)."""
+        if not self.pg:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda" if self.nccl else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
         return float(t.item())
 
     def close(self):
@@ -142,22 +154,36 @@ def measured_peaks():
         return 6800.0, "of fallback"
 
 
-def traffic_record(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the sources it was
-    measured on are unchanged (else None)."""
+def kernel_sources_sha256(files) -> str:
+    """sha256 over the given csrc files (the sources a kernel is compiled from)."""
     import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1512_08401_gb300", "csrc")
+    for f in sorted(files):
+        h.update(f.encode())
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+TILE_SOURCES = ["tile.cu", "tile.cuh", "device_util.cuh", "layout_types.h", "wdb_internal.h"]
+
+
+def traffic_record(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
+    (profiles/traffic.json), if the kernel's sources are unchanged since (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
     except Exception:
         return None
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1512_08401_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
-    entry = rec.get(kernel)
-    if not entry or entry.get("csrc_sha256") != h.hexdigest():
+    entry = rec.get(workload, {}).get(kernel)
+    if not entry:
+        return None
+    try:
+        if entry.get("sources_sha256") != kernel_sources_sha256(entry["sources"]):
+            return None
+    except (KeyError, OSError):
         return None
     return entry.get("dram_bytes_per_launch")
 
@@ -313,6 +339,8 @@ def run_ours(args):
     ms_theta = d.max(torch, statistics.mean(t_ms))
     ms_fft = d.max(torch, statistics.mean(f_ms))
     ms_e2e = d.max(torch, statistics.mean(e_ms))
+    # whole-job throughput: solves of every rank over the slowest rank's timed region
+    solves_per_s = d.sum(torch, float(len(t_ms))) / (d.max(torch, sum(t_ms)) * 1e-3)
     it_theta = statistics.mean(r["iters"] for r in t_res)
     it_fft = statistics.mean(r["iters"] for r in f_res)
     k1 = statistics.mean(r["ms_k1"] for r in t_res)
@@ -327,7 +355,7 @@ def run_ours(args):
     peak, peak_src = measured_peaks()
     achieved = nbytes / (dur * 1e-3) / 1e9
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic_record(name),
+            "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic_record(name, "1024"),
             "bytes_per_launch": nbytes, "launch_ms": dur,
             "note": "1024^2 working set (~24 MB) stays in L2 across iterations; HBM bound judged at 4096^2"}
 
@@ -338,6 +366,7 @@ def run_ours(args):
                       "l2": "flushed between steps (256 MiB write)", "K_eff": th.info.K_eff,
                       "n_taps": th.info.n_taps, "tau": pc["tau"], "L_hat": pc["L_hat"]},
            "iters_to_gap": it_theta, "fista_iters_per_s": it_theta / (ms_theta * 1e-3),
+           "solves_per_s_all_ranks": solves_per_s,
            "fft_path": {"ms": ms_fft, "iters": it_fft, "iters_per_s": it_fft / (ms_fft * 1e-3),
                         "ms_gradient": statistics.mean(r["ms_k1"] for r in f_res),
                         "ms_step": statistics.mean(r["ms_k2"] for r in f_res), "tau": fpc["tau"]},
@@ -390,8 +419,10 @@ def large_study(wdb, torch, peak, peak_src):
     a1, a2 = b1 / (r["ms_k1"] * 1e-3) / 1e9, b2 / (r["ms_k2"] * 1e-3) / 1e9
     it_ms = r["solve_ms"] / max(r["iters"], 1)
     res = {"workload": "4096x4096 gaussian sigma=4 41x41, db4 J=6, K=30N, SPAI, 200 iterations",
-           "k1_residual": {"launch_ms": r["ms_k1"], "achieved": a1, "frac": a1 / peak},
-           "k2_step": {"launch_ms": r["ms_k2"], "achieved": a2, "frac": a2 / peak},
+           "k1_residual": {"launch_ms": r["ms_k1"], "achieved": a1, "frac": a1 / peak, "bytes_per_launch": b1,
+                           "traffic": traffic_record("k1_residual", "4096")},
+           "k2_step": {"launch_ms": r["ms_k2"], "achieved": a2, "frac": a2 / peak, "bytes_per_launch": b2,
+                       "traffic": traffic_record("k2_step", "4096")},
            "iteration": {"achieved": (b1 + b2) / ((r["ms_k1"] + r["ms_k2"]) * 1e-3) / 1e9,
                          "frac": (b1 + b2) / ((r["ms_k1"] + r["ms_k2"]) * 1e-3) / 1e9 / peak,
                          "wall_ms_per_iter": it_ms},
@@ -461,12 +492,105 @@ def run_batch(args):
     return 0
 
 
+def run_large_profile(args):
+    """4096 x 4096 operator (Gaussian sigma = 4 on 41 x 41, J = 6, K = 30 N) and a 3-iteration
+    solve: the small program an ncu capture of the two FISTA kernels runs."""
+    import torch
+    from paper_1512_08401_gb300 import build, synthetic, wdb
+    build.build()
+    wdb.lib()
+    prob = synthetic.large_problem()
+    n, N = 4096, 4096 * 4096
+    th = wdb.Theta.build(prob.psf, n, n, "db4", 6, K=30 * N)
+    u = torch.from_numpy(prob.u0.astype(np.float32).ravel()).cuda()
+    x = torch.zeros(N, device="cuda")
+    r = th.solve(u, x, lam=LAM, max_iters=3, precond=PRECOND, no_graph=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "ok", "workload": "4096^2 large", "n_taps": th.info.n_taps, "iters": r["iters"]}))
+    return 0
+
+
+def run_warm(args):
+    """Learned warm start (an addition to the paper): a U-Net (4 levels, 32 channels, BF16) is
+    trained on the GPU on (observation, Psi x*) pairs of one blur (256 x 256, Gaussian sigma = 2
+    on 15 x 15, lambda = 1e-3, db4 J = 5, K = 30 N, SPAI); held-out observations are then solved
+    to E*(1 + rel) from x = 0 and through wdb_solve_warm (network forward, DWT, start
+    selection, solve), and both are timed."""
+    import torch
+    from paper_1512_08401_gb300 import build, synthetic, wdb
+    from paper_1512_08401_gb300 import warmstart as ws
+    build.build()
+    wdb.lib()
+    n, J, lam = 256, 5, 1e-3
+    psf = synthetic.gaussian_psf(2.0, 15)
+    th = wdb.Theta.build(psf, n, n, "db4", J, K=30 * n * n)
+    t0 = time.perf_counter()
+    train_u = ws.observations(n, psf, args.problems * 2, config_id=50)
+    U = ws._stack(train_u)
+    T = ws.solution_images(th, train_u, lam, iters=400)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    net = wdb.WarmStartNet(4, 32, n, n, max_batch=16, seed=0)
+    log = ws.train(net, U, T, steps=1000, batch=16, lr=1e-3)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    x = torch.zeros(n * n, device="cuda")
+
+    def timed(fn):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        start.record()
+        out = fn()
+        end.record()
+        end.synchronize()
+        return start.elapsed_time(end), out
+
+    rows = {1e-3: [], 1e-4: []}
+    starts = []
+    for u0 in ws.observations(n, psf, 16, config_id=51):
+        u = ws._stack([u0]).view(-1)
+        E = ws.reference_objective(th, u, lam)
+        for rel in rows:
+            kw = dict(lam=lam, max_iters=5000, precond=PRECOND, target_objective=E * (1 + rel))
+            for _ in range(args.warmup):
+                th.solve(u, x, **kw)
+                net.solve_warm(th, u, x, **kw)
+            c_ms, c = timed(lambda: th.solve(u, x, **kw))
+            w_ms, (w, used) = timed(lambda: net.solve_warm(th, u, x, **kw))
+            starts.append(used)
+            rows[rel].append((c_ms, c["first_primal_below"] or c["iters"], w_ms, w["first_primal_below"] or w["iters"],
+                              abs(w["objective"] - c["objective"]) / c["objective"]))
+    V = torch.empty(1, n, n, device="cuda")
+    u1 = U[:1].contiguous()
+    f_ms = statistics.mean(timed(lambda: net.forward(u1, V))[0] for _ in range(10))
+    res = {}
+    for rel, r in rows.items():
+        res[f"rel_{rel:g}"] = {"cold_ms": statistics.mean(a[0] for a in r), "cold_iters": statistics.mean(a[1] for a in r),
+                               "warm_ms": statistics.mean(a[2] for a in r), "warm_iters": statistics.mean(a[3] for a in r),
+                               "max_rel_objective_diff": max(a[4] for a in r)}
+    out = {"metric": "iterations and ms to E*(1+rel), warm start vs cold, 256^2", "value": res["rel_0.0001"]["warm_ms"],
+           "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": 16, "warmup": args.warmup,
+           "dtype": "bf16 network / f32 solver", "data": "synthetic",
+           "config": {"workload": "256x256 gaussian sigma=2 15x15, lambda=1e-3, db4 J=5, K=30N, SPAI; U-Net L=4 C=32; "
+                                  f"{len(train_u)} training pairs (x* after 400 iterations), 1000 Adam steps of 16",
+                      "l2": "flushed before each timed solve"},
+           "results": res, "network_forward_ms": f_ms, "train_s": log.seconds, "pairs_s": gen_s,
+           "train_loss": {"first": float(np.mean(log.losses[:5])), "last": float(np.mean(log.losses[-20:]))},
+           "starts_used": {str(k): starts.count(k) for k in (0, 1, 2)}}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "large":
+        return run_large_profile(args)
+    if args.workload == "warm":
+        return run_warm(args)
     return run_ours(args)
 
 

@@ -231,6 +231,47 @@ wdb_status wdb_dwt_noalloc(const float* img_dev, float* coef_dev, int n_rows, in
 wdb_status wdb_wavelet_filters(const char* wavelet, int cap, double* h_host, double* g_host,
                                int* taps);
 
+/* ---- Learned warm start (an addition to the paper's method) ----
+ * A U-Net v = u + N(u) maps a blurred image u to an image whose wavelet coefficients
+ * x_init = Psi* v start FISTA (wdb_solve_params.x_init_dev); with a good start Algorithm 3
+ * reaches its stopping rule in fewer iterations, and the solver's own stop keeps the result
+ * the minimiser of the same problem. Architecture: `levels` resolutions, `channels` (<= 32)
+ * feature maps, periodic 3x3 convolutions with bias and ReLU, 2x2 average pooling down,
+ * nearest 2x upsampling plus skip addition up; the output convolution is added to u.
+ * Storage: BF16 activations and weights, FP32 accumulation, FP32 master weights, gradients
+ * and Adam moments. Images are [B][height][width] FP32 in device memory.
+ * Parameter vector (FP32, host): per convolution W as [C_out][C_in][3][3] then b, in the
+ * order in, e0, e1a, e1b, ..., e(L-1)a, e(L-1)b, d(L-2)a, d(L-2)b, ..., d0a, d0b, out.
+ * height and width must be divisible by 2^(levels-1); 1 <= B <= max_batch. */
+typedef struct wdb_cnn wdb_cnn;
+wdb_status wdb_cnn_create(int levels, int channels, int height, int width, int max_batch,
+                          unsigned long long seed, void* stream, wdb_cnn** out);
+void wdb_cnn_free(wdb_cnn* net);
+long long wdb_cnn_num_params(const wdb_cnn* net);
+/* Replace the FP32 parameters (count = wdb_cnn_num_params) and reset the Adam state. */
+wdb_status wdb_cnn_set_params(wdb_cnn* net, const float* params_host, long long count, void* stream);
+wdb_status wdb_cnn_get_params(const wdb_cnn* net, float* params_host, long long cap);
+/* v_dev = network(u_dev), both [B][height][width]. */
+wdb_status wdb_cnn_forward(wdb_cnn* net, const float* u_dev, float* v_dev, int B, void* stream);
+/* loss = mean((network(u) - target)^2) (FP64 reduction); grad_host (may be NULL) receives
+ * the FP32 gradient of every parameter. Synchronises `stream`. */
+wdb_status wdb_cnn_loss_grad(wdb_cnn* net, const float* u_dev, const float* target_dev, int B,
+                             void* stream, double* loss_host, float* grad_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on that loss. */
+wdb_status wdb_cnn_train_step(wdb_cnn* net, const float* u_dev, const float* target_dev, int B,
+                              double lr, void* stream, double* loss_host);
+/* Checkpoint: shape, step count, seed, parameters and Adam moments. */
+wdb_status wdb_cnn_save(const wdb_cnn* net, const char* path);
+wdb_status wdb_cnn_load(const char* path, void* stream, wdb_cnn** out);
+/* wdb_solve started from the network: of x = 0 (the cold start), x = Psi* network(u) and
+ * x = Psi* u, the one with the lowest objective E starts FISTA; *start_used (may be NULL)
+ * reports it as 0, 1 or 2. The network must have the operator's image size and
+ * params->x_init_dev must be NULL. The stopping rule is the caller's, so the result solves
+ * the same problem as wdb_solve. Synchronises `stream`. */
+wdb_status wdb_solve_warm(wdb_theta* th, wdb_cnn* net, const float* u_dev, float* x_dev,
+                          const wdb_solve_params* params, void* stream, wdb_solve_result* result,
+                          int* start_used);
+
 /* ---- Diagnostics ---- */
 const char* wdb_status_str(wdb_status s);
 const char* wdb_last_error(void);

@@ -108,8 +108,14 @@ def up2_backward(d):
 # network
 # ---------------------------------------------------------------------------------------
 
-def forward(p: dict, u: np.ndarray, levels: int):
-    """u: [B, H, W] -> (v [B, H, W], cache)."""
+def forward(p: dict, u: np.ndarray, levels: int, store=None):
+    """u: [B, H, W] -> (v [B, H, W], cache).
+
+    `store`, if given, is applied to every intermediate feature map as it is stored (all of
+    them except the input u and the output v); it lets a test evaluate the network with
+    feature maps held in a lower precision, so that ReLU decisions are taken on the same
+    values as in an implementation that stores them that way. None keeps FP64."""
+    S = (lambda t: t) if store is None else store
     x = u[:, None, :, :].astype(np.float64)
     cache = {"u": x}
     enc = []
@@ -118,17 +124,17 @@ def forward(p: dict, u: np.ndarray, levels: int):
             inp = x
             wa, ba, wb, bb = p["in.W"], p["in.b"], p["e0.W"], p["e0.b"]
         else:
-            inp = avgpool2(enc[-1])
+            inp = S(avgpool2(enc[-1]))
             wa, ba, wb, bb = p[f"e{l}a.W"], p[f"e{l}a.b"], p[f"e{l}b.W"], p[f"e{l}b.b"]
-        a = np.maximum(conv(inp, wa, ba), 0.0)
-        e = np.maximum(conv(a, wb, bb), 0.0)
+        a = S(np.maximum(conv(inp, wa, ba), 0.0))
+        e = S(np.maximum(conv(a, wb, bb), 0.0))
         cache[f"enc{l}"] = (inp, a, e)
         enc.append(e)
     d = enc[-1]
     for l in range(levels - 2, -1, -1):
-        s = up2(d) + enc[l]
-        a = np.maximum(conv(s, p[f"d{l}a.W"], p[f"d{l}a.b"]), 0.0)
-        d = np.maximum(conv(a, p[f"d{l}b.W"], p[f"d{l}b.b"]), 0.0)
+        s = S(up2(d) + enc[l])
+        a = S(np.maximum(conv(s, p[f"d{l}a.W"], p[f"d{l}a.b"]), 0.0))
+        d = S(np.maximum(conv(a, p[f"d{l}b.W"], p[f"d{l}b.b"]), 0.0))
         cache[f"dec{l}"] = (s, a, d)
     v = x + conv(d, p["out.W"], p["out.b"])
     cache["d0"] = d
@@ -163,9 +169,9 @@ def backward(p: dict, cache: dict, dv: np.ndarray, levels: int) -> dict:
     return g
 
 
-def loss_and_grads(p: dict, u: np.ndarray, target: np.ndarray, levels: int):
-    """MSE loss (mean over every element) and its parameter gradients."""
-    v, cache = forward(p, u, levels)
+def loss_and_grads(p: dict, u: np.ndarray, target: np.ndarray, levels: int, store=None):
+    """MSE loss (mean over every element) and its parameter gradients (`store` as in forward)."""
+    v, cache = forward(p, u, levels, store)
     diff = v - target
     loss = float(np.mean(diff * diff))
     dv = 2.0 * diff / diff.size

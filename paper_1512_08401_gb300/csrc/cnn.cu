@@ -1,0 +1,791 @@
+// Warm-start network (an addition to the paper's method): a small U-Net that maps a blurred
+// image u to an image v whose wavelet coefficients start FISTA. Forward, backward and Adam
+// run in the kernels below: BF16 activations and weights, FP32 accumulation, FP32 master
+// weights, gradients and Adam moments.
+//
+// Network (levels L, channels C <= 32, periodic 3x3 convolutions, bias everywhere):
+//   enc 0:   a = relu(conv(u)); e_0 = relu(conv(a))
+//   enc l>0: p = avgpool2(e_{l-1}); a = relu(conv(p)); e_l = relu(conv(a))
+//   dec l = L-2..0 (d_{L-1} = e_{L-1}): s = up2(d_{l+1}) + e_l; a = relu(conv(s)); d_l = relu(conv(a))
+//   v = u + conv(d_0)
+// Loss: mean of (v - target)^2. The flat parameter vector lists, per convolution, W
+// ([C_out][C_in][3][3]) then b, in the order: in, e0, e1a, e1b, ..., d(L-2)a, d(L-2)b, ...,
+// d0a, d0b, out.
+//
+// Convolution kernel: one CTA per 16 x 16 output tile of one image; the input tile with its
+// one-pixel periodic halo and the CTA's weights are staged in shared memory; every thread
+// accumulates all output channels of one pixel. The data gradient is the same kernel with
+// flipped, transposed weights. The weight gradient keeps a thread's 36 (c_out, c_in, tap)
+// sums in registers and slides along image rows held in registers.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device_util.cuh"
+#include "wdb_internal.h"
+
+namespace wdb {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int kT = 16;          // tile side
+constexpr int kHalo = kT + 2;
+constexpr int kCMax = 32;
+
+__device__ __forceinline__ float ld(const bf16* p, size_t i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ float ld(const float* p, size_t i) { return p[i]; }
+
+// out mode: 0 store BF16, 1 store FP32, 2 add into FP32
+template <int COMAX, typename TIN>
+__global__ void __launch_bounds__(256) conv3x3_kernel(const TIN* __restrict__ in, int CI, int CO, int H, int W,
+                                                      const bf16* __restrict__ wt, const float* __restrict__ bias,
+                                                      int out_mode, void* out, int relu,
+                                                      const bf16* __restrict__ mask, const float* __restrict__ residual) {
+    extern __shared__ __align__(16) float sm[];
+    float* S = sm;                          // [CI][18][18]
+    float* Wsm = sm + CI * kHalo * kHalo;   // [CI*9][COMAX]
+    const int t = threadIdx.x;
+    const int b = blockIdx.z;
+    const int ty0 = blockIdx.y * kT, tx0 = blockIdx.x * kT;
+    const size_t plane = (size_t)H * W;
+    const int nw = CO * CI * 9;
+    for (int i = t; i < CI * 9 * COMAX; i += 256) Wsm[i] = 0.f;
+    __syncthreads();
+    for (int i = t; i < nw; i += 256) {
+        const int co = i / (CI * 9), rest = i - co * CI * 9;
+        Wsm[rest * COMAX + co] = __bfloat162float(wt[i]);
+    }
+    const TIN* inb = in + (size_t)b * CI * plane;
+    for (int i = t; i < CI * kHalo * kHalo; i += 256) {
+        const int ci = i / (kHalo * kHalo), r = i - ci * kHalo * kHalo;
+        const int y = r / kHalo, x = r - y * kHalo;
+        int gy = (ty0 + y - 1) % H, gx = (tx0 + x - 1) % W;
+        gy += gy < 0 ? H : 0;
+        gx += gx < 0 ? W : 0;
+        S[i] = ld(inb, (size_t)ci * plane + (size_t)gy * W + gx);
+    }
+    __syncthreads();
+    const int py = t / kT, px = t - py * kT;
+    const int oy = ty0 + py, ox = tx0 + px;
+    float acc[COMAX];
+#pragma unroll
+    for (int co = 0; co < COMAX; ++co) acc[co] = (bias && co < CO) ? bias[co] : 0.f;
+    for (int ci = 0; ci < CI; ++ci) {
+        const float* s = S + ci * kHalo * kHalo + py * kHalo + px;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                const float xv = s[ky * kHalo + kx];
+                const float* w = Wsm + (ci * 9 + ky * 3 + kx) * COMAX;
+                if (COMAX % 4 == 0) {
+#pragma unroll
+                    for (int co = 0; co < COMAX; co += 4) {
+                        const float4 w4 = *reinterpret_cast<const float4*>(w + co);
+                        acc[co] += w4.x * xv;
+                        acc[co + 1] += w4.y * xv;
+                        acc[co + 2] += w4.z * xv;
+                        acc[co + 3] += w4.w * xv;
+                    }
+                } else {
+#pragma unroll
+                    for (int co = 0; co < COMAX; ++co) acc[co] += w[co] * xv;
+                }
+            }
+    }
+    if (oy >= H || ox >= W) return;
+    const size_t pix = (size_t)oy * W + ox;
+#pragma unroll
+    for (int co = 0; co < COMAX; ++co) {
+        if (co >= CO) break;
+        float v = acc[co];
+        if (relu) v = fmaxf(v, 0.f);
+        const size_t o = ((size_t)b * CO + co) * plane + pix;
+        if (mask && !(__bfloat162float(mask[o]) > 0.f)) v = 0.f;
+        if (residual) v += residual[(size_t)b * plane + pix];
+        if (out_mode == 0) reinterpret_cast<bf16*>(out)[o] = __float2bfloat16(v);
+        else if (out_mode == 1) reinterpret_cast<float*>(out)[o] = v;
+        else reinterpret_cast<float*>(out)[o] += v;
+    }
+}
+
+// dW[co][ci][k] += sum_{b,p} dout[b][co][p] in[b][ci][p + k - 1]; db[co] += sum dout[b][co][p].
+// Thread t owns c_out = t / 8 and c_in = 4 (t % 8) .. + 3, all 9 taps (36 sums).
+template <typename TIN>
+__global__ void __launch_bounds__(256) wgrad_kernel(const TIN* __restrict__ in, int CI, int CO, int H, int W, int B,
+                                                    const float* __restrict__ dout, float* dW, float* db) {
+    extern __shared__ __align__(16) float sm[];
+    float* S = sm;                             // [CI][18][18]
+    float* D = sm + kCMax * kHalo * kHalo;     // [CO][16][16]
+    const int t = threadIdx.x;
+    const int co = t >> 3, ci0 = (t & 7) * 4;
+    float acc[4][9];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) acc[c][k] = 0.f;
+    float bsum = 0.f;
+    const int tx = (W + kT - 1) / kT, ty = (H + kT - 1) / kT;
+    const int tiles = B * tx * ty;
+    const size_t plane = (size_t)H * W;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int b = tile / (tx * ty), r = tile - b * tx * ty;
+        const int ty0 = (r / tx) * kT, tx0 = (r % tx) * kT;
+        const TIN* inb = in + (size_t)b * CI * plane;
+        for (int i = t; i < CI * kHalo * kHalo; i += 256) {
+            const int c = i / (kHalo * kHalo), q = i - c * kHalo * kHalo;
+            const int y = q / kHalo, x = q - y * kHalo;
+            int gy = (ty0 + y - 1) % H, gx = (tx0 + x - 1) % W;
+            gy += gy < 0 ? H : 0;
+            gx += gx < 0 ? W : 0;
+            S[i] = ld(inb, (size_t)c * plane + (size_t)gy * W + gx);
+        }
+        for (int i = t; i < CO * kT * kT; i += 256) {
+            const int c = i / (kT * kT), q = i - c * kT * kT;
+            const int y = ty0 + q / kT, x = tx0 + (q % kT);
+            D[i] = (y < H && x < W) ? dout[((size_t)b * CO + c) * plane + (size_t)y * W + x] : 0.f;
+        }
+        __syncthreads();
+        if (co < CO) {
+            for (int py = 0; py < kT; ++py) {
+                float d[kT];
+#pragma unroll
+                for (int px = 0; px < kT; ++px) d[px] = D[(co * kT + py) * kT + px];
+                if ((t & 7) == 0) {
+#pragma unroll
+                    for (int px = 0; px < kT; ++px) bsum += d[px];
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (ci0 + c >= CI) break;
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky) {
+                        float row[kHalo];
+                        const float* sr = S + ((ci0 + c) * kHalo + py + ky) * kHalo;
+#pragma unroll
+                        for (int x = 0; x < kHalo; ++x) row[x] = sr[x];
+#pragma unroll
+                        for (int kx = 0; kx < 3; ++kx) {
+                            float a = 0.f;
+#pragma unroll
+                            for (int px = 0; px < kT; ++px) a += d[px] * row[px + kx];
+                            acc[c][ky * 3 + kx] += a;
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (co < CO) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (ci0 + c >= CI) break;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) atomicAdd(&dW[((size_t)co * CI + ci0 + c) * 9 + k], acc[c][k]);
+        }
+        if ((t & 7) == 0) atomicAdd(&db[co], bsum);
+    }
+}
+
+// Wt[ci][co][8-k] = W[co][ci][k] (data gradient weights)
+__global__ void flip_transpose_kernel(const bf16* __restrict__ w, bf16* __restrict__ wt, int CO, int CI) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= CO * CI * 9) return;
+    const int co = i / (CI * 9), r = i - co * CI * 9, ci = r / 9, k = r - ci * 9;
+    wt[((size_t)ci * CO + co) * 9 + (8 - k)] = w[i];
+}
+
+template <typename TIN>
+__global__ void avgpool2_kernel(const TIN* __restrict__ in, bf16* __restrict__ out, int BC, int H, int W) {
+    const size_t n = (size_t)BC * (H / 2) * (W / 2);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % (W / 2));
+        const size_t q = i / (W / 2);
+        const int y = (int)(q % (H / 2));
+        const size_t c = q / (H / 2);
+        const TIN* p = in + c * H * W + (size_t)(2 * y) * W + 2 * x;
+        out[i] = __float2bfloat16(0.25f * (ld(p, 0) + ld(p, 1) + ld(p, W) + ld(p, W + 1)));
+    }
+}
+
+// s = up2(d) + e  (d at half resolution)
+__global__ void up2_add_kernel(const bf16* __restrict__ d, const bf16* __restrict__ e, bf16* __restrict__ s, int BC,
+                               int H, int W) {
+    const size_t n = (size_t)BC * H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W);
+        const size_t q = i / W;
+        const int y = (int)(q % H);
+        const size_t c = q / H;
+        s[i] = __float2bfloat16(__bfloat162float(d[c * (H / 2) * (W / 2) + (size_t)(y / 2) * (W / 2) + x / 2]) +
+                                __bfloat162float(e[i]));
+    }
+}
+
+// gradient into d_{l+1}: sum over every 2 x 2 block of ds (half-resolution output, overwritten)
+__global__ void up2_backward_kernel(const float* __restrict__ ds, float* __restrict__ dd, int BC, int H, int W) {
+    const size_t n = (size_t)BC * (H / 2) * (W / 2);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % (W / 2));
+        const size_t q = i / (W / 2);
+        const int y = (int)(q % (H / 2));
+        const size_t c = q / (H / 2);
+        const float* p = ds + c * H * W + (size_t)(2 * y) * W + 2 * x;
+        dd[i] = p[0] + p[1] + p[W] + p[W + 1];
+    }
+}
+
+// gradient of avgpool2: add 1/4 of the half-resolution gradient to every pixel of its block
+__global__ void avgpool2_backward_add_kernel(const float* __restrict__ dp, float* __restrict__ dx, int BC, int H, int W) {
+    const size_t n = (size_t)BC * H * W;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % W);
+        const size_t q = i / W;
+        const int y = (int)(q % H);
+        const size_t c = q / H;
+        dx[i] += 0.25f * dp[c * (H / 2) * (W / 2) + (size_t)(y / 2) * (W / 2) + x / 2];
+    }
+}
+
+// g = g * (act > 0)
+__global__ void relu_mask_kernel(float* __restrict__ g, const bf16* __restrict__ act, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(act[i]) > 0.f)) g[i] = 0.f;
+}
+
+// dv = 2 (v - t) / n; loss partial sums (FP64 tree)
+__global__ void __launch_bounds__(256) mse_kernel(const float* __restrict__ v, const float* __restrict__ tgt,
+                                                  float* __restrict__ dv, size_t n, double* part, unsigned int* counter,
+                                                  double* out) {
+    float s = 0.f, c = 0.f;
+    const float scale = 2.0f / (float)n;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float d = v[i] - tgt[i];
+        dv[i] = scale * d;
+        neu_add(s, c, d * d);
+    }
+    double a[1] = {(double)s + (double)c}, tot[1];
+    if (grid_reduce<1>(a, 0u, part, counter, tot) && threadIdx.x == 0) out[0] = tot[0] / (double)n;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, bf16* __restrict__ pb, long long n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        p[i] = pi;
+        pb[i] = __float2bfloat16(pi);
+    }
+}
+
+__global__ void to_bf16_kernel(const float* __restrict__ p, bf16* __restrict__ pb, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        pb[i] = __float2bfloat16(p[i]);
+}
+
+// splitmix64 + Box-Muller normal numbers (He initialisation of the weights)
+__global__ void init_normal_kernel(float* __restrict__ p, long long n, unsigned long long seed, float std) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z[2];
+        for (int k = 0; k < 2; ++k) {
+            unsigned long long s = seed + (unsigned long long)(2 * i + k + 1) * 0x9E3779B97F4A7C15ull;
+            s = (s ^ (s >> 30)) * 0xBF58476D1CE4E5B9ull;
+            s = (s ^ (s >> 27)) * 0x94D049BB133111EBull;
+            z[k] = s ^ (s >> 31);
+        }
+        const double u1 = ((double)(z[0] >> 11) + 1.0) * 0x1.0p-53, u2 = (double)(z[1] >> 11) * 0x1.0p-53;
+        p[i] = (float)(std * sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+    }
+}
+
+int ew(long long n) { return (int)std::max<long long>(1, std::min<long long>((n + 255) / 256, 4096)); }
+
+}  // namespace
+}  // namespace wdb
+
+using namespace wdb;
+
+struct ConvLayer {
+    int ci, co;
+    long long w_off, b_off;     // offsets in the flat parameter vector
+};
+
+struct wdb_cnn {
+    int L = 4, C = 32, H = 0, W = 0, Bmax = 0;
+    std::vector<ConvLayer> convs;   // order of the flat vector
+    long long n_params = 0;
+    long long step = 0;
+    unsigned long long seed = 0;
+    std::vector<void*> allocs;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // FP32 master, grad, Adam moments
+    bf16 *pb = nullptr, *wt = nullptr;                              // BF16 weights, flipped copy
+    // activations (BF16) per level: inp (l > 0), a, e; decoder s, a, d
+    std::vector<bf16*> e_inp, e_a, e_e, d_s, d_a, d_d;
+    std::vector<float*> g_enc;          // gradient accumulators of e_l (FP32)
+    float *g0 = nullptr, *g1 = nullptr, *g2 = nullptr;   // scratch gradients at full resolution
+    float* dv = nullptr;
+    double* part = nullptr;
+    unsigned int* counter = nullptr;
+    double* d_loss = nullptr;
+};
+
+namespace {
+
+template <typename T>
+wdb_status cnn_alloc(wdb_cnn* n, T** p, size_t count) {
+    void* q = nullptr;
+    WDB_CK(cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T)));
+    n->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return WDB_OK;
+}
+
+int lvl_h(const wdb_cnn* n, int l) { return n->H >> l; }
+int lvl_w(const wdb_cnn* n, int l) { return n->W >> l; }
+
+// conv layer index in the flat order
+int idx_in() { return 0; }
+int idx_e0() { return 1; }
+int idx_ea(int l) { return 2 + 2 * (l - 1); }
+int idx_eb(int l) { return 3 + 2 * (l - 1); }
+int idx_da(const wdb_cnn* n, int l) { return 2 * n->L + 2 * (n->L - 2 - l); }
+int idx_db(const wdb_cnn* n, int l) { return 2 * n->L + 2 * (n->L - 2 - l) + 1; }
+int idx_out(const wdb_cnn* n) { return (int)n->convs.size() - 1; }
+
+size_t conv_smem(int CI, int COMAX) { return sizeof(float) * (size_t)(CI * kHalo * kHalo + CI * 9 * COMAX); }
+
+template <typename TIN>
+wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int out_mode, void* out, int relu,
+                const bf16* mask, const float* residual, bool flipped, cudaStream_t st) {
+    const ConvLayer& cl = n->convs[layer];
+    const int CI = flipped ? cl.co : cl.ci, CO = flipped ? cl.ci : cl.co;
+    const int H = lvl_h(n, l), W = lvl_w(n, l);
+    const bf16* w = n->pb + cl.w_off;
+    if (flipped) {
+        flip_transpose_kernel<<<(cl.co * cl.ci * 9 + 255) / 256, 256, 0, st>>>(w, n->wt, cl.co, cl.ci);
+        count_launch();
+        w = n->wt;
+    }
+    const float* bias = flipped ? nullptr : n->p + cl.b_off;
+    dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT, B);
+    if (CO <= 1) {
+        conv3x3_kernel<1, TIN><<<grid, 256, conv_smem(CI, 1), st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
+                                                                     mask, residual);
+    } else {
+        static bool attr = false;
+        if (!attr) {
+            WDB_CK(cudaFuncSetAttribute(conv3x3_kernel<32, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)conv_smem(32, 32)));
+            WDB_CK(cudaFuncSetAttribute(conv3x3_kernel<32, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)conv_smem(32, 32)));
+            attr = true;
+        }
+        conv3x3_kernel<32, TIN><<<grid, 256, conv_smem(CI, 32), st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
+                                                                       mask, residual);
+    }
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
+template <typename TIN>
+wdb_status wgrad(const wdb_cnn* n, int layer, const TIN* in, const float* dout, int B, int l, cudaStream_t st) {
+    const ConvLayer& cl = n->convs[layer];
+    static bool attr = false;
+    const size_t smem = sizeof(float) * (size_t)(kCMax * kHalo * kHalo + kCMax * kT * kT);
+    if (!attr) {
+        WDB_CK(cudaFuncSetAttribute(wgrad_kernel<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        WDB_CK(cudaFuncSetAttribute(wgrad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    const int H = lvl_h(n, l), W = lvl_w(n, l);
+    const int tiles = B * ((H + kT - 1) / kT) * ((W + kT - 1) / kT);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = std::max(1, std::min(tiles, 2 * std::max(sms, 1)));
+    wgrad_kernel<TIN><<<grid, 256, smem, st>>>(in, cl.ci, cl.co, H, W, B, dout, n->g + cl.w_off, n->g + cl.b_off);
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
+wdb_status forward(wdb_cnn* n, const float* u, float* v_out, int B, cudaStream_t st) {
+    const int L = n->L, C = n->C;
+    for (int l = 0; l < L; ++l) {
+        const int H = lvl_h(n, l), W = lvl_w(n, l);
+        if (l == 0) {
+            WDB_TRY(conv<float>(n, idx_in(), u, B, 0, 0, n->e_a[0], 1, nullptr, nullptr, false, st));
+            WDB_TRY(conv<bf16>(n, idx_e0(), n->e_a[0], B, 0, 0, n->e_e[0], 1, nullptr, nullptr, false, st));
+        } else {
+            avgpool2_kernel<bf16><<<ew((long long)B * C * H * W), 256, 0, st>>>(n->e_e[l - 1], n->e_inp[l], B * C,
+                                                                              2 * H, 2 * W);
+            count_launch();
+            WDB_TRY(conv<bf16>(n, idx_ea(l), n->e_inp[l], B, l, 0, n->e_a[l], 1, nullptr, nullptr, false, st));
+            WDB_TRY(conv<bf16>(n, idx_eb(l), n->e_a[l], B, l, 0, n->e_e[l], 1, nullptr, nullptr, false, st));
+        }
+    }
+    const bf16* d = n->e_e[L - 1];
+    for (int l = L - 2; l >= 0; --l) {
+        const int H = lvl_h(n, l), W = lvl_w(n, l);
+        up2_add_kernel<<<ew((long long)B * C * H * W), 256, 0, st>>>(d, n->e_e[l], n->d_s[l], B * C, H, W);
+        count_launch();
+        WDB_TRY(conv<bf16>(n, idx_da(n, l), n->d_s[l], B, l, 0, n->d_a[l], 1, nullptr, nullptr, false, st));
+        WDB_TRY(conv<bf16>(n, idx_db(n, l), n->d_a[l], B, l, 0, n->d_d[l], 1, nullptr, nullptr, false, st));
+        d = n->d_d[l];
+    }
+    // v = u + conv(d_0)
+    WDB_TRY(conv<bf16>(n, idx_out(n), d, B, 0, 1, v_out, 0, nullptr, u, false, st));
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
+// d_0 of a 1-level network is e_0
+const bf16* d0_of(const wdb_cnn* n) { return n->L >= 2 ? n->d_d[0] : n->e_e[0]; }
+
+wdb_status backward(wdb_cnn* n, const float* u, int B, cudaStream_t st) {
+    const int L = n->L, C = n->C;
+    const long long full = (long long)B * C * n->H * n->W;
+    WDB_CK(cudaMemsetAsync(n->g, 0, sizeof(float) * n->n_params, st));
+    for (int l = 0; l < L; ++l)
+        WDB_CK(cudaMemsetAsync(n->g_enc[l], 0, sizeof(float) * (size_t)B * C * lvl_h(n, l) * lvl_w(n, l), st));
+    // output convolution
+    WDB_TRY(wgrad<bf16>(n, idx_out(n), d0_of(n), n->dv, B, 0, st));
+    float* dd = n->g0;   // gradient of d_0
+    WDB_TRY(conv<float>(n, idx_out(n), n->dv, B, 0, 1, dd, 0, nullptr, nullptr, true, st));
+    // decoder, level 0 upwards
+    for (int l = 0; l < L - 1; ++l) {
+        const long long cnt = (long long)B * C * lvl_h(n, l) * lvl_w(n, l);
+        relu_mask_kernel<<<ew(cnt), 256, 0, st>>>(dd, n->d_d[l], cnt);
+        count_launch();
+        WDB_TRY(wgrad<bf16>(n, idx_db(n, l), n->d_a[l], dd, B, l, st));
+        float* da = n->g1;
+        WDB_TRY(conv<float>(n, idx_db(n, l), dd, B, l, 1, da, 0, n->d_a[l], nullptr, true, st));
+        WDB_TRY(wgrad<bf16>(n, idx_da(n, l), n->d_s[l], da, B, l, st));
+        float* ds = n->g2;
+        WDB_TRY(conv<float>(n, idx_da(n, l), da, B, l, 1, ds, 0, nullptr, nullptr, true, st));
+        // s = up2(d_{l+1}) + e_l
+        WDB_CK(cudaMemcpyAsync(n->g_enc[l], ds, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
+        up2_backward_kernel<<<ew(cnt / 4), 256, 0, st>>>(ds, n->g0, B * C, lvl_h(n, l), lvl_w(n, l));
+        count_launch();
+        dd = n->g0;
+    }
+    // d_{L-1} = e_{L-1}
+    const long long cb = (long long)B * C * lvl_h(n, L - 1) * lvl_w(n, L - 1);
+    if (L >= 2) {
+        float* ge = n->g_enc[L - 1];
+        WDB_CK(cudaMemcpyAsync(ge, dd, sizeof(float) * cb, cudaMemcpyDeviceToDevice, st));
+    } else {
+        WDB_CK(cudaMemcpyAsync(n->g_enc[0], dd, sizeof(float) * cb, cudaMemcpyDeviceToDevice, st));
+    }
+    // encoder, bottom level first
+    for (int l = L - 1; l >= 0; --l) {
+        const long long cnt = (long long)B * C * lvl_h(n, l) * lvl_w(n, l);
+        float* dz = n->g_enc[l];
+        relu_mask_kernel<<<ew(cnt), 256, 0, st>>>(dz, n->e_e[l], cnt);
+        count_launch();
+        const int la = (l == 0) ? idx_in() : idx_ea(l), lb = (l == 0) ? idx_e0() : idx_eb(l);
+        WDB_TRY(wgrad<bf16>(n, lb, n->e_a[l], dz, B, l, st));
+        float* da = n->g1;
+        WDB_TRY(conv<float>(n, lb, dz, B, l, 1, da, 0, n->e_a[l], nullptr, true, st));
+        if (l == 0) {
+            WDB_TRY(wgrad<float>(n, la, u, da, B, 0, st));
+        } else {
+            WDB_TRY(wgrad<bf16>(n, la, n->e_inp[l], da, B, l, st));
+            float* dp = n->g2;
+            WDB_TRY(conv<float>(n, la, da, B, l, 1, dp, 0, nullptr, nullptr, true, st));
+            avgpool2_backward_add_kernel<<<ew(cnt * 4), 256, 0, st>>>(dp, n->g_enc[l - 1], B * C, 2 * lvl_h(n, l),
+                                                                      2 * lvl_w(n, l));
+            count_launch();
+        }
+    }
+    (void)full;
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
+wdb_status loss(wdb_cnn* n, const float* v, const float* tgt, int B, cudaStream_t st, double* out) {
+    const size_t cnt = (size_t)B * n->H * n->W;
+    WDB_CK(cudaMemsetAsync(n->counter, 0, sizeof(unsigned int), st));
+    mse_kernel<<<std::min(ew((long long)cnt), 1024), 256, 0, st>>>(v, tgt, n->dv, cnt, n->part, n->counter, n->d_loss);
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    WDB_CK(cudaMemcpyAsync(out, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    WDB_CK(cudaStreamSynchronize(st));
+    return WDB_OK;
+}
+
+void cnn_release(wdb_cnn* n) {
+    if (!n) return;
+    for (void* p : n->allocs) cudaFree(p);
+    delete n;
+}
+
+constexpr char kMagicCnn[8] = {'W', 'D', 'B', 'C', 'N', 'N', '0', '1'};
+
+}  // namespace
+
+extern "C" {
+
+wdb_status wdb_cnn_create(int levels, int channels, int height, int width, int max_batch, unsigned long long seed,
+                          void* stream, wdb_cnn** out) {
+    if (!out) return set_error(WDB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (levels < 1 || levels > 8) return set_error(WDB_EINVAL, "levels must be in [1, 8]");
+    if (channels < 1 || channels > kCMax) return set_error(WDB_EINVAL, "channels must be in [1, 32]");
+    if (max_batch < 1) return set_error(WDB_EINVAL, "max_batch must be >= 1");
+    if (height <= 0 || width <= 0 || (height % (1 << (levels - 1))) || (width % (1 << (levels - 1))))
+        return set_error(WDB_EINVAL, "image sides must be divisible by 2^(levels-1)");
+    int nd = 0;
+    if (cudaGetDeviceCount(&nd) != cudaSuccess || nd == 0) return set_error(WDB_ECUDA, "no CUDA device available");
+    wdb_cnn* n = new (std::nothrow) wdb_cnn();
+    if (!n) return set_error(WDB_ENOMEM, "host allocation");
+    n->L = levels;
+    n->C = channels;
+    n->H = height;
+    n->W = width;
+    n->Bmax = max_batch;
+    n->seed = seed;
+    const int C = channels;
+    auto add = [&](int ci, int co) {
+        ConvLayer c{ci, co, n->n_params, n->n_params + (long long)co * ci * 9};
+        n->n_params += (long long)co * ci * 9 + co;
+        n->convs.push_back(c);
+    };
+    add(1, C);
+    add(C, C);
+    for (int l = 1; l < levels; ++l) {
+        add(C, C);
+        add(C, C);
+    }
+    for (int l = levels - 2; l >= 0; --l) {
+        add(C, C);
+        add(C, C);
+    }
+    add(C, 1);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    wdb_status s = WDB_OK;
+    auto A = [&](auto** p, size_t cnt) {
+        if (s == WDB_OK) s = cnn_alloc(n, p, cnt);
+    };
+    A(&n->p, n->n_params);
+    A(&n->g, n->n_params);
+    A(&n->m, n->n_params);
+    A(&n->v, n->n_params);
+    A(&n->pb, n->n_params);
+    A(&n->wt, (size_t)C * C * 9);
+    const size_t B = (size_t)max_batch;
+    n->e_inp.assign(levels, nullptr);
+    n->e_a.assign(levels, nullptr);
+    n->e_e.assign(levels, nullptr);
+    n->d_s.assign(levels, nullptr);
+    n->d_a.assign(levels, nullptr);
+    n->d_d.assign(levels, nullptr);
+    n->g_enc.assign(levels, nullptr);
+    for (int l = 0; l < levels; ++l) {
+        const size_t cnt = B * C * (size_t)(height >> l) * (size_t)(width >> l);
+        if (l > 0) A(&n->e_inp[l], cnt);
+        A(&n->e_a[l], cnt);
+        A(&n->e_e[l], cnt);
+        if (l < levels - 1) {
+            A(&n->d_s[l], cnt);
+            A(&n->d_a[l], cnt);
+            A(&n->d_d[l], cnt);
+        }
+        A(&n->g_enc[l], cnt);
+    }
+    const size_t full = B * C * (size_t)height * width;
+    A(&n->g0, full);
+    A(&n->g1, full);
+    A(&n->g2, full);
+    A(&n->dv, B * (size_t)height * width);
+    A(&n->part, 4096 * 4);
+    A(&n->counter, 4);
+    A(&n->d_loss, 4);
+    if (s == WDB_OK) {
+        // He initialisation (weights), zero biases; the output convolution starts at 0.1 x
+        cudaMemsetAsync(n->p, 0, sizeof(float) * n->n_params, st);
+        for (size_t k = 0; k < n->convs.size(); ++k) {
+            const ConvLayer& c = n->convs[k];
+            const long long nw = (long long)c.co * c.ci * 9;
+            float std = sqrtf(2.0f / (float)(c.ci * 9)) * (k + 1 == n->convs.size() ? 0.1f : 1.0f);
+            init_normal_kernel<<<ew(nw), 256, 0, st>>>(n->p + c.w_off, nw, seed + 0x1000ull * (k + 1), std);
+        }
+        cudaMemsetAsync(n->m, 0, sizeof(float) * n->n_params, st);
+        cudaMemsetAsync(n->v, 0, sizeof(float) * n->n_params, st);
+        to_bf16_kernel<<<ew(n->n_params), 256, 0, st>>>(n->p, n->pb, n->n_params);
+        cudaMemsetAsync(n->counter, 0, sizeof(unsigned int) * 4, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_error(e, "cnn init", __FILE__, __LINE__);
+    }
+    if (s != WDB_OK) {
+        cnn_release(n);
+        return s;
+    }
+    *out = n;
+    return WDB_OK;
+}
+
+void wdb_cnn_free(wdb_cnn* n) { cnn_release(n); }
+
+long long wdb_cnn_num_params(const wdb_cnn* n) { return n ? n->n_params : -1; }
+
+wdb_status wdb_cnn_set_params(wdb_cnn* n, const float* host, long long count, void* stream) {
+    if (!n || !host) return set_error(WDB_EINVAL, "NULL argument");
+    if (count != n->n_params) return set_error(WDB_EINVAL, "expected %lld parameters, got %lld", n->n_params, count);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WDB_CK(cudaMemcpyAsync(n->p, host, sizeof(float) * count, cudaMemcpyHostToDevice, st));
+    WDB_CK(cudaMemsetAsync(n->m, 0, sizeof(float) * count, st));
+    WDB_CK(cudaMemsetAsync(n->v, 0, sizeof(float) * count, st));
+    to_bf16_kernel<<<ew(count), 256, 0, st>>>(n->p, n->pb, count);
+    count_launch();
+    n->step = 0;
+    WDB_CK(cudaStreamSynchronize(st));
+    return WDB_OK;
+}
+
+wdb_status wdb_cnn_get_params(const wdb_cnn* n, float* host, long long count) {
+    if (!n || !host) return set_error(WDB_EINVAL, "NULL argument");
+    if (count < n->n_params) return set_error(WDB_EINVAL, "capacity %lld < %lld", count, n->n_params);
+    WDB_CK(cudaMemcpy(host, n->p, sizeof(float) * n->n_params, cudaMemcpyDeviceToHost));
+    return WDB_OK;
+}
+
+wdb_status wdb_cnn_forward(wdb_cnn* n, const float* u_dev, float* v_dev, int B, void* stream) {
+    if (!n || !u_dev || !v_dev) return set_error(WDB_EINVAL, "NULL argument");
+    if (B < 1 || B > n->Bmax) return set_error(WDB_EINVAL, "batch %d outside [1, %d]", B, n->Bmax);
+    return forward(n, u_dev, v_dev, B, static_cast<cudaStream_t>(stream));
+}
+
+wdb_status wdb_cnn_loss_grad(wdb_cnn* n, const float* u_dev, const float* target_dev, int B, void* stream,
+                             double* loss_host, float* grad_host) {
+    if (!n || !u_dev || !target_dev || !loss_host) return set_error(WDB_EINVAL, "NULL argument");
+    if (B < 1 || B > n->Bmax) return set_error(WDB_EINVAL, "batch %d outside [1, %d]", B, n->Bmax);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float* vbuf = n->g2;   // the forward output is consumed by the loss before backward reuses g2
+    WDB_TRY(forward(n, u_dev, vbuf, B, st));
+    WDB_TRY(loss(n, vbuf, target_dev, B, st, loss_host));
+    WDB_TRY(backward(n, u_dev, B, st));
+    if (grad_host) {
+        WDB_CK(cudaMemcpyAsync(grad_host, n->g, sizeof(float) * n->n_params, cudaMemcpyDeviceToHost, st));
+        WDB_CK(cudaStreamSynchronize(st));
+    }
+    return WDB_OK;
+}
+
+wdb_status wdb_cnn_train_step(wdb_cnn* n, const float* u_dev, const float* target_dev, int B, double lr, void* stream,
+                              double* loss_host) {
+    double l = 0.0;
+    WDB_TRY(wdb_cnn_loss_grad(n, u_dev, target_dev, B, stream, &l, nullptr));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    n->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)n->step), c2 = 1.f - powf(b2, (float)n->step);
+    adam_kernel<<<ew(n->n_params), 256, 0, st>>>(n->p, n->g, n->m, n->v, n->pb, n->n_params, (float)lr, b1, b2, 1e-8f,
+                                                 c1, c2);
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    if (loss_host) *loss_host = l;
+    return WDB_OK;
+}
+
+wdb_status wdb_solve_warm(wdb_theta* th, wdb_cnn* n, const float* u_dev, float* x_dev, const wdb_solve_params* params,
+                          void* stream, wdb_solve_result* result, int* start_used) {
+    if (!th || !n || !u_dev || !x_dev || !params || !result) return set_error(WDB_EINVAL, "NULL argument");
+    if (th->lay.n_rows != n->H || th->lay.n_cols != n->W)
+        return set_error(WDB_EINVAL, "network is %dx%d, operator is %dx%d", n->H, n->W, th->lay.n_rows,
+                         th->lay.n_cols);
+    if (params->x_init_dev) return set_error(WDB_EINVAL, "x_init_dev must be NULL: the network provides the start");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const long long N = th->lay.N;
+    float* v = n->g0;       // network output (image), then zeros
+    float* xw = n->g1;      // its coefficients
+    float* x0 = n->dv;      // coefficients of u
+    float* scratch = n->g2; // N/2 floats of DWT scratch
+    WDB_TRY(forward(n, u_dev, v, 1, st));
+    WDB_TRY(dwt2<float>(v, xw, th->lay, th->filt, scratch, st));
+    WDB_TRY(dwt2<float>(u_dev, x0, th->lay, th->filt, scratch, st));
+    WDB_CK(cudaMemsetAsync(v, 0, sizeof(float) * N, st));
+    // candidates: 0 (the cold start), the network's start, the observation's coefficients
+    const float* cand[3] = {v, xw, x0};
+    double E[3];
+    int best = 0;
+    for (int c = 0; c < 3; ++c) {
+        WDB_TRY(wdb_theta_objective(th, cand[c], x0, params->lambda, params->w_subband_host, stream, &E[c]));
+        if (std::isfinite(E[c]) && E[c] < E[best]) best = c;
+    }
+    wdb_solve_params p = *params;
+    p.x_init_dev = best == 0 ? nullptr : cand[best];
+    if (start_used) *start_used = best;
+    return wdb_solve(th, u_dev, x_dev, &p, stream, result);
+}
+
+wdb_status wdb_cnn_save(const wdb_cnn* n, const char* path) {
+    if (!n || !path) return set_error(WDB_EINVAL, "NULL argument");
+    std::vector<float> p(n->n_params), m(n->n_params), v(n->n_params);
+    WDB_CK(cudaMemcpy(p.data(), n->p, sizeof(float) * n->n_params, cudaMemcpyDeviceToHost));
+    WDB_CK(cudaMemcpy(m.data(), n->m, sizeof(float) * n->n_params, cudaMemcpyDeviceToHost));
+    WDB_CK(cudaMemcpy(v.data(), n->v, sizeof(float) * n->n_params, cudaMemcpyDeviceToHost));
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return set_error(WDB_EIO, "cannot open %s", path);
+    long long hdr[7] = {n->L, n->C, n->H, n->W, n->Bmax, n->step, (long long)n->seed};
+    bool ok = std::fwrite(kMagicCnn, 1, 8, f) == 8 && std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+              std::fwrite(p.data(), sizeof(float), p.size(), f) == p.size() &&
+              std::fwrite(m.data(), sizeof(float), m.size(), f) == m.size() &&
+              std::fwrite(v.data(), sizeof(float), v.size(), f) == v.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? WDB_OK : set_error(WDB_EIO, "write failed: %s", path);
+}
+
+wdb_status wdb_cnn_load(const char* path, void* stream, wdb_cnn** out) {
+    if (!path || !out) return set_error(WDB_EINVAL, "NULL argument");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return set_error(WDB_EIO, "cannot open %s", path);
+    char magic[8];
+    long long hdr[7];
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagicCnn, 8) == 0 &&
+              std::fread(hdr, sizeof hdr, 1, f) == 1;
+    wdb_cnn* n = nullptr;
+    if (ok) {
+        wdb_status s = wdb_cnn_create((int)hdr[0], (int)hdr[1], (int)hdr[2], (int)hdr[3], (int)hdr[4],
+                                      (unsigned long long)hdr[6], stream, &n);
+        if (s != WDB_OK) {
+            std::fclose(f);
+            return s;
+        }
+        std::vector<float> p(n->n_params), m(n->n_params), v(n->n_params);
+        ok = std::fread(p.data(), sizeof(float), p.size(), f) == p.size() &&
+             std::fread(m.data(), sizeof(float), m.size(), f) == m.size() &&
+             std::fread(v.data(), sizeof(float), v.size(), f) == v.size();
+        if (ok) {
+            cudaStream_t st = static_cast<cudaStream_t>(stream);
+            cudaMemcpyAsync(n->p, p.data(), sizeof(float) * p.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(n->m, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(n->v, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice, st);
+            to_bf16_kernel<<<ew(n->n_params), 256, 0, st>>>(n->p, n->pb, n->n_params);
+            n->step = hdr[5];
+            ok = cudaStreamSynchronize(st) == cudaSuccess;
+        }
+    }
+    std::fclose(f);
+    if (!ok) {
+        cnn_release(n);
+        return set_error(WDB_EIO, "bad or truncated file: %s", path);
+    }
+    *out = n;
+    return WDB_OK;
+}
+
+}  // extern "C"

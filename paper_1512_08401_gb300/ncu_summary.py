@@ -1,7 +1,7 @@
 """Summarise an ncu launch list (--metrics gpu__time_duration.sum --csv) per kernel:
 launches, total device time and share, split by NVTX range when ncu recorded one.
 
-    python -m paper_1512_08401_gb300.ncu_summary gpurun_out/launches.csv
+    python -m paper_1512_08401_gb300.ncu_summary launches.csv
 """
 from __future__ import annotations
 

@@ -84,6 +84,17 @@ _SIGS = {
     "wdb_idwt": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
     "wdb_dwt_noalloc": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
     "wdb_wavelet_filters": (i32, [C.c_char_p, i32, pd, pd, pi]),
+    "wdb_cnn_create": (i32, [i32, i32, i32, i32, i32, C.c_ulonglong, vp, C.POINTER(vp)]),
+    "wdb_cnn_free": (None, [vp]),
+    "wdb_cnn_num_params": (i64, [vp]),
+    "wdb_cnn_set_params": (i32, [vp, C.POINTER(C.c_float), i64, vp]),
+    "wdb_cnn_get_params": (i32, [vp, C.POINTER(C.c_float), i64]),
+    "wdb_cnn_forward": (i32, [vp, vp, vp, i32, vp]),
+    "wdb_cnn_loss_grad": (i32, [vp, vp, vp, i32, vp, pd, C.POINTER(C.c_float)]),
+    "wdb_cnn_train_step": (i32, [vp, vp, vp, i32, f64, vp, pd]),
+    "wdb_cnn_save": (i32, [vp, C.c_char_p]),
+    "wdb_cnn_load": (i32, [C.c_char_p, vp, C.POINTER(vp)]),
+    "wdb_solve_warm": (i32, [vp, vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult), pi]),
     "wdb_status_str": (C.c_char_p, [i32]),
     "wdb_last_error": (C.c_char_p, []),
     "wdb_kernel_launches": (i64, [i32]),
@@ -360,3 +371,87 @@ def solve_batch(thetas, us, xs, params_list, stream=None):
     R = (SolveResult * B)()
     _check(lib().wdb_solve_batch(B, TH, U, X, P, _stream(stream), R))
     return [R[i].as_dict() for i in range(B)]
+
+
+class WarmStartNet:
+    """The warm-start U-Net (wdb_cnn_*): images are [B, H, W] float32 CUDA tensors."""
+
+    def __init__(self, levels=4, channels=32, height=128, width=128, max_batch=16, seed=0, stream=None,
+                 _handle=None):
+        self._h = C.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            _check(lib().wdb_cnn_create(levels, channels, height, width, max_batch, seed, _stream(stream),
+                                        C.byref(self._h)))
+        self.levels, self.channels, self.height, self.width, self.max_batch = levels, channels, height, width, max_batch
+
+    @classmethod
+    def load(cls, path, stream=None):
+        h = C.c_void_p()
+        _check(lib().wdb_cnn_load(path.encode(), _stream(stream), C.byref(h)))
+        with open(path, "rb") as f:
+            hdr = np.frombuffer(f.read(8 + 7 * 8)[8:], dtype=np.int64)
+        return cls(int(hdr[0]), int(hdr[1]), int(hdr[2]), int(hdr[3]), int(hdr[4]), _handle=h)
+
+    @property
+    def num_params(self) -> int:
+        return int(lib().wdb_cnn_num_params(self._h))
+
+    def set_params(self, flat, stream=None):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(lib().wdb_cnn_set_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size, _stream(stream)))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().wdb_cnn_get_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size))
+        return a
+
+    def _img(self, t):
+        B = t.shape[0] if t.dim() == 3 else 1
+        return _dev(t, B * self.height * self.width), B
+
+    def forward(self, u, v, stream=None):
+        pu, B = self._img(u)
+        pv, _ = self._img(v)
+        _check(lib().wdb_cnn_forward(self._h, pu, pv, B, _stream(stream)))
+        return v
+
+    def loss_grad(self, u, target, want_grad=True, stream=None):
+        pu, B = self._img(u)
+        pt, _ = self._img(target)
+        loss = C.c_double()
+        g = np.empty(self.num_params, dtype=np.float32) if want_grad else None
+        gp = g.ctypes.data_as(C.POINTER(C.c_float)) if want_grad else None
+        _check(lib().wdb_cnn_loss_grad(self._h, pu, pt, B, _stream(stream), C.byref(loss), gp))
+        return loss.value, g
+
+    def train_step(self, u, target, lr, stream=None):
+        pu, B = self._img(u)
+        pt, _ = self._img(target)
+        loss = C.c_double()
+        _check(lib().wdb_cnn_train_step(self._h, pu, pt, B, lr, _stream(stream), C.byref(loss)))
+        return loss.value
+
+    def solve_warm(self, theta, u, x, stream=None, **kw):
+        """wdb_solve_warm: returns (result dict, start used: 0 zero, 1 network, 2 Psi* u)."""
+        p, _keep = make_params(**kw)
+        r = SolveResult()
+        used = C.c_int()
+        _check(lib().wdb_solve_warm(theta._h, self._h, _dev(u, theta.N), _dev(x, theta.N), C.byref(p),
+                                    _stream(stream), C.byref(r), C.byref(used)))
+        return r.as_dict(), int(used.value)
+
+    def save(self, path):
+        _check(lib().wdb_cnn_save(self._h, path.encode()))
+
+    def free(self):
+        if self._h:
+            lib().wdb_cnn_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

@@ -1,0 +1,205 @@
+"""Warm-start network: the CUDA forward, loss, gradients and Adam step against the FP64
+oracle (oracle/cnn.py), checkpoints, argument checks, and the warm start's effect on
+Algorithm 3 (fewer iterations to the same objective target on held-out observations).
+
+Tolerances. The library keeps weights and feature maps in BF16 (8 significant bits) with
+FP32 accumulation and FP32 gradients. Two comparisons:
+  * against the plain FP64 oracle on the BF16-rounded weights the library uses: loss within
+    2e-2 relative and the forward correction v - u within 5e-2 (the correction is about 10x
+    smaller than the feature maps at initialisation, so their 2^-9 rounding shows up 10x);
+  * against the oracle evaluated with every stored feature map rounded to BF16 (its `store`
+    hook), so that both sides take the ReLU decisions on the same values: every gradient
+    tensor within `tol` relative (2-norm). What is left is FP32 against FP64 accumulation,
+    which moves a value across a BF16 rounding boundary with probability about
+    (accumulation error / BF16 spacing), near 3e-4 per value for 288-term sums. With a few
+    thousand stored values (C <= 8, small images) that happens a handful of times and the
+    results agree to 1e-6 ... 1e-4, so tol = 1e-3 there still catches any indexing error.
+    At C = 32 on 64 x 64 (about 2 M stored values) hundreds of values move by one BF16 step,
+    and the output correction, 10x smaller than the feature maps at initialisation, moves by
+    ~1e-2; tol = 2e-2 there, the per-tensor bound for BF16 training."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cnn as ocnn
+from paper_1512_08401_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wdb():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1512_08401_gb300 import build, wdb as w
+    build.build()
+    w.lib()
+    return w
+
+
+def bf16_round(a):
+    """Round float32 values to the nearest BF16 (ties to even), returned as float64."""
+    x = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    x = (x + 0x7FFF + ((x >> 16) & 1)) & 0xFFFF0000
+    return x.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def batch(n, B, seed):
+    rng = np.random.default_rng(seed)
+    psf = synthetic.gaussian_psf(1.5, 9)
+    clean = [synthetic.clean_image(n, n, rng) for _ in range(B)]
+    u = np.stack([synthetic.blur_fft(c, psf) + 0.01 * rng.standard_normal((n, n)) for c in clean])
+    return u, np.stack(clean)
+
+
+def params_as_used(levels, channels, seed):
+    """Oracle initial parameters with the weights rounded to BF16 as the library stores them
+    (biases stay FP32)."""
+    p = ocnn.init_params(levels, channels, seed)
+    for k in p:
+        p[k] = bf16_round(p[k]) if k.endswith(".W") else p[k].astype(np.float32).astype(np.float64)
+    # non-zero biases so their gradients and the bias path are exercised
+    rng = np.random.default_rng(seed + 1)
+    for k in p:
+        if k.endswith(".b"):
+            p[k] = (0.05 * rng.standard_normal(p[k].shape)).astype(np.float32).astype(np.float64)
+    return p
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-30))
+
+
+def compare(wdb, levels, channels, u, t, seed, tol):
+    p = params_as_used(levels, channels, seed)
+    flat = ocnn.flatten(p, levels, channels)
+    B, H, W = u.shape
+    net = wdb.WarmStartNet(levels, channels, H, W, max_batch=B, seed=1)
+    assert net.num_params == flat.size
+    net.set_params(flat)
+    assert np.array_equal(net.get_params(), flat.astype(np.float32))
+    U, T = dev(u), dev(t)
+    V = torch.empty_like(U)
+    net.forward(U, V)
+    loss, g = net.loss_grad(U, T)
+    v_ref = ocnn.forward(p, u, levels)[0]
+    l_ref = ocnn.loss_and_grads(p, u, t, levels)[0]
+    l_bf, g_bf, v_bf = ocnn.loss_and_grads(p, u, t, levels, store=bf16_round)
+    errs = {"v-u (fp64)": rel(V.cpu().numpy() - u, v_ref - u), "loss (fp64)": abs(loss - l_ref) / l_ref,
+            "v-u (bf16 maps)": rel(V.cpu().numpy() - u, v_bf - u), "loss (bf16 maps)": abs(loss - l_bf) / l_bf}
+    gg = ocnn.unflatten(g.astype(np.float64), levels, channels)
+    for name, _ in ocnn.param_shapes(levels, channels):
+        errs[name] = rel(gg[name], g_bf[name])
+    lim = {"v-u (fp64)": 5e-2, "loss (fp64)": 2e-2}
+    bad = {k: e for k, e in errs.items() if e > lim.get(k, tol)}
+    assert not bad, (bad, errs)
+    return errs
+
+
+@pytest.mark.parametrize("levels,channels,n,B,tol", [(1, 4, 16, 2, 1e-3), (3, 8, 32, 2, 1e-3), (2, 5, 24, 3, 1e-3),
+                                                     (4, 32, 64, 1, 2e-2)])
+def test_forward_loss_grads_match_oracle(wdb, levels, channels, n, B, tol):
+    u, clean = batch(n, B, seed=11 + n)
+    compare(wdb, levels, channels, u, clean, seed=7 + levels, tol=tol)
+
+
+def test_ragged_tiles_match_oracle(wdb):
+    # 40 x 24: tiles of 16 do not divide the image; the deepest level (10 x 6) is smaller than a tile
+    rng = np.random.default_rng(5)
+    compare(wdb, 3, 6, rng.uniform(0, 1, (2, 40, 24)), rng.uniform(0, 1, (2, 40, 24)), seed=3, tol=1e-3)
+
+
+def test_adam_first_step(wdb):
+    # first bias-corrected Adam step: p1 = p0 - lr g / (|g| + eps)
+    levels, channels, n = 2, 4, 16
+    p = params_as_used(levels, channels, seed=2)
+    flat = ocnn.flatten(p, levels, channels).astype(np.float32)
+    u, clean = batch(n, 2, seed=4)
+    net = wdb.WarmStartNet(levels, channels, n, n, max_batch=2)
+    net.set_params(flat)
+    _, g = net.loss_grad(dev(u), dev(clean))
+    lr = 1e-3
+    net.train_step(dev(u), dev(clean), lr)
+    p1 = net.get_params().astype(np.float64)
+    step = flat.astype(np.float64) - p1
+    big = np.abs(g) > 1e-3 * np.abs(g).max()
+    # the step recomputes the gradient (atomic accumulation order may differ), so compare where
+    # it is not tiny; the FP32 subtraction p0 - step rounds to the ulp of p0 (|p0| < 4)
+    expect = lr * g / (np.abs(g) + 1e-8)
+    assert np.allclose(step[big], expect[big], rtol=1e-3, atol=5e-7)
+    assert np.all(np.abs(step) <= lr + 5e-7)
+
+
+def test_training_reduces_loss_and_checkpoint_roundtrip(wdb, tmp_path):
+    n, B = 32, 8
+    u, clean = batch(n, B, seed=9)
+    U, T = dev(u), dev(clean)
+    net = wdb.WarmStartNet(3, 16, n, n, max_batch=B, seed=3)
+    l0 = net.train_step(U, T, 1e-3)
+    for _ in range(60):
+        l1 = net.train_step(U, T, 1e-3)
+    assert l1 < 0.5 * l0
+    path = str(tmp_path / "net.ckpt")
+    net.save(path)
+    net2 = wdb.WarmStartNet.load(path)
+    assert (net2.levels, net2.channels, net2.height, net2.width) == (3, 16, n, n)
+    assert np.array_equal(net2.get_params(), net.get_params())
+    V1, V2 = torch.empty_like(U), torch.empty_like(U)
+    net.forward(U, V1)
+    net2.forward(U, V2)
+    assert torch.equal(V1, V2)
+    # the Adam moments travel with the checkpoint: the next steps match closely
+    a = net.train_step(U, T, 1e-3)
+    b = net2.train_step(U, T, 1e-3)
+    assert abs(a - b) <= 1e-4 * a
+
+
+def test_rejects_bad_arguments(wdb):
+    with pytest.raises(wdb.WdbError):
+        wdb.WarmStartNet(3, 8, 30, 32)          # 30 not divisible by 4
+    with pytest.raises(wdb.WdbError):
+        wdb.WarmStartNet(2, 33, 32, 32)         # more than 32 channels
+    net = wdb.WarmStartNet(2, 4, 16, 16, max_batch=2)
+    with pytest.raises(wdb.WdbError):
+        net.set_params(np.zeros(net.num_params + 1, dtype=np.float32))
+    U = torch.zeros(3, 16, 16, device="cuda")
+    with pytest.raises(wdb.WdbError):
+        net.forward(U, torch.empty_like(U))     # batch 3 > max_batch 2
+    th = wdb.Theta.build(synthetic.gaussian_psf(1.0, 5), 32, 32, "db4", 2, K=30 * 32 * 32)
+    x = torch.zeros(th.N, device="cuda")
+    with pytest.raises(wdb.WdbError):
+        net.solve_warm(th, torch.zeros(th.N, device="cuda"), x, lam=1e-3)   # 16x16 net, 32x32 operator
+
+
+def test_warm_start_cuts_iterations(wdb):
+    """Train on x* of seeded observations for one blur (128^2, Gaussian sigma = 2), then count
+    iterations to the same objective targets on held-out observations from three starts:
+    x = 0, x = Psi* u0 and the network's. The network's start must be chosen (lowest E), save
+    at least 15 % of the iterations to E*(1 + 1e-3) and never cost iterations at 1e-4."""
+    from paper_1512_08401_gb300 import warmstart as ws
+    n, J, lam = 128, 4, 1e-3
+    psf = synthetic.gaussian_psf(2.0, 15)
+    th = wdb.Theta.build(psf, n, n, "db4", J, K=30 * n * n)
+    train_u = ws.observations(n, psf, 256, config_id=40)
+    U = ws._stack(train_u)
+    T = ws.solution_images(th, train_u, lam, iters=400)
+    net = wdb.WarmStartNet(4, 32, n, n, max_batch=16, seed=0)
+    log = ws.train(net, U, T, steps=600, batch=16, lr=1e-3)
+    assert np.mean(log.losses[-20:]) < 0.05 * np.mean(log.losses[:5])
+    c3, c4 = [], []
+    for u0 in ws.observations(n, psf, 6, config_id=41):
+        u = ws._stack([u0]).view(-1)
+        E = ws.reference_objective(th, u, lam)
+        c3.append(ws.iterations_to_target(th, net, u, lam, E, rel=1e-3))
+        c4.append(ws.iterations_to_target(th, net, u, lam, E, rel=1e-4))
+    assert all(c["start"] == 1 for c in c3 + c4), (c3, c4)
+    warm3 = np.mean([c["warm"] for c in c3])
+    cold3 = np.mean([min(c["cold"], c["obs"]) for c in c3])
+    assert warm3 <= 0.85 * cold3, c3
+    assert all(c["warm"] <= min(c["cold"], c["obs"]) for c in c4), c4
