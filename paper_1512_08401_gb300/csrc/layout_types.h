@@ -36,7 +36,7 @@ void count_launch(long long n = 1);
 // ---------------------------------------------------------------------------------------
 // Subband layout (Sec. 2): subband-planar, A_J first, then (0,1),(1,0),(1,1) for s=J..1
 // ---------------------------------------------------------------------------------------
-struct SubbandDev {      // per subband, device-resident copy
+struct alignas(16) SubbandDev {   // per subband, device-resident copy (16-byte aligned: vector loads)
     long long off;       // start in the coefficient vector
     int rows, cols;
     int level;           // s (1 = finest)

@@ -291,14 +291,159 @@ static void build_ops(wdb_theta* th) {
     }
     pack_op(L, F, th->fwd_h);
     pack_op(L, A, th->adj_h);
+    // the tiles are shared by about 3 resident CTAs per SM
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int ctas = 3 * std::max(sms, 1);
+    th->plan_ctas = ctas;
     for (int op = 0; op < 2; ++op) {
         const std::vector<PEntry>& src = op ? A : F;
-        std::vector<TileEntry> te(src.size());
+        std::vector<TileEntry>& te = th->tent[op];
+        te.resize(src.size());
         for (size_t i = 0; i < src.size(); ++i)
             te[i] = TileEntry{src[i].out, src[i].in, src[i].up, src[i].lg, src[i].phase, src[i].dy, src[i].dx, src[i].v};
-        th->tplan[op][0] = make_tile_plan(L, te, 4, kTileSmemBudget);
-        th->tplan[op][1] = make_tile_plan(L, te, 8, kTileSmemBudget);
+        th->tplan[op][0] = make_tile_plan(L, te, 4, kTileSmemBudget, ctas);
+        th->tplan[op][1] = make_tile_plan(L, te, 8, kTileSmemBudget, ctas);
     }
+}
+
+namespace {
+
+// Device copy of a candidate plan, freed after it has been timed.
+struct TempPlan {
+    std::vector<void*> bufs;
+    TileArgs a{};
+    ~TempPlan() {
+        for (void* p : bufs) cudaFree(p);
+    }
+};
+
+template <typename T>
+wdb_status temp_copy(TempPlan& d, const std::vector<T>& h, const T** out, cudaStream_t st) {
+    void* p = nullptr;
+    WDB_CK(cudaMalloc(&p, std::max<size_t>(h.size(), 1) * sizeof(T)));
+    d.bufs.push_back(p);
+    if (!h.empty()) WDB_CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    *out = static_cast<const T*>(p);
+    return WDB_OK;
+}
+
+wdb_status temp_plan(const wdb_theta* th, const TilePlanHost& h, TempPlan& d, cudaStream_t st) {
+    TilePlanDev& p = d.a.plan;
+    WDB_TRY(temp_copy(d, h.pairs, &p.pairs, st));
+    WDB_TRY(temp_copy(d, h.subs, &p.subs, st));
+    WDB_TRY(temp_copy(d, h.batches, &p.batches, st));
+    WDB_TRY(temp_copy(d, h.items, &p.items, st));
+    WDB_TRY(temp_copy(d, h.tap_off, &p.tap_off, st));
+    WDB_TRY(temp_copy(d, h.tap_lin, &p.tap_lin, st));
+    WDB_TRY(temp_copy(d, h.tap_v, &p.tap_v, st));
+    WDB_TRY(temp_copy(d, h.tap_v64, &p.tap_v64, st));
+    p.n_items = (int)h.items.size();
+    p.buf_elems = h.buf_elems;
+    p.smem_bytes = h.smem_bytes;
+    d.a.sb = th->d_sb;
+    void* q = nullptr;
+    WDB_CK(cudaMalloc(&q, sizeof(TileQueue)));
+    d.bufs.push_back(q);
+    WDB_CK(cudaMemsetAsync(q, 0, sizeof(TileQueue), st));
+    d.a.queue = static_cast<TileQueue*>(q);
+    d.a.grid = std::max(1, std::min(p.n_items, tile_grid(h.smem_bytes)));
+    return WDB_OK;
+}
+
+}  // namespace
+
+// Autotuned FP32 tile plans: for every output level, each candidate (tile side, 1 or 4
+// outputs per thread) is planned for that level's tiles alone and applied on this GPU (best
+// of 3 after a warm-up); the per-level winners form one plan, which then competes, over the
+// whole operator, with the planner's own plans (per-tile cost caps of 1, 2 and 4 per-CTA
+// shares, which balance the levels against each other). The fastest is kept.
+static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
+    const Layout& L = th->lay;
+    const long long N = L.N;
+    float *in = nullptr, *out = nullptr;
+    double* part = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    wdb_status s = WDB_OK;
+    auto fail = [&](wdb_status v) {
+        if (s == WDB_OK) s = v;
+    };
+    if (cudaMalloc(&in, sizeof(float) * N) != cudaSuccess || cudaMalloc(&out, sizeof(float) * N) != cudaSuccess ||
+        cudaMalloc(&part, sizeof(double) * 2 * 8192) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        fail(set_error(WDB_ENOMEM, "autotune workspace"));
+    if (s == WDB_OK && cudaMemsetAsync(in, 0, sizeof(float) * N, st) != cudaSuccess) fail(set_error(WDB_ECUDA, "memset"));
+    // milliseconds of one application of plan h (1e30 on error)
+    auto time_plan = [&](const TilePlanHost& h) {
+        float ms = 1e30f;
+        TempPlan d;
+        wdb_status r = temp_plan(th, h, d, st);
+        if (r != WDB_OK) {
+            fail(r);
+            return ms;
+        }
+        for (int rep = 0; rep < 4 && s == WDB_OK; ++rep) {
+            if (cudaEventRecord(e0, st) != cudaSuccess) fail(set_error(WDB_ECUDA, "event"));
+            r = tile_apply<float>(d.a, in, out, nullptr, nullptr, part, st);
+            if (r != WDB_OK) fail(r);
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+                fail(set_error(WDB_ECUDA, "autotune timing"));
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);   // the first application is a warm-up
+        }
+        return ms;
+    };
+    for (int op = 0; op < 2 && s == WDB_OK; ++op) {
+        std::vector<TileTune> best(L.S, TileTune{0, 0});
+        for (int lev = 1; lev <= L.J && s == WDB_OK; ++lev) {
+            int side = 1;
+            for (int o = 0; o < L.S; ++o)
+                if (L.sb[o].level == lev) side = std::max(side, std::max(L.sb[o].rows, L.sb[o].cols));
+            int tsmax = 1;
+            while (tsmax < side && tsmax < 32) tsmax <<= 1;
+            float best_ms = 1e30f;
+            TileTune pick{0, 0};
+            for (int ts = tsmax; ts >= 1 && s == WDB_OK; ts >>= 1)
+                for (int e4 = 1; e4 >= 0; --e4) {
+                    if ((e4 && ts < 8) || (!e4 && ts == 32)) continue;
+                    std::vector<TileTune> tune(L.S, TileTune{0, 0});
+                    for (int o = 0; o < L.S; ++o)
+                        if (L.sb[o].level == lev) tune[o] = TileTune{ts, e4};
+                    const TilePlanHost h =
+                        make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, &tune, lev);
+                    if (h.items.empty()) continue;
+                    const float ms = time_plan(h);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        pick = TileTune{ts, e4};
+                    }
+                }
+            for (int o = 0; o < L.S; ++o)
+                if (L.sb[o].level == lev) best[o] = pick;
+        }
+        if (s != WDB_OK) break;
+        std::vector<TilePlanHost> whole;
+        whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, &best, 0));
+        for (double cap : {1.0, 2.0, 4.0})
+            whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, cap));
+        float best_ms = 1e30f;
+        for (size_t k = 0; k < whole.size() && s == WDB_OK; ++k) {
+            const float ms = time_plan(whole[k]);
+            if (ms < best_ms) {
+                best_ms = ms;
+                th->tplan[op][0] = whole[k];
+            }
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(in);
+    cudaFree(out);
+    cudaFree(part);
+    if (s == WDB_OK) th->tuned = 1;
+    return s;
 }
 
 static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a, cudaStream_t st) {
@@ -307,6 +452,7 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
     WDB_TRY(upload(th, h.batches, const_cast<TileBatch**>(&a.plan.batches), st));
     WDB_TRY(upload(th, h.items, const_cast<TileItem**>(&a.plan.items), st));
     WDB_TRY(upload(th, h.tap_off, const_cast<int**>(&a.plan.tap_off), st));
+    WDB_TRY(upload(th, h.tap_lin, const_cast<int**>(&a.plan.tap_lin), st));
     WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&a.plan.tap_v), st));
     WDB_TRY(upload(th, h.tap_v64, const_cast<double**>(&a.plan.tap_v64), st));
     a.plan.n_items = (int)h.items.size();
@@ -426,6 +572,7 @@ wdb_status theta_finalize(wdb_theta* th, cudaStream_t st) {
     WDB_TRY(upload(th, th->sched.vb_start, &th->d_vb_start, st));
     th->grid = std::max(1, std::min(th->sched.nvb, stencil_grid_limit()));
     th->part_len = th->grid;
+    if (kAutotunePlans) WDB_TRY(autotune_plans(th, st));
     for (int op = 0; op < 2; ++op)
         for (int pr = 0; pr < 2; ++pr) {
             WDB_TRY(upload_plan(th, th->tplan[op][pr], th->targs[op][pr], st));

@@ -30,4 +30,7 @@ std::vector<double> precond_table(const std::vector<double>& Md, const std::vect
                                   double eps);
 wdb_status precond_upload(wdb_theta* th, PrecondCache& pc, cudaStream_t st);
 
+// Time candidate FP32 tile plans on the GPU when an operator is finalised (autotuning).
+constexpr bool kAutotunePlans = true;
+
 }  // namespace wdb

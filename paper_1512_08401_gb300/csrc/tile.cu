@@ -22,7 +22,16 @@ struct PairBuild {
     int out, in, up, lg;
     int dy0 = 1 << 30, dy1 = -(1 << 30), dx0 = 1 << 30, dx1 = -(1 << 30);
     std::vector<const TileEntry*> taps;
+    int maxph = 0;     // taps applied per output: all taps (down), the fullest phase (up)
 };
+
+// Cost model of one tile, in thread instructions (used to choose the tile side and, per
+// pair, staging against gathering from global memory / L2).
+constexpr double kCostStage = 8.0;       // per staged input element (cp.async, wrap, index)
+constexpr double kCostTapStage = 6.0;    // per staged tap (offset + value)
+constexpr double kCostMacGlobal = 60.0;  // per multiply-add gathered from global memory (latency bound)
+constexpr double kCostItem = 20000.0;    // per tile (scheduling, descriptors, barriers, epilogue)
+constexpr int kUpStagedLg = 3;           // up pairs with r <= 8 stage their phase tables
 
 int next_pow2(int v) {
     int p = 1;
@@ -31,33 +40,71 @@ int next_pow2(int v) {
 }
 
 struct Geometry {
-    int RR, RC, PR, PC;
+    int RR, RC, PR, PC, PS;
     long long bytes;
 };
 
-Geometry geometry(const PairBuild& p, int TS, int esize) {
+// Row pitch of a staged region. With 4 outputs per thread (TS >= 8) the threads of one warp
+// read TS / 4 consecutive words in each of 128 / TS rows, so a pitch congruent to TS / 4
+// modulo TS / 2 puts the rows on disjoint banks; one output per thread: an odd pitch.
+int pitch(int width, int TS, bool e4) {
+    if (TS < 8 || !e4) return width | 1;
+    const int lanes = TS / 4;
+    int p = width;
+    while (p % (2 * lanes) != lanes) ++p;
+    return p;
+}
+
+Geometry geometry(const PairBuild& p, int TS, int esize, bool e4) {
     Geometry g;
     const int r = 1 << p.lg;
     if (!p.up) {
         g.RR = r * (TS - 1) + (p.dy1 - p.dy0) + 1;
         g.RC = r * (TS - 1) + (p.dx1 - p.dx0) + 1;
         g.PR = (g.RR + r - 1) / r;
-        g.PC = ((g.RC + r - 1) / r) | 1;
-        g.bytes = (long long)r * r * g.PR * g.PC * esize;
+        g.PC = pitch((g.RC + r - 1) / r, TS, e4);
+        g.PS = g.PR * g.PC;
+        g.bytes = (long long)r * r * g.PS * esize;
     } else {
         const int rows = std::max(1, TS >> p.lg);
         g.RR = rows + (p.dy1 - p.dy0);
         g.RC = rows + (p.dx1 - p.dx0);
         g.PR = g.RR;
-        g.PC = g.RC | 1;
+        g.PC = pitch(g.RC, TS, e4);
+        g.PS = g.PR * g.PC;
         g.bytes = (long long)g.PR * g.PC * esize;
     }
     return g;
 }
 
+
+// Modelled cost per output of subband o's tiles of side ts; glob[k] receives the cheaper
+// mode of pair k (true: gather from global memory).
+double subband_cost(const SubbandDev& so, const std::vector<PairBuild*>& prs, int ts, bool e4, int esize, int budget,
+                    std::vector<bool>& glob) {
+    const double outs = (double)std::min(ts, so.rows) * std::min(ts, so.cols);
+    const double mac_smem = e4 ? 2.75 : 5.0;
+    double c = kCostItem;
+    glob.assign(prs.size(), false);
+    for (size_t k = 0; k < prs.size(); ++k) {
+        const PairBuild& pb = *prs[k];
+        const Geometry g = geometry(pb, ts, esize, e4);
+        const double macs = outs * pb.maxph;
+        double cs = 1e300;
+        if (g.bytes <= budget)
+            cs = (double)g.RR * g.RC * kCostStage + macs * mac_smem +
+                 kCostTapStage * (double)(!pb.up ? (int)pb.taps.size() : (pb.lg <= kUpStagedLg ? pb.maxph << (2 * pb.lg) : 0));
+        const double cg = macs * kCostMacGlobal;
+        glob[k] = cg < cs;
+        c += std::min(cs, cg);
+    }
+    return c / outs;
+}
+
 }  // namespace
 
-TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int budget) {
+TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int budget, int ctas,
+                            const std::vector<TileTune>* tune, int level_only, double cap_share) {
     TilePlanHost plan;
     std::map<std::pair<int, int>, PairBuild> pairs;
     for (const TileEntry& e : entries) {
@@ -81,33 +128,81 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         double cost;
     };
     std::vector<ItemCost> items;
+    for (int o = 0; o < L.S; ++o)
+        for (PairBuild* pb : by_out[o]) {
+            if (!pb->up) {
+                pb->maxph = (int)pb->taps.size();
+            } else {
+                std::vector<int> cnt(1 << (2 * pb->lg), 0);
+                for (const TileEntry* e : pb->taps) cnt[e->phase]++;
+                pb->maxph = *std::max_element(cnt.begin(), cnt.end());
+            }
+        }
+    // balance: the whole operator's modelled cost (each subband at its cheapest tile side)
+    // shared by `ctas` CTAs bounds the cost of one tile, so that no tile is the critical path
+    std::vector<int> ts_max(L.S);
+    double total = 0.0;
+    {
+        std::vector<bool> tmp;
+        for (int o = 0; o < L.S; ++o) {
+            const SubbandDev& so = L.sb[o];
+            ts_max[o] = std::min(32, next_pow2(std::max(so.rows, so.cols)));
+            double bc = 1e300;
+            for (int ts = ts_max[o]; ts >= 1; ts >>= 1)
+                bc = std::min(bc, subband_cost(so, by_out[o], ts, ts >= 8, esize, budget, tmp));
+            total += bc * so.rows * so.cols;
+        }
+    }
+    // (a tile's fixed cost makes tiles cheaper than ~16 of it wasteful, so the cap never
+    // goes below that: small operators accept some imbalance)
+    const double item_cap = std::max(cap_share * total / std::max(1, ctas), 16.0 * kCostItem);
     for (int o = 0; o < L.S; ++o) {
         const SubbandDev& so = L.sb[o];
-        // largest tile (<= 32, <= the subband) whose staged regions each fit one buffer;
-        // a pair that does not fit even for 1 x 1 tiles gathers from global memory
+        // tile side and per-pair mode (staged in shared memory or gathered from global
+        // memory) that minimise the modelled cost per output, among the sides whose tiles
+        // stay under the balance cap (else the side with the cheapest tile); a staged region
+        // must fit one buffer
         const int np = (int)by_out[o].size();
-        std::vector<bool> global(np, false);
-        auto fits = [&](int ts) {
-            for (int k = 0; k < np; ++k)
-                if (geometry(*by_out[o][k], ts, esize).bytes > budget) return false;
-            return true;
-        };
-        int TS = std::min(32, next_pow2(std::max(so.rows, so.cols)));
-        while (TS > 1 && !fits(TS)) TS >>= 1;
-        for (int k = 0; k < np; ++k)
-            if (geometry(*by_out[o][k], TS, esize).bytes > budget) global[k] = true;
-        // staged pairs first (in batches that fill a buffer), then the global ones
+        std::vector<bool> global, trial;
+        int TS = 0;
+        bool e4 = false;
+        double best = 1e300, best_item = 1e300;
+        if (tune && (*tune)[o].ts > 0) {   // forced by the autotuner
+            TS = std::min((*tune)[o].ts, ts_max[o]);
+            e4 = TS == 32 || (TS >= 8 && (*tune)[o].e4);
+            best = subband_cost(so, by_out[o], TS, e4, esize, budget, global);
+        } else {
+            for (int ts = ts_max[o]; ts >= 1; ts >>= 1) {
+                const double c = subband_cost(so, by_out[o], ts, ts >= 8, esize, budget, trial);
+                const double item = c * std::min(ts, so.rows) * std::min(ts, so.cols);
+                const bool ok = item <= item_cap, best_ok = best_item <= item_cap;
+                if (TS == 0 || (ok && (!best_ok || c < best)) || (!ok && !best_ok && item < best_item)) {
+                    TS = ts;
+                    best = c;
+                    best_item = item;
+                    global = trial;
+                }
+            }
+            e4 = TS >= 8;
+        }
+        // staged down pairs, staged up pairs (in batches that fill a buffer), then the global
+        // ones; within a batch the staged taps (down pairs only) are contiguous
         std::vector<int> order;
         for (int k = 0; k < np; ++k)
-            if (!global[k]) order.push_back(k);
+            if (!global[k] && !by_out[o][k]->up) order.push_back(k);
+        for (int k = 0; k < np; ++k)
+            if (!global[k] && by_out[o][k]->up && by_out[o][k]->lg <= kUpStagedLg) order.push_back(k);
+        for (int k = 0; k < np; ++k)
+            if (!global[k] && by_out[o][k]->up && by_out[o][k]->lg > kUpStagedLg) order.push_back(k);
         for (int k = 0; k < np; ++k)
             if (global[k]) order.push_back(k);
         TileSub& sub = plan.subs[o];
         sub.TS = TS;
+        sub.e4 = e4 ? 1 : 0;
         sub.pair_begin = (int)plan.pairs.size();
         sub.batch_begin = sub.batch_end = 0;
         // (batches are filled in below)
-        double taps_per_out = 0.0, stage_per_tile = 0.0;
+        double taps_per_out = 0.0;
         // first pass: geometry and batch membership (regions plus their taps must fit)
         const int ebudget = budget / esize;
         std::vector<int> batch_of(order.size()), pair_soff(order.size(), 0);
@@ -119,15 +214,11 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 continue;
             }
             const PairBuild& pb = *by_out[o][k];
-            const Geometry g = geometry(pb, TS, esize);
+            const Geometry g = geometry(pb, TS, esize, e4);
             const int need = (int)((g.bytes + 15) / 16 * 16 / esize);
-            const int r = 1 << pb.lg;
-            int nt = (int)pb.taps.size();
-            if (pb.up) {
-                std::vector<int> cnt(r * r, 0);
-                for (const TileEntry* e : pb.taps) cnt[e->phase]++;
-                nt = *std::max_element(cnt.begin(), cnt.end()) * r * r;
-            }
+            // staged taps: down pairs and up pairs with r <= 8 (larger phase tables are read
+            // from global memory)
+            const int nt = !pb.up ? (int)pb.taps.size() : (pb.lg <= kUpStagedLg ? pb.maxph << (2 * pb.lg) : 0);
             // taps: one int offset + one value each, rounded to 16 bytes
             auto tap_elems = [&](int ntaps) { return (int)(((long long)ntaps * (4 + esize) + 15) / 16 * 16 / esize); };
             const bool nonempty = batch_regions.back() > 0;
@@ -149,7 +240,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         for (size_t q = 0; q < order.size(); ++q) {
             const int k = order[q];
             const PairBuild& pb = *by_out[o][k];
-            const Geometry g = geometry(pb, TS, esize);
+            const Geometry g = geometry(pb, TS, esize, e4);
             const int r = 1 << pb.lg, m = r - 1;
             TileBatch& bt = plan.batches[sub.batch_begin + batch_of[q]];
             if (bt.pair_end == bt.pair_begin) {
@@ -164,16 +255,23 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             tp.RC = g.RC;
             tp.PR = g.PR;
             tp.PC = g.PC;
+            tp.PS = g.PS;
             tp.y0 = pb.dy0;
             tp.x0 = pb.dx0;
+            if (global[k]) {   // bounding box of the taps (input units) for the interior test
+                tp.RR = pb.dy1 - pb.dy0 + 1;
+                tp.RC = pb.dx1 - pb.dx0 + 1;
+                tp.PR = tp.PC = tp.PS = 0;
+            }
             tp.soff = global[k] ? 0 : pair_soff[q];
             tp.tap_begin = (int)plan.tap_off.size();
+            const int cin = L.sb[pb.in].cols;
             auto offset = [&](const TileEntry& e) -> int {
                 if (global[k]) return (e.dy << 16) | (e.dx & 0xffff);
                 if (!pb.up) {
                     const int yy = e.dy - pb.dy0, xx = e.dx - pb.dx0;
                     const int plane = ((yy & m) << pb.lg) + (xx & m);
-                    return plane * g.PR * g.PC + (yy >> pb.lg) * g.PC + (xx >> pb.lg) + tp.soff;
+                    return plane * g.PS + (yy >> pb.lg) * g.PC + (xx >> pb.lg) + tp.soff;
                 }
                 return (e.dy - pb.dy0) * g.PC + (e.dx - pb.dx0) + tp.soff;
             };
@@ -181,6 +279,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 tp.ntap = (int)pb.taps.size();
                 for (const TileEntry* e : pb.taps) {
                     plan.tap_off.push_back(offset(*e));
+                    plan.tap_lin.push_back(global[k] ? e->dy * cin + e->dx : 0);
                     plan.tap_v.push_back((float)e->v);
                     plan.tap_v64.push_back(e->v);
                 }
@@ -195,20 +294,23 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                     for (int qq = 0; qq < nph; ++qq) {
                         if (j < (int)ph[qq].size()) {
                             plan.tap_off.push_back(offset(*ph[qq][j]));
+                            plan.tap_lin.push_back(global[k] ? ph[qq][j]->dy * cin + ph[qq][j]->dx : 0);
                             plan.tap_v.push_back((float)ph[qq][j]->v);
                             plan.tap_v64.push_back(ph[qq][j]->v);
                         } else {
+                            // padding: value 0 at the region origin (staged) or the
+                            // output's own input position (global)
                             plan.tap_off.push_back(global[k] ? 0 : tp.soff);
+                            plan.tap_lin.push_back(0);
                             plan.tap_v.push_back(0.f);
                             plan.tap_v64.push_back(0.0);
                         }
                     }
             }
             taps_per_out += tp.ntap;
-            stage_per_tile += global[k] ? 0.0 : (double)g.RR * g.RC;
             plan.pairs.push_back(tp);
             bt.pair_end = (int)plan.pairs.size();
-            if (!global[k]) bt.tap_end = (int)plan.tap_off.size();
+            if (!global[k] && (!pb.up || pb.lg <= kUpStagedLg)) bt.tap_end = (int)plan.tap_off.size();
         }
         // tap copies follow the regions of each batch in the buffer
         for (int bi = sub.batch_begin; bi < (int)plan.batches.size(); ++bi) {
@@ -223,7 +325,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         }
         sub.pair_end = (int)plan.pairs.size();
         sub.batch_end = (int)plan.batches.size();
-        sub.pad[0] = sub.pad[1] = 0;
+        sub.pad = 0;
         sub.lgTS = 0;
         while ((1 << sub.lgTS) < TS) ++sub.lgTS;
         const int ty = (so.rows + TS - 1) / TS, tx = (so.cols + TS - 1) / TS;
@@ -232,9 +334,9 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 const int vy = std::min(TS, so.rows - a * TS), vx = std::min(TS, so.cols - b * TS);
                 const double outs = (double)vy * vx;
                 // MACs per thread-slot plus staging; small tiles leave threads in groups
-                const double cost = outs * taps_per_out + 2.0 * stage_per_tile + 256.0;
+                const double cost = best * outs;
                 plan.macs += (long long)(outs * taps_per_out);
-                items.push_back({TileItem{o, a * TS, b * TS, 0}, cost});
+                if (level_only <= 0 || so.level == level_only) items.push_back({TileItem{o, a * TS, b * TS, 0}, cost});
             }
     }
     std::stable_sort(items.begin(), items.end(), [](const ItemCost& x, const ItemCost& y) { return x.cost > y.cost; });
@@ -253,6 +355,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
 namespace {
 
 enum Epi { kApply = 0, kApplyNorm = 1, kK1 = 2, kK2 = 3, kResNorm = 4, kObj = 5 };
+constexpr int kUpStagedLgDev = 3;   // must equal the planner's kUpStagedLg
 
 struct EpiArgs {
     const float* x0;          // kK1, kResNorm, kObj
@@ -278,9 +381,11 @@ __device__ __forceinline__ int wrap1(int v, int n) {
     return v - ((v >= n) ? n : 0);
 }
 
+// v mod n for v within a few periods of [0, n) (region origins): no integer division
 __device__ __forceinline__ int pos_mod(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
 }
 
 __device__ __forceinline__ float gw_ratio(float g, float w) {
@@ -288,91 +393,155 @@ __device__ __forceinline__ float gw_ratio(float g, float w) {
     return w > 0.f ? ag / w : (ag > 0.f ? FLT_MAX : 0.f);
 }
 
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+template <int B>
+__device__ __forceinline__ void cp_async_to(unsigned s, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(B) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Issue the asynchronous copies of batch `bi` of tile `w` into buffer S: every staged region
-// (row by row, one warp per row, lanes along the row, periodic wrap) and the batch's taps.
+// (one warp per row, lanes along the row, periodic wrap) and the batch's taps. Lane l copies
+// the row's columns xr = l + 32k; for a down pair (r = 2^lg <= 32) its polyphase destination
+// is then (l & m) * plane + (l >> lg) + k * (32 >> lg): one constant per lane plus a fixed
+// step, so the inner loop is one copy and three additions.
 template <typename T>
 __device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const SubbandDev* __restrict__ sb,
                                             const T* __restrict__ in, const TileItem& w, int bi, T* S) {
     const TileBatch bt = plan.batches[bi];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = kTileThreads / 32;
+    constexpr unsigned ES = sizeof(T);
+    const unsigned S0 = smem_addr(S);
     for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
         const TilePair P = plan.pairs[pi];
-        if (P.mode != kDown && P.mode != kUp) continue;
+        if (P.mode != kDown && P.mode != kUp) break;   // global pairs come last in a subband
         const SubbandDev si = sb[P.in_sb];
         const T* __restrict__ src = in + si.off;
         const int lg = P.lg, m = (1 << lg) - 1;
-        const int Y0 = (P.mode == kDown) ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
-        const int X0 = (P.mode == kDown) ? ((w.tx0 << lg) + P.x0) : ((w.tx0 >> lg) + P.x0);
+        const bool down = P.mode == kDown;
+        const int Y0 = down ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
+        const int X0 = down ? ((w.tx0 << lg) + P.x0) : ((w.tx0 >> lg) + P.x0);
         const int yb = pos_mod(Y0, si.rows), xb = pos_mod(X0, si.cols);
-        const int plane = P.PR * P.PC;
-        T* dst = S + P.soff;
-        for (int yr = warp; yr < P.RR; yr += NW) {
-            int gy = yb + yr;
-            while (gy >= si.rows) gy -= si.rows;
-            const T* __restrict__ row = src + (size_t)gy * si.cols;
-            T* drow = (P.mode == kDown) ? dst + ((yr & m) << lg) * plane + (yr >> lg) * P.PC : dst + yr * P.PC;
-            int gx = xb + lane;
-            while (gx >= si.cols) gx -= si.cols;
-            for (int xr = lane; xr < P.RC; xr += 32) {
-                const int idx = (P.mode == kDown) ? ((xr & m) * plane + (xr >> lg)) : xr;
-                cp_async(drow + idx, row + gx, (int)sizeof(T));
-                gx += 32;
+        const int plane = P.PS;
+        const unsigned base = S0 + (unsigned)P.soff * ES;
+        if (!down || lg <= 5) {
+            const int colc = down ? ((lane & m) * plane + (lane >> lg)) : lane;
+            const unsigned step = (unsigned)(down ? (32 >> lg) : 32) * ES;
+            for (int yr = warp; yr < P.RR; yr += NW) {
+                int gy = yb + yr;
+                while (gy >= si.rows) gy -= si.rows;
+                const T* __restrict__ row = src + (size_t)gy * si.cols;
+                const int rowoff = down ? (((yr & m) << lg) * plane + (yr >> lg) * P.PC) : yr * P.PC;
+                unsigned d = base + (unsigned)(rowoff + colc) * ES;
+                int gx = xb + lane;
                 while (gx >= si.cols) gx -= si.cols;
+                for (int xr = lane; xr < P.RC; xr += 32) {
+                    cp_async_to<ES>(d, row + gx);
+                    d += step;
+                    gx += 32;
+                    while (gx >= si.cols) gx -= si.cols;
+                }
+            }
+        } else {
+            for (int yr = warp; yr < P.RR; yr += NW) {
+                int gy = yb + yr;
+                while (gy >= si.rows) gy -= si.rows;
+                const T* __restrict__ row = src + (size_t)gy * si.cols;
+                const int rowoff = ((yr & m) << lg) * plane + (yr >> lg) * P.PC;
+                int gx = xb + lane;
+                while (gx >= si.cols) gx -= si.cols;
+                for (int xr = lane; xr < P.RC; xr += 32) {
+                    cp_async_to<ES>(base + (unsigned)(rowoff + (xr & m) * plane + (xr >> lg)) * ES, row + gx);
+                    gx += 32;
+                    while (gx >= si.cols) gx -= si.cols;
+                }
             }
         }
     }
     const int nt = bt.tap_end - bt.tap_begin;
-    int* toff = reinterpret_cast<int*>(S) + bt.tap_soff;
-    T* tval = S + bt.val_soff;
-    const T* __restrict__ vals = tvals<T>(plan);
+    const unsigned toff = S0 + (unsigned)bt.tap_soff * 4u, tval = S0 + (unsigned)bt.val_soff * ES;
+    const T* __restrict__ vals = tvals<T>(plan) + bt.tap_begin;
+    const int* __restrict__ offs = plan.tap_off + bt.tap_begin;
     for (int j = threadIdx.x; j < nt; j += kTileThreads) {
-        cp_async(toff + j, plan.tap_off + bt.tap_begin + j, 4);
-        cp_async(tval + j, vals + bt.tap_begin + j, (int)sizeof(T));
+        cp_async_to<4>(toff + 4u * j, offs + j);
+        cp_async_to<ES>(tval + ES * j, vals + j);
     }
 }
 
-// Outputs of this thread in a TS x TS tile: TS = 32 -> 4 outputs (rows ly + 8e); smaller
-// tiles -> 1 output, with G thread groups splitting the taps.
+// Outputs of this thread in a TS x TS tile. TS = 32, or TS = 8 / 16 with the e4 map: 4
+// outputs in row ly at columns lx + sx e (sx = TS / 4, lx < sx), so the e-th output of a
+// down pair is sx e words after the first in the polyphase plane (an immediate offset);
+// G = 1024 / TS^2 thread groups split the taps. Otherwise 1 output per thread and
+// G = 256 / TS^2 groups.
 struct ThreadMap {
     int E, G, g, nout;
-    int ly[4], lx[4];
+    int sx, lgsx;     // column stride of the 4 outputs (TS >= 8)
+    int ly, lx;       // first output of this thread (row, column within the tile)
 };
 
 __device__ __forceinline__ ThreadMap thread_map(const TileSub& sub) {
     ThreadMap tm;
     const int t = threadIdx.x, TS = sub.TS, lgTS = sub.lgTS;
     tm.nout = TS * TS;
-    if (TS == 32) {
+    if (TS == 32 || (TS >= 8 && sub.e4)) {
         tm.E = 4;
-        tm.G = 1;
-        tm.g = 0;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            tm.lx[e] = t & 31;
-            tm.ly[e] = (t >> 5) + 8 * e;
-        }
+        tm.lgsx = lgTS - 2;
+        tm.sx = 1 << tm.lgsx;
+        const int lgper = 2 * lgTS - 2;             // threads per group: TS^2 / 4
+        tm.G = kTileThreads >> lgper;
+        tm.g = t >> lgper;
+        const int u = t & ((1 << lgper) - 1);
+        tm.lx = u & (tm.sx - 1);
+        tm.ly = u >> tm.lgsx;
     } else {
         tm.E = 1;
+        tm.sx = tm.lgsx = 0;
         tm.G = kTileThreads >> (2 * lgTS);
         tm.g = t >> (2 * lgTS);
         const int oi = t & (tm.nout - 1);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            tm.lx[e] = oi & (TS - 1);
-            tm.ly[e] = oi >> lgTS;
-        }
+        tm.lx = oi & (TS - 1);
+        tm.ly = oi >> lgTS;
     }
     return tm;
+}
+
+// Down pair, 4 outputs SX words apart in the plane; taps j = j0, j0 + G, ...
+template <int SX, typename T>
+__device__ __forceinline__ void down_taps4(const int* __restrict__ to, const T* __restrict__ tv, int j0, int n, int G,
+                                           const T* __restrict__ Sb, T (&acc)[4]) {
+#pragma unroll 2
+    for (int j = j0; j < n; j += G) {
+        const T v = tv[j];
+        const T* s = Sb + to[j];
+        acc[0] = fma(v, s[0], acc[0]);
+        acc[1] = fma(v, s[SX], acc[1]);
+        acc[2] = fma(v, s[2 * SX], acc[2]);
+        acc[3] = fma(v, s[3 * SX], acc[3]);
+    }
+}
+
+// Up pair with staged phase tables and r dividing the output stride sx: the 4 outputs of a
+// thread share one phase and their coarse columns are STEP = sx / r apart; taps j0, j0 + G, ...
+template <int STEP, typename T>
+__device__ __forceinline__ void up_taps4(const int* __restrict__ to, const T* __restrict__ tv, int j0, int n, int G,
+                                         int rr, const T* __restrict__ Sb, T (&acc)[4]) {
+    to += j0 * rr;
+    tv += j0 * rr;
+    const int stp = G * rr;
+    for (int j = j0; j < n; j += G) {
+        const int o = *to;
+        const T v = *tv;
+        to += stp;
+        tv += stp;
+        const T* s = Sb + o;
+        acc[0] = fma(v, s[0], acc[0]);
+        acc[1] = fma(v, s[STEP], acc[1]);
+        acc[2] = fma(v, s[2 * STEP], acc[2]);
+        acc[3] = fma(v, s[3 * STEP], acc[3]);
+    }
 }
 
 // Accumulate the pairs of batch `bi` of tile `w` (staged in S) into acc.
@@ -389,83 +558,81 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const Sub
         const TilePair P = plan.pairs[pi];
         const int lg = P.lg, r = 1 << lg, m = r - 1;
         if (P.mode == kDown) {
-            int base[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) base[e] = tm.ly[e] * P.PC + tm.lx[e];
             const int* __restrict__ to = soffs + P.tap_begin;
             const T* __restrict__ tv = svals + P.tap_begin;
-            int j = g;
+            const T* __restrict__ Sb = S + tm.ly * P.PC + tm.lx;
             if (E == 4) {
-                for (; j + 1 < P.ntap; j += 2) {
-                    const int o0 = to[j], o1 = to[j + 1];
-                    const T v0 = tv[j], v1 = tv[j + 1];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]] + v1 * S[o1 + base[e]];
-                }
-                for (; j < P.ntap; ++j) {
-                    const int o0 = to[j];
-                    const T v0 = tv[j];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
-                }
+                if (tm.sx == 8) down_taps4<8, T>(to, tv, g, P.ntap, G, Sb, acc);
+                else if (tm.sx == 4) down_taps4<4, T>(to, tv, g, P.ntap, G, Sb, acc);
+                else down_taps4<2, T>(to, tv, g, P.ntap, G, Sb, acc);
             } else {
-                const T* __restrict__ Sb = S + base[0];
                 T a0 = 0, a1 = 0;
+                int j = g;
                 for (; j + G < P.ntap; j += 2 * G) {
-                    a0 += tv[j] * Sb[to[j]];
-                    a1 += tv[j + G] * Sb[to[j + G]];
+                    a0 = fma(tv[j], Sb[to[j]], a0);
+                    a1 = fma(tv[j + G], Sb[to[j + G]], a1);
                 }
-                if (j < P.ntap) a0 += tv[j] * Sb[to[j]];
+                if (j < P.ntap) a0 = fma(tv[j], Sb[to[j]], a0);
                 acc[0] += a0 + a1;
             }
         } else if (P.mode == kUp) {
+            // the phase tables (r^2 interleaved phases per tap slot) stay in global memory:
+            // neighbouring outputs read neighbouring phases, and every tile of the subband
+            // reads the same table, so these loads are coalesced L1/L2 hits
             const int rr = r * r;
-            const int py0 = w.ty0 >> lg, px0 = w.tx0 >> lg;
-            int base[4], ph[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int yy = w.ty0 + tm.ly[e], xx = w.tx0 + tm.lx[e];
-                base[e] = ((yy >> lg) - py0) * P.PC + ((xx >> lg) - px0);
-                ph[e] = ((yy & m) << lg) + (xx & m);
-            }
-            if (E == 1 || r <= 8) {
-                const int* __restrict__ to = soffs + P.tap_begin + ph[0];
-                const T* __restrict__ tv = svals + P.tap_begin + ph[0];
-                if (E == 4) {
-                    for (int j = 0; j < P.ntap; ++j) {
-                        const int o0 = to[j * rr];
-                        const T v0 = tv[j * rr];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) acc[e] += v0 * S[o0 + base[e]];
-                    }
-                } else {
-                    const T* __restrict__ Sb = S + base[0];
-                    T a0 = 0, a1 = 0;
-                    int j = g;
-                    for (; j + G < P.ntap; j += 2 * G) {
-                        a0 += tv[j * rr] * Sb[to[j * rr]];
-                        a1 += tv[(j + G) * rr] * Sb[to[(j + G) * rr]];
-                    }
-                    if (j < P.ntap) a0 += tv[j * rr] * Sb[to[j * rr]];
-                    acc[0] += a0 + a1;
-                }
-            } else {
+            const int py = w.ty0 + tm.ly, px = w.tx0 + tm.lx;
+            const int rowb = ((py >> lg) - (w.ty0 >> lg)) * P.PC;
+            const bool st = lg <= kUpStagedLgDev;   // phase tables staged with the batch
+            const int* __restrict__ gto = (st ? soffs : plan.tap_off) + P.tap_begin;
+            const T* __restrict__ gtv = (st ? svals : gvals) + P.tap_begin;
+            if (E == 4 && st && lg <= tm.lgsx) {
+                const int ph = ((py & m) << lg) + (px & m);
+                const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
+                const int stepc = tm.lgsx - lg;   // log2 of the coarse column step
+                if (stepc == 2) up_taps4<4, T>(gto + ph, gtv + ph, g, P.ntap, G, rr, Sb, acc);
+                else if (stepc == 1) up_taps4<2, T>(gto + ph, gtv + ph, g, P.ntap, G, rr, Sb, acc);
+                else up_taps4<1, T>(gto + ph, gtv + ph, g, P.ntap, G, rr, Sb, acc);
+            } else if (E == 4) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int* __restrict__ to = soffs + P.tap_begin + ph[e];
-                    const T* __restrict__ tv = svals + P.tap_begin + ph[e];
-                    for (int j = g; j < P.ntap; j += G) acc[e] += tv[j * rr] * S[to[j * rr] + base[e]];
+                    const int pxe = px + tm.sx * e;
+                    const int ph = ((py & m) << lg) + (pxe & m);
+                    const T* __restrict__ Sb = S + rowb + ((pxe >> lg) - (w.tx0 >> lg));
+                    const int* __restrict__ to = gto + ph + g * rr;
+                    const T* __restrict__ tv = gtv + ph + g * rr;
+                    const int stp = G * rr;
+                    T a = 0;
+                    for (int j = g; j < P.ntap; j += G) {
+                        a = fma(*tv, Sb[*to], a);
+                        to += stp;
+                        tv += stp;
+                    }
+                    acc[e] += a;
                 }
+            } else {
+                const int ph = ((py & m) << lg) + (px & m);
+                const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
+                const int* __restrict__ to = gto + ph + g * rr;
+                const T* __restrict__ tv = gtv + ph + g * rr;
+                const int stp = G * rr;
+                T a = 0;
+                for (int j = g; j < P.ntap; j += G) {
+                    a = fma(*tv, Sb[*to], a);
+                    to += stp;
+                    tv += stp;
+                }
+                acc[0] += a;
             }
         } else {
-            // gather from global memory (regions larger than the shared-memory budget)
+            // gather from global memory (regions larger than the shared-memory budget, or
+            // too little reuse to pay for staging)
             const SubbandDev si = sb[P.in_sb];
             const T* __restrict__ src = in + si.off;
             const int R = si.rows, C = si.cols;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (e >= E) continue;
-                const int py = w.ty0 + tm.ly[e], px = w.tx0 + tm.lx[e];
+                const int py = w.ty0 + tm.ly, px = w.tx0 + tm.lx + tm.sx * e;
                 if (py >= so.rows || px >= so.cols) continue;
                 int by, bx, tb, step;
                 if (P.mode == kDownGlobal) {
@@ -480,10 +647,19 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const Sub
                     step = r * r;
                 }
                 T a = 0;
-                for (int j = g; j < P.ntap; j += G) {
-                    const int pk = __ldg(plan.tap_off + tb + j * step);
-                    const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
-                    a += __ldg(gvals + tb + j * step) * src[(size_t)yy * C + xx];
+                // interior: every tap of the pair lands inside the input subband, no wrap
+                const bool inside = by + P.y0 >= 0 && by + P.y0 + P.RR <= R && bx + P.x0 >= 0 && bx + P.x0 + P.RC <= C;
+                if (inside) {
+                    const T* __restrict__ bp = src + (size_t)by * C + bx;
+                    const int* __restrict__ tl = plan.tap_lin + tb;
+                    const T* __restrict__ tv = gvals + tb;
+                    for (int j = g; j < P.ntap; j += G) a += __ldg(tv + j * step) * __ldg(bp + __ldg(tl + j * step));
+                } else {
+                    for (int j = g; j < P.ntap; j += G) {
+                        const int pk = __ldg(plan.tap_off + tb + j * step);
+                        const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
+                        a += __ldg(gvals + tb + j * step) * src[(size_t)yy * C + xx];
+                    }
                 }
                 acc[e] += a;
             }
@@ -495,10 +671,16 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const Sub
 template <typename T>
 __device__ __forceinline__ void group_reduce(const ThreadMap& tm, T (&acc)[4], T* red_buf) {
     if (tm.G > 1) {
-        red_buf[threadIdx.x] = acc[0];
+        const int per = kTileThreads / tm.G;   // threads per group
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (e < tm.E) red_buf[e * kTileThreads + threadIdx.x] = acc[e];
         __syncthreads();
         if (tm.g == 0)
-            for (int k = 1; k < tm.G; ++k) acc[0] += red_buf[threadIdx.x + k * tm.nout];
+            for (int k = 1; k < tm.G; ++k)
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (e < tm.E) acc[e] += red_buf[e * kTileThreads + threadIdx.x + k * per];
     }
 }
 
@@ -516,7 +698,7 @@ __device__ __forceinline__ void epilogue(const TileItem& w, const SubbandDev& so
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         if (e >= tm.E) continue;
-        const int py = w.ty0 + tm.ly[e], px = w.tx0 + tm.lx[e];
+        const int py = w.ty0 + tm.ly, px = w.tx0 + tm.lx + tm.sx * e;
         if (py >= so.rows || px >= so.cols) continue;
         const size_t i = so.off + (size_t)py * so.cols + px;
         const int mR = (1 << so.lgR) - 1;
@@ -558,13 +740,12 @@ __device__ __forceinline__ void epilogue(const TileItem& w, const SubbandDev& so
 // Single problem: persistent CTAs, heaviest tiles first, (tile, batch) double buffering
 // ---------------------------------------------------------------------------------------
 template <typename T, int EPI>
-__global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T* __restrict__ in,
+__global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const T* __restrict__ in,
                                                             T* __restrict__ out, EpiArgs ep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const buf0 = reinterpret_cast<T*>(smem_raw);
     T* const buf1 = buf0 + A.plan.buf_elems;
-    __shared__ T red_buf[kTileThreads];
-    __shared__ int s_next;
+    __shared__ T red_buf[4 * kTileThreads];
     if (EPI == kK1 || EPI == kK2) {
         if (*(volatile int*)&ep.st->stop) return;
     }
@@ -576,6 +757,7 @@ __global__ void __launch_bounds__(kTileThreads) tile_kernel(TileArgs A, const T*
         const int k = ep.st->k;
         beta = (float)(k - 1) / (float)(k + 2);
     }
+    __shared__ int s_next;
     if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
     __syncthreads();
     int it = s_next;
@@ -674,11 +856,11 @@ __device__ __forceinline__ void flush_partials(Partials& pt, double* sums, doubl
 }
 
 template <int EPI>
-__global__ void __launch_bounds__(kTileThreads) tile_batch_kernel(BatchArgs B) {
+__global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* const buf0 = reinterpret_cast<float*>(smem_raw);
     float* const buf1 = buf0 + B.buf_elems;
-    __shared__ float red_buf[kTileThreads];
+    __shared__ float red_buf[4 * kTileThreads];
     __shared__ double red_d[2 * kTileThreads / 32];
     __shared__ int s_next;
     const int t = threadIdx.x;

@@ -23,27 +23,35 @@ constexpr int kTileThreads = 256;
 
 enum TileMode { kDown = 0, kUp = 1, kDownGlobal = 2, kUpGlobal = 3 };
 
-struct TilePair {
+// The descriptors are 16-byte aligned so that a thread reads one with 128-bit loads.
+struct alignas(16) TilePair {
     int in_sb;
     int soff;         // staged: element offset of this pair's region in the tile's buffer
     int mode;         // TileMode
     int lg;           // log2 of the scale ratio r
     int RR, RC;       // staged region rows / cols (input units for down, P units for up)
     int PR, PC;       // plane rows / cols (down: ceil(RR / r), ceil(RC / r) padded; up: RR, RC padded)
+    int PS;           // down: element stride between polyphase planes (>= PR * PC)
     int y0, x0;       // region origin: down Y0 = (ty0 << lg) + y0; up Y0 = (ty0 >> lg) + y0
     int tap_begin;    // first tap (up: phase-interleaved, index tap_begin + j r^2 + phase)
     int ntap;         // down: taps; up: padded taps per phase
 };
 
-struct TileSub {      // per output subband
+struct alignas(16) TileSub {      // per output subband
     int TS;           // tile side (a power of two)
     int lgTS;
     int pair_begin, pair_end;
     int batch_begin, batch_end;   // batches of pairs whose staged regions share one buffer
-    int pad[2];
+    int e4;           // 1: 4 outputs per thread (TS >= 8), 0: 1 output per thread
+    int pad;
 };
 
-struct TileBatch {    // pairs [pair_begin, pair_end) of one subband, staged together
+struct TileTune {     // autotuner's choice for one output subband (ts = 0: the planner's)
+    int ts;
+    int e4;
+};
+
+struct alignas(16) TileBatch {    // pairs [pair_begin, pair_end) of one subband, staged together
     int pair_begin, pair_end;
     int tap_begin, tap_end;       // taps of the staged pairs, copied to shared memory
     int tap_soff;                 // element offset of the tap offsets (ints) in the buffer
@@ -51,7 +59,7 @@ struct TileBatch {    // pairs [pair_begin, pair_end) of one subband, staged tog
     int pad[2];
 };
 
-struct TileItem {
+struct alignas(16) TileItem {
     int o;
     int ty0, tx0;
     int pad;
@@ -63,6 +71,7 @@ struct TilePlanDev {
     const TileBatch* batches;
     const TileItem* items;
     const int* tap_off;       // staged: offset in shared memory; global: (dy << 16) | (dx & 0xffff)
+    const int* tap_lin;       // global pairs: dy * (input columns) + dx (interior fast path)
     const float* tap_v;
     const double* tap_v64;
     int n_items;
@@ -76,6 +85,7 @@ struct TilePlanHost {
     std::vector<TileBatch> batches;
     std::vector<TileItem> items;
     std::vector<int> tap_off;
+    std::vector<int> tap_lin;
     std::vector<float> tap_v;
     std::vector<double> tap_v64;
     std::vector<double> item_cost;   // estimated cost of every item (items are sorted by it)
@@ -90,8 +100,11 @@ struct TileEntry {             // one tap of one pair, in gather form
 };
 
 // Build the plan of one operator for element size `esize` and a per-buffer shared-memory
-// budget (a batch of staged regions shares one buffer; a CTA holds two buffers).
-TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget);
+// budget (a batch of staged regions shares one buffer; a CTA holds two buffers); `ctas` is
+// the number of CTAs that will share the tiles (it caps the cost of one tile).
+TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget,
+                            int ctas = 456, const std::vector<TileTune>* tune = nullptr, int level_only = 0,
+                            double cap_share = 2.0);
 
 struct TileQueue {             // device counters of one operator launch
     unsigned int next;         // next work item

@@ -156,6 +156,9 @@ struct wdb_theta {
     wdb::OpHost fwd_h, adj_h;
     wdb::OpDev fwd{}, adj{};
     wdb::TilePlanHost tplan[2][2];         // [0 Theta_K, 1 Theta_K^T][0 FP32, 1 FP64]
+    std::vector<wdb::TileEntry> tent[2];   // gather-form taps of Theta_K and Theta_K^T (plan input)
+    int plan_ctas = 0;                     // CTAs the plans are balanced for
+    int tuned = 0;                         // 1: the FP32 plans were autotuned on this GPU
     wdb::TileArgs targs[2][2];
     int part_len = 0;                      // capacity (CTAs) of the per-CTA partial buffers
     std::vector<void*> allocs;             // device buffers owned by the handle
