@@ -120,7 +120,7 @@ class Clocks:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                                          "-lms", "20"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
@@ -576,7 +576,7 @@ def run_warm(args):
                       "l2": "flushed before each timed solve"},
            "results": res, "network_forward_ms": f_ms, "train_s": log.seconds, "pairs_s": gen_s,
            "train_loss": {"first": float(np.mean(log.losses[:5])), "last": float(np.mean(log.losses[-20:]))},
-           "starts_used": {str(k): starts.count(k) for k in (0, 1, 2)}}
+           "starts_used": {"network": starts.count(1), "cold_fallback": starts.count(0)}}
     print(json.dumps(out))
     return 0
 

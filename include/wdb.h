@@ -263,11 +263,11 @@ wdb_status wdb_cnn_train_step(wdb_cnn* net, const float* u_dev, const float* tar
 /* Checkpoint: shape, step count, seed, parameters and Adam moments. */
 wdb_status wdb_cnn_save(const wdb_cnn* net, const char* path);
 wdb_status wdb_cnn_load(const char* path, void* stream, wdb_cnn** out);
-/* wdb_solve started from the network: of x = 0 (the cold start), x = Psi* network(u) and
- * x = Psi* u, the one with the lowest objective E starts FISTA; *start_used (may be NULL)
- * reports it as 0, 1 or 2. The network must have the operator's image size and
- * params->x_init_dev must be NULL. The stopping rule is the caller's, so the result solves
- * the same problem as wdb_solve. Synchronises `stream`. */
+/* wdb_solve started from the network: x_init = Psi* network(u) when its objective E is below
+ * that of x = 0 (E(0) = 1/2 ||Psi* u||^2), else the cold start x = 0 (the fallback);
+ * *start_used (may be NULL) reports 1 (network) or 0 (cold). The network must have the
+ * operator's image size and params->x_init_dev must be NULL. The stopping rule is the
+ * caller's, so the result solves the same problem as wdb_solve. Synchronises `stream`. */
 wdb_status wdb_solve_warm(wdb_theta* th, wdb_cnn* net, const float* u_dev, float* x_dev,
                           const wdb_solve_params* params, void* stream, wdb_solve_result* result,
                           int* start_used);

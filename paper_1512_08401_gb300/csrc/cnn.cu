@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "device_util.cuh"
@@ -105,6 +106,136 @@ __global__ void __launch_bounds__(256) conv3x3_kernel(const TIN* __restrict__ in
         if (co >= CO) break;
         float v = acc[co];
         if (relu) v = fmaxf(v, 0.f);
+        const size_t o = ((size_t)b * CO + co) * plane + pix;
+        if (mask && !(__bfloat162float(mask[o]) > 0.f)) v = 0.f;
+        if (residual) v += residual[(size_t)b * plane + pix];
+        if (out_mode == 0) reinterpret_cast<bf16*>(out)[o] = __float2bfloat16(v);
+        else if (out_mode == 1) reinterpret_cast<float*>(out)[o] = v;
+        else reinterpret_cast<float*>(out)[o] += v;
+    }
+}
+
+// Tensor-core 3x3 convolution of BF16 feature maps (2 <= C_in, C_out <= 32), as an implicit
+// GEMM per 16 x 16 output tile: M = 256 pixels, N = C_out (padded to 32), K = 9 taps x C_in
+// (padded to KCH = 16 or 32). The input tile with its periodic halo is staged channels-last
+// ([18 x 18 pixels][kCP channels]) and the weights as [tap][C_out][kCP], both BF16, so that
+// every A fragment (16 pixels of one tile row, 16 channels) and B fragment (8 output
+// channels, 16 input channels) is one ldmatrix; mma.sync m16n8k16 (BF16 in, FP32 accumulate).
+// Warp w computes tile rows 2w and 2w + 1. The FP32 results go through shared memory
+// ([C_out][256 pixels]) so that the stores to the NCHW output are coalesced.
+constexpr int kCP = 40;                       // channel pitch in shared memory (80 B: no ldmatrix bank conflicts)
+constexpr int kMmaHalo = 18 * 18 * kCP;       // bf16 elements of the staged input tile
+constexpr int kMmaW = 9 * 32 * kCP;           // bf16 elements of the staged weights
+constexpr size_t kMmaSmem = sizeof(bf16) * (kMmaHalo + kMmaW);
+
+__device__ __forceinline__ void ldsm_x4(unsigned addr, unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0, %1, %2, %3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+template <int KCH>
+__global__ void __launch_bounds__(256) conv3x3_mma_kernel(const bf16* __restrict__ in, int CI, int CO, int H, int W,
+                                                          const bf16* __restrict__ wt, const float* __restrict__ bias,
+                                                          int out_mode, void* out, int relu,
+                                                          const bf16* __restrict__ mask,
+                                                          const float* __restrict__ residual) {
+    extern __shared__ __align__(16) unsigned char cnn_smem[];
+    bf16* halo = reinterpret_cast<bf16*>(cnn_smem);   // [18*18][kCP]
+    bf16* ws = halo + kMmaHalo;                        // [9][32][kCP]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int b = blockIdx.z;
+    const int ty0 = blockIdx.y * kT, tx0 = blockIdx.x * kT;
+    const size_t plane = (size_t)H * W;
+    const bf16 zero = __float2bfloat16(0.f);
+    // stage the input tile (periodic halo), channels-last; channels CI..KCH-1 are zero
+    const bf16* inb = in + (size_t)b * CI * plane;
+    for (int i = t; i < KCH * kHalo * kHalo; i += 256) {
+        const int ci = i / (kHalo * kHalo), q = i - ci * kHalo * kHalo;
+        const int y = q / kHalo, x = q - y * kHalo;
+        bf16 v = zero;
+        if (ci < CI) {
+            int gy = ty0 + y - 1, gx = tx0 + x - 1;
+            while (gy < 0) gy += H;
+            while (gy >= H) gy -= H;
+            while (gx < 0) gx += W;
+            while (gx >= W) gx -= W;
+            v = inb[(size_t)ci * plane + (size_t)gy * W + gx];
+        }
+        halo[q * kCP + ci] = v;
+    }
+    // weights [CO][CI][3][3] -> [tap][co][ci], zero outside CO x CI
+    for (int i = t; i < 9 * 32 * KCH; i += 256) {
+        const int tap = i / (32 * KCH), r = i - tap * 32 * KCH;
+        const int co = r / KCH, ci = r - co * KCH;
+        ws[(tap * 32 + co) * kCP + ci] = (co < CO && ci < CI) ? wt[((size_t)co * CI + ci) * 9 + tap] : zero;
+    }
+    __syncthreads();
+    float acc[2][4][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[m][nt][k] = 0.f;
+    const unsigned hb = (unsigned)__cvta_generic_to_shared(halo), wb = (unsigned)__cvta_generic_to_shared(ws);
+    // ldmatrix row addresses: A rows are pixels (lane % 16), k half (lane / 16);
+    // B rows are output channels (lane % 8 + 8 (lane / 16)), k half ((lane / 8) % 2)
+    const int a_pix = lane & 15, a_k = (lane >> 4) * 8;
+    const int b_n = (lane & 7) + ((lane >> 4) << 3), b_k = ((lane >> 3) & 1) * 8;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap - ky * 3;
+#pragma unroll
+        for (int kc = 0; kc < KCH / 16; ++kc) {
+            unsigned a[2][4], bf[2][4];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+                const int pix = (2 * warp + m + ky) * kHalo + a_pix + kx;
+                ldsm_x4(hb + 2u * (unsigned)(pix * kCP + kc * 16 + a_k), a[m][0], a[m][1], a[m][2], a[m][3]);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                ldsm_x4(wb + 2u * (unsigned)((tap * 32 + 16 * h + b_n) * kCP + kc * 16 + b_k), bf[h][0], bf[h][1],
+                        bf[h][2], bf[h][3]);
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+                    mma_bf16(acc[m][nt], a[m][0], a[m][1], a[m][2], a[m][3], bf[nt >> 1][(nt & 1) * 2],
+                             bf[nt >> 1][(nt & 1) * 2 + 1]);
+        }
+    }
+    __syncthreads();
+    // results -> shared [co][256 pixels] (FP32), then coalesced stores
+    float* res = reinterpret_cast<float*>(cnn_smem);
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int px = (lane >> 2) + ((k >> 1) << 3);
+                const int co = nt * 8 + (lane & 3) * 2 + (k & 1);
+                res[co * 256 + (2 * warp + m) * kT + px] = acc[m][nt][k];
+            }
+    __syncthreads();
+    for (int i = t; i < CO * 256; i += 256) {
+        const int co = i >> 8, p = i & 255;
+        const int oy = ty0 + (p >> 4), ox = tx0 + (p & 15);
+        if (oy >= H || ox >= W) continue;
+        float v = res[i] + (bias ? bias[co] : 0.f);
+        if (relu) v = fmaxf(v, 0.f);
+        const size_t pix = (size_t)oy * W + ox;
         const size_t o = ((size_t)b * CO + co) * plane + pix;
         if (mask && !(__bfloat162float(mask[o]) > 0.f)) v = 0.f;
         if (residual) v += residual[(size_t)b * plane + pix];
@@ -274,6 +405,16 @@ __global__ void __launch_bounds__(256) mse_kernel(const float* __restrict__ v, c
     if (grid_reduce<1>(a, 0u, part, counter, tot) && threadIdx.x == 0) out[0] = tot[0] / (double)n;
 }
 
+// tot = sum v^2 (FP64 tree)
+__global__ void __launch_bounds__(256) sumsq_kernel(const float* __restrict__ v, size_t n, double* part,
+                                                    unsigned int* counter, double* out) {
+    float s = 0.f, c = 0.f;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        neu_add(s, c, v[i] * v[i]);
+    double a[1] = {(double)s + (double)c}, tot[1];
+    if (grid_reduce<1>(a, 0u, part, counter, tot) && threadIdx.x == 0) out[0] = tot[0];
+}
+
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, bf16* __restrict__ pb, long long n, float lr, float b1, float b2,
                             float eps, float c1, float c2) {
@@ -379,6 +520,27 @@ wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int ou
     }
     const float* bias = flipped ? nullptr : n->p + cl.b_off;
     dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT, B);
+    if constexpr (std::is_same<TIN, bf16>::value) {
+        if (CI >= 2 && CO >= 2 && CI <= kCMax && CO <= kCMax) {   // BF16 feature maps: tensor cores
+            static bool attr = false;
+            if (!attr) {
+                WDB_CK(cudaFuncSetAttribute(conv3x3_mma_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kMmaSmem));
+                WDB_CK(cudaFuncSetAttribute(conv3x3_mma_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kMmaSmem));
+                attr = true;
+            }
+            if (CI <= 16)
+                conv3x3_mma_kernel<16><<<grid, 256, kMmaSmem, st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
+                                                                    mask, residual);
+            else
+                conv3x3_mma_kernel<32><<<grid, 256, kMmaSmem, st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
+                                                                    mask, residual);
+            count_launch();
+            WDB_CK(cudaGetLastError());
+            return WDB_OK;
+        }
+    }
     if (CO <= 1) {
         conv3x3_kernel<1, TIN><<<grid, 256, conv_smem(CI, 1), st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
                                                                      mask, residual);
@@ -710,25 +872,26 @@ wdb_status wdb_solve_warm(wdb_theta* th, wdb_cnn* n, const float* u_dev, float* 
     if (params->x_init_dev) return set_error(WDB_EINVAL, "x_init_dev must be NULL: the network provides the start");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const long long N = th->lay.N;
-    float* v = n->g0;       // network output (image), then zeros
-    float* xw = n->g1;      // its coefficients
+    float* v = n->g0;       // network output (image)
+    float* xw = n->g1;      // its coefficients: the candidate start
     float* x0 = n->dv;      // coefficients of u
     float* scratch = n->g2; // N/2 floats of DWT scratch
     WDB_TRY(forward(n, u_dev, v, 1, st));
     WDB_TRY(dwt2<float>(v, xw, th->lay, th->filt, scratch, st));
     WDB_TRY(dwt2<float>(u_dev, x0, th->lay, th->filt, scratch, st));
-    WDB_CK(cudaMemsetAsync(v, 0, sizeof(float) * N, st));
-    // candidates: 0 (the cold start), the network's start, the observation's coefficients
-    const float* cand[3] = {v, xw, x0};
-    double E[3];
-    int best = 0;
-    for (int c = 0; c < 3; ++c) {
-        WDB_TRY(wdb_theta_objective(th, cand[c], x0, params->lambda, params->w_subband_host, stream, &E[c]));
-        if (std::isfinite(E[c]) && E[c] < E[best]) best = c;
-    }
+    // E(x = 0) = 1/2 ||x0||^2; the network's start is kept only when its E is lower
+    WDB_CK(cudaMemsetAsync(n->counter, 0, sizeof(unsigned int), st));
+    sumsq_kernel<<<std::min(ew(N), 1024), 256, 0, st>>>(x0, (size_t)N, n->part, n->counter, n->d_loss);
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    double Ec = 0.0, Ew = 0.0;
+    WDB_CK(cudaMemcpyAsync(&Ec, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    WDB_TRY(wdb_theta_objective(th, xw, x0, params->lambda, params->w_subband_host, stream, &Ew));   // synchronises
+    Ec *= 0.5;
+    const bool warm = std::isfinite(Ew) && Ew < Ec;
     wdb_solve_params p = *params;
-    p.x_init_dev = best == 0 ? nullptr : cand[best];
-    if (start_used) *start_used = best;
+    p.x_init_dev = warm ? xw : nullptr;
+    if (start_used) *start_used = warm ? 1 : 0;
     return wdb_solve(th, u_dev, x_dev, &p, stream, result);
 }
 

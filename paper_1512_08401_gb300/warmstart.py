@@ -3,8 +3,8 @@
 A U-Net (`wdb.WarmStartNet`, kernels in csrc/cnn.cu) is trained to map an observation u0 to
 the image Psi x* of the minimiser x* of the l1-l2 problem for one blur (one Theta_K). At
 solve time `WarmStartNet.solve_warm` starts FISTA from Psi* network(u0) when that start has a
-lower objective than x = 0 and x = Psi* u0, and the caller's stopping rule is unchanged, so
-the returned x solves the same problem; only the number of iterations changes.
+lower objective than x = 0 (else it falls back to x = 0), and the caller's stopping rule is
+unchanged, so the returned x solves the same problem; only the number of iterations changes.
 
 This module is the host driver: it draws observations from the seeded generator, computes
 x* with the library's own solver, and runs the training loop. Every arithmetic step (solver,

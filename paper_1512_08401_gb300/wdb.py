@@ -434,7 +434,7 @@ class WarmStartNet:
         return loss.value
 
     def solve_warm(self, theta, u, x, stream=None, **kw):
-        """wdb_solve_warm: returns (result dict, start used: 0 zero, 1 network, 2 Psi* u)."""
+        """wdb_solve_warm: returns (result dict, start used: 1 network, 0 cold start x = 0)."""
         p, _keep = make_params(**kw)
         r = SolveResult()
         used = C.c_int()

@@ -177,6 +177,25 @@ def test_rejects_bad_arguments(wdb):
         net.solve_warm(th, torch.zeros(th.N, device="cuda"), x, lam=1e-3)   # 16x16 net, 32x32 operator
 
 
+def test_warm_start_falls_back_to_cold_start(wdb):
+    """A network whose start is worse than x = 0 is not used: the solve is the cold solve."""
+    n, J, lam = 64, 3, 1e-3
+    psf = synthetic.gaussian_psf(1.5, 9)
+    th = wdb.Theta.build(psf, n, n, "db4", J, K=30 * n * n)
+    net = wdb.WarmStartNet(2, 4, n, n, max_batch=1, seed=3)
+    p = net.get_params()
+    p[-37:-1] *= 1e4        # out.W (4 x 9 weights before out.b): a huge correction
+    net.set_params(p)
+    u0, _ = batch(n, 1, seed=21)
+    u = dev(u0).view(-1)
+    x_cold = torch.zeros(th.N, device="cuda")
+    x_warm = torch.zeros(th.N, device="cuda")
+    r_cold = th.solve(u, x_cold, lam=lam, max_iters=50)
+    r_warm, used = net.solve_warm(th, u, x_warm, lam=lam, max_iters=50)
+    assert used == 0
+    assert r_warm["iters"] == r_cold["iters"] and torch.equal(x_warm, x_cold)
+
+
 def test_warm_start_cuts_iterations(wdb):
     """Train on x* of seeded observations for one blur (128^2, Gaussian sigma = 2), then count
     iterations to the same objective targets on held-out observations from three starts:
