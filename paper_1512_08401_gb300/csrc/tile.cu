@@ -206,10 +206,16 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         // first pass: geometry and batch membership (regions plus their taps must fit)
         const int ebudget = budget / esize;
         std::vector<int> batch_of(order.size()), pair_soff(order.size(), 0);
-        std::vector<int> batch_regions(1, 0), batch_taps(1, 0);
+        std::vector<int> batch_regions(1, 0), batch_taps(1, 0), batch_count(1, 0);
         for (size_t q = 0; q < order.size(); ++q) {
             const int k = order[q];
-            if (global[k]) {
+            if (global[k]) {   // global pairs join the last batch while it has room
+                if (batch_count.back() >= kMaxBatchPairs) {
+                    batch_regions.push_back(0);
+                    batch_taps.push_back(0);
+                    batch_count.push_back(0);
+                }
+                batch_count.back() += 1;
                 batch_of[q] = (int)batch_regions.size() - 1;
                 continue;
             }
@@ -222,10 +228,13 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             // taps: one int offset + one value each, rounded to 16 bytes
             auto tap_elems = [&](int ntaps) { return (int)(((long long)ntaps * (4 + esize) + 15) / 16 * 16 / esize); };
             const bool nonempty = batch_regions.back() > 0;
-            if (nonempty && batch_regions.back() + need + tap_elems(batch_taps.back() + nt) > ebudget) {
+            if (nonempty && (batch_regions.back() + need + tap_elems(batch_taps.back() + nt) > ebudget ||
+                             batch_count.back() >= kMaxBatchPairs)) {
                 batch_regions.push_back(0);
                 batch_taps.push_back(0);
+                batch_count.push_back(0);
             }
+            batch_count.back() += 1;
             batch_of[q] = (int)batch_regions.size() - 1;
             pair_soff[q] = batch_regions.back();
             batch_regions.back() += need;
@@ -402,23 +411,46 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// A pair's descriptor with its input subband's geometry, kept in shared memory for the batch
+// (one lane loads each pair's entry, so the per-pair set-up reads shared memory instead of a
+// chain of dependent global loads per thread).
+struct alignas(16) PairSm {
+    TilePair p;
+    long long in_off;
+    int in_rows, in_cols;
+};
+
 // Issue the asynchronous copies of batch `bi` of tile `w` into buffer S: every staged region
 // (one warp per row, lanes along the row, periodic wrap) and the batch's taps. Lane l copies
 // the row's columns xr = l + 32k; for a down pair (r = 2^lg <= 32) its polyphase destination
 // is then (l & m) * plane + (l >> lg) + k * (32 >> lg): one constant per lane plus a fixed
 // step, so the inner loop is one copy and three additions.
+// The batch's pair table `tab` is filled first (one thread per pair, then a barrier that
+// every thread of the CTA reaches).
 template <typename T>
 __device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const SubbandDev* __restrict__ sb,
-                                            const T* __restrict__ in, const TileItem& w, int bi, T* S) {
+                                            const T* __restrict__ in, const TileItem& w, int bi, T* S,
+                                            PairSm* tab) {
     const TileBatch bt = plan.batches[bi];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = kTileThreads / 32;
     constexpr unsigned ES = sizeof(T);
     const unsigned S0 = smem_addr(S);
-    for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
-        const TilePair P = plan.pairs[pi];
-        if (P.mode != kDown && P.mode != kUp) break;   // global pairs come last in a subband
+    const int np = bt.pair_end - bt.pair_begin;
+    if ((int)threadIdx.x < np) {
+        const TilePair P = plan.pairs[bt.pair_begin + threadIdx.x];
         const SubbandDev si = sb[P.in_sb];
+        PairSm& e = tab[threadIdx.x];
+        e.p = P;
+        e.in_off = si.off;
+        e.in_rows = si.rows;
+        e.in_cols = si.cols;
+    }
+    __syncthreads();
+    for (int i = 0; i < np; ++i) {
+        const TilePair P = tab[i].p;
+        if (P.mode != kDown && P.mode != kUp) break;   // global pairs come last in a subband
+        const SubbandDev si{tab[i].in_off, tab[i].in_rows, tab[i].in_cols, 0, 0, 0, 0};
         const T* __restrict__ src = in + si.off;
         const int lg = P.lg, m = (1 << lg) - 1;
         const bool down = P.mode == kDown;
@@ -546,16 +578,17 @@ __device__ __forceinline__ void up_taps4(const int* __restrict__ to, const T* __
 
 // Accumulate the pairs of batch `bi` of tile `w` (staged in S) into acc.
 template <typename T>
-__device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const SubbandDev* __restrict__ sb,
-                                              const T* __restrict__ in, const TileItem& w, const SubbandDev& so,
-                                              int bi, const T* __restrict__ S, const ThreadMap& tm, T (&acc)[4]) {
+__device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* __restrict__ in, const TileItem& w,
+                                              const SubbandDev& so, int bi, const T* __restrict__ S,
+                                              const PairSm* __restrict__ tab, const ThreadMap& tm, T (&acc)[4]) {
     const TileBatch bt = plan.batches[bi];
     const int* __restrict__ soffs = reinterpret_cast<const int*>(S) + bt.tap_soff - bt.tap_begin;
     const T* __restrict__ svals = S + bt.val_soff - bt.tap_begin;
     const T* __restrict__ gvals = tvals<T>(plan);
     const int E = tm.E, G = tm.G, g = tm.g;
-    for (int pi = bt.pair_begin; pi < bt.pair_end; ++pi) {
-        const TilePair P = plan.pairs[pi];
+    const int np = bt.pair_end - bt.pair_begin;
+    for (int i = 0; i < np; ++i) {
+        const TilePair P = tab[i].p;
         const int lg = P.lg, r = 1 << lg, m = r - 1;
         if (P.mode == kDown) {
             const int* __restrict__ to = soffs + P.tap_begin;
@@ -626,9 +659,8 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const Sub
         } else {
             // gather from global memory (regions larger than the shared-memory budget, or
             // too little reuse to pay for staging)
-            const SubbandDev si = sb[P.in_sb];
-            const T* __restrict__ src = in + si.off;
-            const int R = si.rows, C = si.cols;
+            const T* __restrict__ src = in + tab[i].in_off;
+            const int R = tab[i].in_rows, C = tab[i].in_cols;
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (e >= E) continue;
@@ -764,7 +796,10 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
     int bi = (it < plan.n_items) ? plan.subs[plan.items[it].o].batch_begin : 0;
     T* S = buf0;
     T* Snext = buf1;
-    if (it < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[it], bi, S);
+    __shared__ PairSm tab_buf[2][kMaxBatchPairs];
+    PairSm* tab = tab_buf[0];
+    PairSm* tab_next = tab_buf[1];
+    if (it < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[it], bi, S, tab);
     cp_async_commit();
     T acc[4] = {0, 0, 0, 0};
     while (it < plan.n_items) {
@@ -778,13 +813,13 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
             nit = s_next;
             nbi = (nit < plan.n_items) ? plan.subs[plan.items[nit].o].batch_begin : 0;
         }
-        if (nit < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[nit], nbi, Snext);
+        if (nit < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[nit], nbi, Snext, tab_next);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         const SubbandDev so = A.sb[w.o];
         const ThreadMap tm = thread_map(sub);
-        compute_batch<T>(plan, A.sb, in, w, so, bi, S, tm, acc);
+        compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc);
         if (bi + 1 == sub.batch_end) {
             group_reduce<T>(tm, acc, red_buf);
             epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
@@ -796,6 +831,9 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         T* tmp = S;
         S = Snext;
         Snext = tmp;
+        PairSm* tt = tab;
+        tab = tab_next;
+        tab_next = tt;
     }
     cp_async_wait<0>();
     __syncthreads();
@@ -887,11 +925,14 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
     int bi = 0;
     float* S = buf0;
     float* Snext = buf1;
+    __shared__ PairSm tab_buf[2][kMaxBatchPairs];
+    PairSm* tab = tab_buf[0];
+    PairSm* tab_next = tab_buf[1];
     if (it < B.n_items) {
         const BatchItem bw = B.items[it];
         const TilePlanDev& pl = plan_of(bw.p);
         bi = pl.subs[pl.items[bw.item].o].batch_begin;
-        stage_batch<float>(pl, B.probs[bw.p].sb, in_of(bw.p), pl.items[bw.item], bi, S);
+        stage_batch<float>(pl, B.probs[bw.p].sb, in_of(bw.p), pl.items[bw.item], bi, S, tab);
     }
     cp_async_commit();
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -915,14 +956,14 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         if (nit < B.n_items) {
             const BatchItem nb = B.items[nit];
             const TilePlanDev& npl = plan_of(nb.p);
-            stage_batch<float>(npl, B.probs[nb.p].sb, in_of(nb.p), npl.items[nb.item], nbi, Snext);
+            stage_batch<float>(npl, B.probs[nb.p].sb, in_of(nb.p), npl.items[nb.item], nbi, Snext, tab_next);
         }
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         const SubbandDev so = P.sb[w.o];
         const ThreadMap tm = thread_map(sub);
-        compute_batch<float>(pl, P.sb, in_of(bw.p), w, so, bi, S, tm, acc);
+        compute_batch<float>(pl, in_of(bw.p), w, so, bi, S, tab, tm, acc);
         if (bi + 1 == sub.batch_end) {
             group_reduce<float>(tm, acc, red_buf);
             EpiArgs ep{};
@@ -946,6 +987,9 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         float* tmp = S;
         S = Snext;
         Snext = tmp;
+        PairSm* tt = tab;
+        tab = tab_next;
+        tab_next = tt;
     }
     cp_async_wait<0>();
     __syncthreads();

@@ -37,6 +37,8 @@ struct alignas(16) TilePair {
     int ntap;         // down: taps; up: padded taps per phase
 };
 
+constexpr int kMaxBatchPairs = 16;   // pairs per batch (their descriptors sit in shared memory)
+
 struct alignas(16) TileSub {      // per output subband
     int TS;           // tile side (a power of two)
     int lgTS;
