@@ -43,7 +43,7 @@ std::vector<BatchItem> merge_items(const std::vector<wdb_theta*>& th, int op) {
     };
     std::vector<C> all;
     for (int p = 0; p < (int)th.size(); ++p) {
-        const TilePlanHost& h = th[p]->tplan[op][0];
+        const TilePlanHost& h = th[p]->bplan[op];
         for (int i = 0; i < (int)h.items.size(); ++i) all.push_back({BatchItem{p, i}, h.item_cost[i]});
     }
     std::stable_sort(all.begin(), all.end(), [](const C& a, const C& b) { return a.cost > b.cost; });
@@ -104,8 +104,9 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
         s0.target = p.target_objective > 0.0 ? p.target_objective : 0.0;
         WDB_CK(cudaMemcpyAsync(t->d_state, &s0, sizeof s0, cudaMemcpyHostToDevice, st));
         BatchProblem& q = hp[b];
-        q.fwd = t->targs[0][0].plan;
-        q.adj = t->targs[1][0].plan;
+        WDB_TRY(theta_batch_plans(t, st));
+        q.fwd = t->bargs[0].plan;
+        q.adj = t->bargs[1].plan;
         q.sb = t->d_sb;
         q.y = t->d_y;
         q.x = t->d_xs;

@@ -470,6 +470,18 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
 
 TileArgs tile_args(const wdb_theta* th, bool adj, bool fp64) { return th->targs[adj ? 1 : 0][fp64 ? 1 : 0]; }
 
+// Plans for batched solves: the planner's choice with a loose per-tile cap (16 per-CTA
+// shares), since the tiles of many problems share the CTAs; built on first use.
+wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st) {
+    if (th->bplan_ok) return WDB_OK;
+    for (int op = 0; op < 2; ++op) {
+        th->bplan[op] = make_tile_plan(th->lay, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, 16.0);
+        WDB_TRY(upload_plan(th, th->bplan[op], th->bargs[op], st));
+    }
+    th->bplan_ok = true;
+    return WDB_OK;
+}
+
 static wdb_status upload_op(wdb_theta* th, const OpHost& h, OpDev& d, cudaStream_t st) {
     WDB_TRY(upload(th, h.pair_start, const_cast<int**>(&d.pair_start), st));
     WDB_TRY(upload(th, h.pairs, const_cast<PairDesc**>(&d.pairs), st));
