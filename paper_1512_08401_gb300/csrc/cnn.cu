@@ -145,7 +145,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
 
 template <int KCH>
 __global__ void __launch_bounds__(256) conv3x3_mma_kernel(const bf16* __restrict__ in, int CI, int CO, int H, int W,
-                                                          const bf16* __restrict__ wt, const float* __restrict__ bias,
+                                                          const bf16* __restrict__ wlay, const float* __restrict__ bias,
                                                           int out_mode, void* out, int relu,
                                                           const bf16* __restrict__ mask,
                                                           const float* __restrict__ residual) {
@@ -156,28 +156,34 @@ __global__ void __launch_bounds__(256) conv3x3_mma_kernel(const bf16* __restrict
     const int b = blockIdx.z;
     const int ty0 = blockIdx.y * kT, tx0 = blockIdx.x * kT;
     const size_t plane = (size_t)H * W;
-    const bf16 zero = __float2bfloat16(0.f);
-    // stage the input tile (periodic halo), channels-last; channels CI..KCH-1 are zero
-    const bf16* inb = in + (size_t)b * CI * plane;
-    for (int i = t; i < KCH * kHalo * kHalo; i += 256) {
-        const int ci = i / (kHalo * kHalo), q = i - ci * kHalo * kHalo;
-        const int y = q / kHalo, x = q - y * kHalo;
-        bf16 v = zero;
-        if (ci < CI) {
-            int gy = ty0 + y - 1, gx = tx0 + x - 1;
-            while (gy < 0) gy += H;
-            while (gy >= H) gy -= H;
-            while (gx < 0) gx += W;
-            while (gx >= W) gx -= W;
-            v = inb[(size_t)ci * plane + (size_t)gy * W + gx];
-        }
-        halo[q * kCP + ci] = v;
+    // weights, already laid out as [tap][co][kCP] (zeros outside C_out x C_in): 16-byte copies
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(wlay);
+        uint4* dst = reinterpret_cast<uint4*>(ws);
+        for (int i = t; i < kMmaW / 8; i += 256) dst[i] = src[i];
     }
-    // weights [CO][CI][3][3] -> [tap][co][ci], zero outside CO x CI
-    for (int i = t; i < 9 * 32 * KCH; i += 256) {
-        const int tap = i / (32 * KCH), r = i - tap * 32 * KCH;
-        const int co = r / KCH, ci = r - co * KCH;
-        ws[(tap * 32 + co) * kCP + ci] = (co < CO && ci < CI) ? wt[((size_t)co * CI + ci) * 9 + tap] : zero;
+    // input tile with its periodic halo, channels-last: one pixel per thread, channel pairs
+    // packed into 32-bit words, 16-byte stores; channels CI..KCH-1 are zero
+    const bf16* inb = in + (size_t)b * CI * plane;
+    for (int q = t; q < kHalo * kHalo; q += 256) {
+        const int y = q / kHalo, x = q - y * kHalo;
+        int gy = ty0 + y - 1, gx = tx0 + x - 1;
+        while (gy < 0) gy += H;
+        while (gy >= H) gy -= H;
+        while (gx < 0) gx += W;
+        while (gx >= W) gx -= W;
+        const bf16* src = inb + (size_t)gy * W + gx;
+        unsigned packed[KCH / 2];
+#pragma unroll
+        for (int c = 0; c < KCH / 2; ++c) {
+            const unsigned short lo = (2 * c < CI) ? __bfloat16_as_ushort(src[(size_t)(2 * c) * plane]) : 0;
+            const unsigned short hi = (2 * c + 1 < CI) ? __bfloat16_as_ushort(src[(size_t)(2 * c + 1) * plane]) : 0;
+            packed[c] = (unsigned)lo | ((unsigned)hi << 16);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(halo + q * kCP);
+#pragma unroll
+        for (int c = 0; c < KCH / 8; ++c)
+            dst[c] = make_uint4(packed[4 * c], packed[4 * c + 1], packed[4 * c + 2], packed[4 * c + 3]);
     }
     __syncthreads();
     float acc[2][4][4];
@@ -243,6 +249,16 @@ __global__ void __launch_bounds__(256) conv3x3_mma_kernel(const bf16* __restrict
         else if (out_mode == 1) reinterpret_cast<float*>(out)[o] = v;
         else reinterpret_cast<float*>(out)[o] += v;
     }
+}
+
+// BF16 weights [C_out][C_in][3][3] -> [tap][32][kCP] (zeros outside C_out x C_in), the layout
+// conv3x3_mma_kernel stages with 16-byte copies
+__global__ void relayout_weights_kernel(const bf16* __restrict__ w, bf16* __restrict__ out, int CO, int CI) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMmaW) return;
+    const int tap = i / (32 * kCP), r = i - tap * 32 * kCP;
+    const int co = r / kCP, ci = r - co * kCP;
+    out[i] = (co < CO && ci < CI) ? w[((size_t)co * CI + ci) * 9 + tap] : __float2bfloat16(0.f);
 }
 
 // dW[co][ci][k] += sum_{b,p} dout[b][co][p] in[b][ci][p + k - 1]; db[co] += sum dout[b][co][p].
@@ -471,6 +487,7 @@ struct wdb_cnn {
     std::vector<void*> allocs;
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // FP32 master, grad, Adam moments
     bf16 *pb = nullptr, *wt = nullptr;                              // BF16 weights, flipped copy
+    bf16* wlay = nullptr;                                           // per layer: [tap][32][kCP] for the MMA path
     // activations (BF16) per level: inp (l > 0), a, e; decoder s, a, d
     std::vector<bf16*> e_inp, e_a, e_e, d_s, d_a, d_d;
     std::vector<float*> g_enc;          // gradient accumulators of e_l (FP32)
@@ -521,7 +538,8 @@ wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int ou
     const float* bias = flipped ? nullptr : n->p + cl.b_off;
     dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT, B);
     if constexpr (std::is_same<TIN, bf16>::value) {
-        if (CI >= 2 && CO >= 2 && CI <= kCMax && CO <= kCMax) {   // BF16 feature maps: tensor cores
+        if (!flipped && CI >= 2 && CO >= 2 && CI <= kCMax && CO <= kCMax) {   // BF16 feature maps: tensor cores
+            const bf16* wl = n->wlay + (size_t)layer * kMmaW;
             static bool attr = false;
             if (!attr) {
                 WDB_CK(cudaFuncSetAttribute(conv3x3_mma_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -531,10 +549,10 @@ wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int ou
                 attr = true;
             }
             if (CI <= 16)
-                conv3x3_mma_kernel<16><<<grid, 256, kMmaSmem, st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
+                conv3x3_mma_kernel<16><<<grid, 256, kMmaSmem, st>>>(in, CI, CO, H, W, wl, bias, out_mode, out, relu,
                                                                     mask, residual);
             else
-                conv3x3_mma_kernel<32><<<grid, 256, kMmaSmem, st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
+                conv3x3_mma_kernel<32><<<grid, 256, kMmaSmem, st>>>(in, CI, CO, H, W, wl, bias, out_mode, out, relu,
                                                                     mask, residual);
             count_launch();
             WDB_CK(cudaGetLastError());
@@ -694,6 +712,17 @@ void cnn_release(wdb_cnn* n) {
     delete n;
 }
 
+// refresh the MMA-layout copy of every layer's BF16 weights (after any parameter change)
+wdb_status relayout(wdb_cnn* n, cudaStream_t st) {
+    for (size_t k = 0; k < n->convs.size(); ++k) {
+        const ConvLayer& c = n->convs[k];
+        relayout_weights_kernel<<<(kMmaW + 255) / 256, 256, 0, st>>>(n->pb + c.w_off, n->wlay + k * kMmaW, c.co, c.ci);
+        count_launch();
+    }
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
 constexpr char kMagicCnn[8] = {'W', 'D', 'B', 'C', 'N', 'N', '0', '1'};
 
 }  // namespace
@@ -747,6 +776,7 @@ wdb_status wdb_cnn_create(int levels, int channels, int height, int width, int m
     A(&n->v, n->n_params);
     A(&n->pb, n->n_params);
     A(&n->wt, (size_t)C * C * 9);
+    A(&n->wlay, (size_t)kMmaW * n->convs.size());
     const size_t B = (size_t)max_batch;
     n->e_inp.assign(levels, nullptr);
     n->e_a.assign(levels, nullptr);
@@ -787,6 +817,7 @@ wdb_status wdb_cnn_create(int levels, int channels, int height, int width, int m
         cudaMemsetAsync(n->m, 0, sizeof(float) * n->n_params, st);
         cudaMemsetAsync(n->v, 0, sizeof(float) * n->n_params, st);
         to_bf16_kernel<<<ew(n->n_params), 256, 0, st>>>(n->p, n->pb, n->n_params);
+        if (relayout(n, st) != WDB_OK) s = WDB_ECUDA;
         cudaMemsetAsync(n->counter, 0, sizeof(unsigned int) * 4, st);
         cudaError_t e = cudaStreamSynchronize(st);
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -813,6 +844,7 @@ wdb_status wdb_cnn_set_params(wdb_cnn* n, const float* host, long long count, vo
     WDB_CK(cudaMemsetAsync(n->v, 0, sizeof(float) * count, st));
     to_bf16_kernel<<<ew(count), 256, 0, st>>>(n->p, n->pb, count);
     count_launch();
+    WDB_TRY(relayout(n, st));
     n->step = 0;
     WDB_CK(cudaStreamSynchronize(st));
     return WDB_OK;
@@ -858,6 +890,7 @@ wdb_status wdb_cnn_train_step(wdb_cnn* n, const float* u_dev, const float* targe
     adam_kernel<<<ew(n->n_params), 256, 0, st>>>(n->p, n->g, n->m, n->v, n->pb, n->n_params, (float)lr, b1, b2, 1e-8f,
                                                  c1, c2);
     count_launch();
+    WDB_TRY(relayout(n, st));
     WDB_CK(cudaGetLastError());
     if (loss_host) *loss_host = l;
     return WDB_OK;
@@ -938,6 +971,7 @@ wdb_status wdb_cnn_load(const char* path, void* stream, wdb_cnn** out) {
             cudaMemcpyAsync(n->m, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(n->v, v.data(), sizeof(float) * v.size(), cudaMemcpyHostToDevice, st);
             to_bf16_kernel<<<ew(n->n_params), 256, 0, st>>>(n->p, n->pb, n->n_params);
+            relayout(n, st);
             n->step = hdr[5];
             ok = cudaStreamSynchronize(st) == cudaSuccess;
         }
