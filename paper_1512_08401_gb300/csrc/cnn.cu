@@ -496,6 +496,12 @@ struct wdb_cnn {
     double* part = nullptr;
     unsigned int* counter = nullptr;
     double* d_loss = nullptr;
+    // batch-1 forward replayed as a CUDA graph (input copied to u1, output in g0)
+    float* u1 = nullptr;
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t fwd1 = nullptr;
+    long long fwd1_launches = 0;
 };
 
 namespace {
@@ -708,8 +714,44 @@ wdb_status loss(wdb_cnn* n, const float* v, const float* tgt, int B, cudaStream_
 
 void cnn_release(wdb_cnn* n) {
     if (!n) return;
+    if (n->work) cudaStreamSynchronize(n->work);
+    if (n->fwd1) cudaGraphExecDestroy(n->fwd1);
+    if (n->ev_in) cudaEventDestroy(n->ev_in);
+    if (n->ev_out) cudaEventDestroy(n->ev_out);
+    if (n->work) cudaStreamDestroy(n->work);
     for (void* p : n->allocs) cudaFree(p);
     delete n;
+}
+
+// Forward of one image u_dev into n->g0 as one CUDA graph launch on the network's stream,
+// joined to `st` by events; the graph is captured on first use (after an eager warm-up run
+// that also sets the kernels' shared-memory attributes).
+wdb_status forward1_graph(wdb_cnn* n, const float* u_dev, cudaStream_t st) {
+    WDB_TRY(work_enter(&n->work, &n->ev_in, &n->ev_out, st));
+    const size_t img = (size_t)n->H * n->W;
+    WDB_CK(cudaMemcpyAsync(n->u1, u_dev, sizeof(float) * img, cudaMemcpyDeviceToDevice, n->work));
+    if (!n->fwd1) {
+        WDB_TRY(forward(n, n->u1, n->g0, 1, n->work));
+        WDB_CK(cudaStreamSynchronize(n->work));
+        const long long before = wdb_kernel_launches(0);
+        cudaGraph_t g = nullptr;
+        WDB_CK(cudaStreamBeginCapture(n->work, cudaStreamCaptureModeThreadLocal));
+        const wdb_status s = forward(n, n->u1, n->g0, 1, n->work);
+        const cudaError_t e = cudaStreamEndCapture(n->work, &g);
+        if (s != WDB_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        n->fwd1_launches = wdb_kernel_launches(0) - before;
+        count_launch(-n->fwd1_launches);   // captured, not run
+        const cudaError_t ie = cudaGraphInstantiate(&n->fwd1, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return cuda_error(ie, "cudaGraphInstantiate", __FILE__, __LINE__);
+    }
+    WDB_CK(cudaGraphLaunch(n->fwd1, n->work));
+    count_launch(n->fwd1_launches);
+    return work_exit(n->work, n->ev_out, st);
 }
 
 // refresh the MMA-layout copy of every layer's BF16 weights (after any parameter change)
@@ -802,6 +844,7 @@ wdb_status wdb_cnn_create(int levels, int channels, int height, int width, int m
     A(&n->g1, full);
     A(&n->g2, full);
     A(&n->dv, B * (size_t)height * width);
+    A(&n->u1, (size_t)height * width);
     A(&n->part, 4096 * 4);
     A(&n->counter, 4);
     A(&n->d_loss, 4);
@@ -909,7 +952,7 @@ wdb_status wdb_solve_warm(wdb_theta* th, wdb_cnn* n, const float* u_dev, float* 
     float* xw = n->g1;      // its coefficients: the candidate start
     float* x0 = n->dv;      // coefficients of u
     float* scratch = n->g2; // N/2 floats of DWT scratch
-    WDB_TRY(forward(n, u_dev, v, 1, st));
+    WDB_TRY(forward1_graph(n, u_dev, st));
     WDB_TRY(dwt2<float>(v, xw, th->lay, th->filt, scratch, st));
     WDB_TRY(dwt2<float>(u_dev, x0, th->lay, th->filt, scratch, st));
     // E(x = 0) = 1/2 ||x0||^2; the network's start is kept only when its E is lower

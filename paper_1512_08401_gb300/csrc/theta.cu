@@ -332,6 +332,7 @@ wdb_status temp_copy(TempPlan& d, const std::vector<T>& h, const T** out, cudaSt
 wdb_status temp_plan(const wdb_theta* th, const TilePlanHost& h, TempPlan& d, cudaStream_t st) {
     TilePlanDev& p = d.a.plan;
     WDB_TRY(temp_copy(d, h.pairs, &p.pairs, st));
+    WDB_TRY(temp_copy(d, h.pair_sm, &p.pair_sm, st));
     WDB_TRY(temp_copy(d, h.subs, &p.subs, st));
     WDB_TRY(temp_copy(d, h.batches, &p.batches, st));
     WDB_TRY(temp_copy(d, h.items, &p.items, st));
@@ -448,6 +449,7 @@ static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
 
 static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a, cudaStream_t st) {
     WDB_TRY(upload(th, h.pairs, const_cast<TilePair**>(&a.plan.pairs), st));
+    WDB_TRY(upload(th, h.pair_sm, const_cast<PairSm**>(&a.plan.pair_sm), st));
     WDB_TRY(upload(th, h.subs, const_cast<TileSub**>(&a.plan.subs), st));
     WDB_TRY(upload(th, h.batches, const_cast<TileBatch**>(&a.plan.batches), st));
     WDB_TRY(upload(th, h.items, const_cast<TileItem**>(&a.plan.items), st));

@@ -345,13 +345,20 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 // MACs per thread-slot plus staging; small tiles leave threads in groups
                 const double cost = best * outs;
                 plan.macs += (long long)(outs * taps_per_out);
-                if (level_only <= 0 || so.level == level_only) items.push_back({TileItem{o, a * TS, b * TS, 0}, cost});
+                if (level_only <= 0 || so.level == level_only)
+                    items.push_back({TileItem{o, a * TS, b * TS, sub.batch_begin, sub.batch_end, TS, sub.lgTS, sub.e4},
+                                     cost});
             }
     }
     std::stable_sort(items.begin(), items.end(), [](const ItemCost& x, const ItemCost& y) { return x.cost > y.cost; });
     for (auto& ic : items) {
         plan.items.push_back(ic.it);
         plan.item_cost.push_back(ic.cost);
+    }
+    plan.pair_sm.resize(plan.pairs.size());
+    for (size_t k = 0; k < plan.pairs.size(); ++k) {
+        const SubbandDev& si = L.sb[plan.pairs[k].in_sb];
+        plan.pair_sm[k] = PairSm{plan.pairs[k], si.off, si.rows, si.cols};
     }
     plan.buf_elems = std::max(max_bytes, 16) / esize;
     plan.smem_bytes = 2 * plan.buf_elems * esize;
@@ -411,15 +418,6 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// A pair's descriptor with its input subband's geometry, kept in shared memory for the batch
-// (one lane loads each pair's entry, so the per-pair set-up reads shared memory instead of a
-// chain of dependent global loads per thread).
-struct alignas(16) PairSm {
-    TilePair p;
-    long long in_off;
-    int in_rows, in_cols;
-};
-
 // Issue the asynchronous copies of batch `bi` of tile `w` into buffer S: every staged region
 // (one warp per row, lanes along the row, periodic wrap) and the batch's taps. Lane l copies
 // the row's columns xr = l + 32k; for a down pair (r = 2^lg <= 32) its polyphase destination
@@ -428,24 +426,15 @@ struct alignas(16) PairSm {
 // The batch's pair table `tab` is filled first (one thread per pair, then a barrier that
 // every thread of the CTA reaches).
 template <typename T>
-__device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const SubbandDev* __restrict__ sb,
-                                            const T* __restrict__ in, const TileItem& w, int bi, T* S,
-                                            PairSm* tab) {
+__device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const T* __restrict__ in, const TileItem& w,
+                                            int bi, T* S, PairSm* tab) {
     const TileBatch bt = plan.batches[bi];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = kTileThreads / 32;
     constexpr unsigned ES = sizeof(T);
     const unsigned S0 = smem_addr(S);
     const int np = bt.pair_end - bt.pair_begin;
-    if ((int)threadIdx.x < np) {
-        const TilePair P = plan.pairs[bt.pair_begin + threadIdx.x];
-        const SubbandDev si = sb[P.in_sb];
-        PairSm& e = tab[threadIdx.x];
-        e.p = P;
-        e.in_off = si.off;
-        e.in_rows = si.rows;
-        e.in_cols = si.cols;
-    }
+    if ((int)threadIdx.x < np) tab[threadIdx.x] = plan.pair_sm[bt.pair_begin + threadIdx.x];
     __syncthreads();
     for (int i = 0; i < np; ++i) {
         const TilePair P = tab[i].p;
@@ -514,11 +503,11 @@ struct ThreadMap {
     int ly, lx;       // first output of this thread (row, column within the tile)
 };
 
-__device__ __forceinline__ ThreadMap thread_map(const TileSub& sub) {
+__device__ __forceinline__ ThreadMap thread_map(const TileItem& w) {
     ThreadMap tm;
-    const int t = threadIdx.x, TS = sub.TS, lgTS = sub.lgTS;
+    const int t = threadIdx.x, TS = w.TS, lgTS = w.lgTS;
     tm.nout = TS * TS;
-    if (TS == 32 || (TS >= 8 && sub.e4)) {
+    if (TS == 32 || (TS >= 8 && w.e4)) {
         tm.E = 4;
         tm.lgsx = lgTS - 2;
         tm.sx = 1 << tm.lgsx;
@@ -789,38 +778,42 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         const int k = ep.st->k;
         beta = (float)(k - 1) / (float)(k + 2);
     }
+    // work items come from a queue, heaviest first
     __shared__ int s_next;
     if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
     __syncthreads();
     int it = s_next;
-    int bi = (it < plan.n_items) ? plan.subs[plan.items[it].o].batch_begin : 0;
+    TileItem w = (it < plan.n_items) ? plan.items[it] : TileItem{};
+    int bi = w.batch_begin;
     T* S = buf0;
     T* Snext = buf1;
     __shared__ PairSm tab_buf[2][kMaxBatchPairs];
     PairSm* tab = tab_buf[0];
     PairSm* tab_next = tab_buf[1];
-    if (it < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[it], bi, S, tab);
+    if (it < plan.n_items) stage_batch<T>(plan, in, w, bi, S, tab);
     cp_async_commit();
     T acc[4] = {0, 0, 0, 0};
     while (it < plan.n_items) {
-        const TileItem w = plan.items[it];
-        const TileSub sub = plan.subs[w.o];
         int nit = it, nbi = bi + 1;
+        TileItem nw = w;
         __syncthreads();
-        if (nbi >= sub.batch_end) {
+        if (nbi >= w.batch_end) {
             if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
             __syncthreads();
             nit = s_next;
-            nbi = (nit < plan.n_items) ? plan.subs[plan.items[nit].o].batch_begin : 0;
+            if (nit < plan.n_items) {
+                nw = plan.items[nit];
+                nbi = nw.batch_begin;
+            }
         }
-        if (nit < plan.n_items) stage_batch<T>(plan, A.sb, in, plan.items[nit], nbi, Snext, tab_next);
+        if (nit < plan.n_items) stage_batch<T>(plan, in, nw, nbi, Snext, tab_next);
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         const SubbandDev so = A.sb[w.o];
-        const ThreadMap tm = thread_map(sub);
+        const ThreadMap tm = thread_map(w);
         compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc);
-        if (bi + 1 == sub.batch_end) {
+        if (bi + 1 == w.batch_end) {
             group_reduce<T>(tm, acc, red_buf);
             epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
 #pragma unroll
@@ -828,6 +821,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         }
         it = nit;
         bi = nbi;
+        w = nw;
         T* tmp = S;
         S = Snext;
         Snext = tmp;
@@ -931,8 +925,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
     if (it < B.n_items) {
         const BatchItem bw = B.items[it];
         const TilePlanDev& pl = plan_of(bw.p);
-        bi = pl.subs[pl.items[bw.item].o].batch_begin;
-        stage_batch<float>(pl, B.probs[bw.p].sb, in_of(bw.p), pl.items[bw.item], bi, S, tab);
+        bi = pl.items[bw.item].batch_begin;
+        stage_batch<float>(pl, in_of(bw.p), pl.items[bw.item], bi, S, tab);
     }
     cp_async_commit();
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -942,29 +936,27 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         const BatchProblem& P = B.probs[bw.p];
         const TilePlanDev& pl = plan_of(bw.p);
         const TileItem w = pl.items[bw.item];
-        const TileSub sub = pl.subs[w.o];
         int nit = it, nbi = bi + 1;
         __syncthreads();
-        if (nbi >= sub.batch_end) {
+        if (nbi >= w.batch_end) {
             nit = fetch();
             if (nit < B.n_items) {
                 const BatchItem nb = B.items[nit];
-                const TilePlanDev& npl = plan_of(nb.p);
-                nbi = npl.subs[npl.items[nb.item].o].batch_begin;
+                nbi = plan_of(nb.p).items[nb.item].batch_begin;
             }
         }
         if (nit < B.n_items) {
             const BatchItem nb = B.items[nit];
             const TilePlanDev& npl = plan_of(nb.p);
-            stage_batch<float>(npl, B.probs[nb.p].sb, in_of(nb.p), npl.items[nb.item], nbi, Snext, tab_next);
+            stage_batch<float>(npl, in_of(nb.p), npl.items[nb.item], nbi, Snext, tab_next);
         }
         cp_async_commit();
         cp_async_wait<1>();
         __syncthreads();
         const SubbandDev so = P.sb[w.o];
-        const ThreadMap tm = thread_map(sub);
+        const ThreadMap tm = thread_map(w);
         compute_batch<float>(pl, in_of(bw.p), w, so, bi, S, tab, tm, acc);
-        if (bi + 1 == sub.batch_end) {
+        if (bi + 1 == w.batch_end) {
             group_reduce<float>(tm, acc, red_buf);
             EpiArgs ep{};
             ep.x0 = P.x0;

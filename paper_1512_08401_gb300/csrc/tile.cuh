@@ -61,10 +61,19 @@ struct alignas(16) TileBatch {    // pairs [pair_begin, pair_end) of one subband
     int pad[2];
 };
 
-struct alignas(16) TileItem {
+struct alignas(16) TileItem {     // one tile; carries what the kernel needs without further lookups
     int o;
     int ty0, tx0;
-    int pad;
+    int batch_begin, batch_end;   // the subband's batches
+    int TS, lgTS, e4;             // the subband's tile side and thread map
+};
+
+// A pair's descriptor with its input subband's geometry (the per-batch shared-memory table
+// of the kernel holds these).
+struct alignas(16) PairSm {
+    TilePair p;
+    long long in_off;
+    int in_rows, in_cols;
 };
 
 struct TilePlanDev {
@@ -72,6 +81,7 @@ struct TilePlanDev {
     const TileSub* subs;
     const TileBatch* batches;
     const TileItem* items;
+    const PairSm* pair_sm;    // pairs with their input geometry (parallel to pairs)
     const int* tap_off;       // staged: offset in shared memory; global: (dy << 16) | (dx & 0xffff)
     const int* tap_lin;       // global pairs: dy * (input columns) + dx (interior fast path)
     const float* tap_v;
@@ -86,6 +96,7 @@ struct TilePlanHost {
     std::vector<TileSub> subs;
     std::vector<TileBatch> batches;
     std::vector<TileItem> items;
+    std::vector<PairSm> pair_sm;
     std::vector<int> tap_off;
     std::vector<int> tap_lin;
     std::vector<float> tap_v;
