@@ -359,7 +359,8 @@ wdb_status temp_plan(const wdb_theta* th, const TilePlanHost& h, TempPlan& d, cu
 // outputs per thread) is planned for that level's tiles alone and applied on this GPU (best
 // of 3 after a warm-up); the per-level winners form one plan, which then competes, over the
 // whole operator, with the planner's own plans (per-tile cost caps of 1, 2 and 4 per-CTA
-// shares, which balance the levels against each other). The fastest is kept.
+// shares, which balance the levels against each other, and staging buffers of 24, 32 and
+// 48 KB, which trade batches per tile against resident CTAs). The fastest is kept.
 static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
     const Layout& L = th->lay;
     const long long N = L.N;
@@ -427,8 +428,9 @@ static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
         if (s != WDB_OK) break;
         std::vector<TilePlanHost> whole;
         whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, &best, 0));
-        for (double cap : {1.0, 2.0, 4.0})
-            whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, cap));
+        for (int budget : {kTileSmemBudget * 3 / 4, kTileSmemBudget, kTileSmemBudget * 3 / 2})
+            for (double cap : {1.0, 2.0, 4.0})
+                whole.push_back(make_tile_plan(L, th->tent[op], 4, budget, th->plan_ctas, nullptr, 0, cap));
         float best_ms = 1e30f;
         for (size_t k = 0; k < whole.size() && s == WDB_OK; ++k) {
             const float ms = time_plan(whole[k]);
