@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=20)
-    ap.add_argument("--workload", choices=["headline", "batch", "large", "warm"], default="headline",
+    ap.add_argument("--workload", choices=["headline", "batch", "large", "warm", "sweep"], default="headline",
                     help="batch: 256 problems of mixed size, batched solve vs a per-problem loop")
     ap.add_argument("--problems", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
@@ -492,6 +492,64 @@ def run_batch(args):
     return 0
 
 
+def run_sweep(args):
+    """The 1024^2 headline variants: blur (Gaussian sigma = 3 on 31x31, or a 21-px motion line),
+    K / N in {10, 30, 100} and preconditioner in {none, SPAI} (Jacobi as an extra): ms and
+    iterations to E*(1 + 1e-4) for the Theta_K path and the FFT path, E* from long runs of
+    each path, and the two FISTA kernels' launch times."""
+    import torch
+    from paper_1512_08401_gb300 import build, synthetic, wdb
+    build.build()
+    wdb.lib()
+    n, N = N_SIDE, N_SIDE * N_SIDE
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    x = torch.zeros(N, device="cuda")
+
+    def timed(fn):
+        ms = []
+        for _ in range(args.warmup):
+            fn()
+        out = None
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            start.record()
+            out = fn()
+            end.record()
+            end.synchronize()
+            ms.append(start.elapsed_time(end))
+        return statistics.mean(ms), out
+
+    rows = []
+    for blur in ("gaussian", "motion"):
+        prob = synthetic.headline_problem(blur, 0)
+        u = torch.from_numpy(prob.u0.astype(np.float32).ravel()).cuda()
+        fop = wdb.FFTOp(prob.psf, n, n, "db4", LEVELS)
+        for kn in (10, 30, 100):
+            th = wdb.Theta.build(prob.psf, n, n, "db4", LEVELS, K=kn * N)
+            for pre in ("none", "spai", "jacobi"):
+                E = th.solve(u, x, lam=LAM, max_iters=3000, precond=pre)["objective"]
+                ms, r = timed(lambda: th.solve(u, x, lam=LAM, max_iters=20000, precond=pre,
+                                               target_objective=E * (1 + REL_GAP), time_kernels=True))
+                row = {"blur": blur, "K_over_N": kn, "precond": pre, "ms": ms, "iters": r["first_primal_below"],
+                       "k1_us": 1e3 * r["ms_k1"], "k2_us": 1e3 * r["ms_k2"], "n_taps": th.info.n_taps,
+                       "E_star": E}
+                if kn == 30:
+                    Ef = fop.solve(u, x, lam=LAM, max_iters=3000, precond=pre)["objective"]
+                    fms, fr = timed(lambda: fop.solve(u, x, lam=LAM, max_iters=20000, precond=pre,
+                                                      target_objective=Ef * (1 + REL_GAP)))
+                    row.update({"fft_ms": fms, "fft_iters": fr["first_primal_below"], "E_star_fft": Ef})
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+            th.free()
+        fop.free()
+    print(json.dumps({"metric": "ms to 1e-4 rel. objective gap, 1024^2 variants", "unit": "ms",
+                      "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "data": "synthetic", "l2": "flushed before each timed solve", "rows": rows}))
+    return 0
+
+
 def run_large_profile(args):
     """4096 x 4096 operator (Gaussian sigma = 4 on 41 x 41, J = 6, K = 30 N) and a 3-iteration
     solve: the small program an ncu capture of the two FISTA kernels runs."""
@@ -591,6 +649,8 @@ def main():
         return run_large_profile(args)
     if args.workload == "warm":
         return run_warm(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     return run_ours(args)
 
 
