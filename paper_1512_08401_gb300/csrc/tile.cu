@@ -55,14 +55,22 @@ int pitch(int width, int TS, bool e4) {
     return p;
 }
 
-Geometry geometry(const PairBuild& p, int TS, int esize, bool e4) {
+// Rows of an up pair or an r = 1 down pair can be staged in 16-byte chunks starting at the
+// 4-aligned column at or before the region's first column (16- or 32-wide tiles with the
+// 4-output map, whose pitches are multiples of 4, and inputs whose rows are 4-aligned).
+bool vec_pair(const PairBuild& p, const Layout& L, int TS, bool e4, int esize) {
+    const SubbandDev& si = L.sb[p.in];
+    return esize == 4 && e4 && TS >= 16 && (p.up || p.lg == 0) && si.cols % 4 == 0 && si.off % 4 == 0;
+}
+
+Geometry geometry(const PairBuild& p, int TS, int esize, bool e4, bool vec = false) {
     Geometry g;
     const int r = 1 << p.lg;
     if (!p.up) {
         g.RR = r * (TS - 1) + (p.dy1 - p.dy0) + 1;
         g.RC = r * (TS - 1) + (p.dx1 - p.dx0) + 1;
         g.PR = (g.RR + r - 1) / r;
-        g.PC = pitch((g.RC + r - 1) / r, TS, e4);
+        g.PC = pitch(vec ? (g.RC + 6) & ~3 : (g.RC + r - 1) / r, TS, e4);
         g.PS = g.PR * g.PC;
         g.bytes = (long long)r * r * g.PS * esize;
     } else {
@@ -70,7 +78,7 @@ Geometry geometry(const PairBuild& p, int TS, int esize, bool e4) {
         g.RR = rows + (p.dy1 - p.dy0);
         g.RC = rows + (p.dx1 - p.dx0);
         g.PR = g.RR;
-        g.PC = pitch(g.RC, TS, e4);
+        g.PC = pitch(vec ? (g.RC + 6) & ~3 : g.RC, TS, e4);
         g.PS = g.PR * g.PC;
         g.bytes = (long long)g.PR * g.PC * esize;
     }
@@ -185,6 +193,11 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             }
             e4 = TS >= 8;
         }
+        // pairs whose rows are staged in 16-byte chunks (when their wider region still fits)
+        std::vector<bool> vecf(np, false);
+        for (int k = 0; k < np; ++k)
+            vecf[k] = !global[k] && vec_pair(*by_out[o][k], L, TS, e4, esize) &&
+                      geometry(*by_out[o][k], TS, esize, e4, true).bytes <= budget;
         // staged down pairs, staged up pairs (in batches that fill a buffer), then the global
         // ones; within a batch the staged taps (down pairs only) are contiguous
         std::vector<int> order;
@@ -220,7 +233,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 continue;
             }
             const PairBuild& pb = *by_out[o][k];
-            const Geometry g = geometry(pb, TS, esize, e4);
+            const Geometry g = geometry(pb, TS, esize, e4, vecf[k]);
             const int need = (int)((g.bytes + 15) / 16 * 16 / esize);
             // staged taps: down pairs and up pairs with r <= 8 (larger phase tables are read
             // from global memory)
@@ -249,7 +262,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         for (size_t q = 0; q < order.size(); ++q) {
             const int k = order[q];
             const PairBuild& pb = *by_out[o][k];
-            const Geometry g = geometry(pb, TS, esize, e4);
+            const Geometry g = geometry(pb, TS, esize, e4, vecf[k]);
             const int r = 1 << pb.lg, m = r - 1;
             TileBatch& bt = plan.batches[sub.batch_begin + batch_of[q]];
             if (bt.pair_end == bt.pair_begin) {
@@ -267,6 +280,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             tp.PS = g.PS;
             tp.y0 = pb.dy0;
             tp.x0 = pb.dx0;
+            tp.vec = vecf[k] ? 1 : 0;
             if (global[k]) {   // bounding box of the taps (input units) for the interior test
                 tp.RR = pb.dy1 - pb.dy0 + 1;
                 tp.RC = pb.dx1 - pb.dx0 + 1;
@@ -358,7 +372,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
     plan.pair_sm.resize(plan.pairs.size());
     for (size_t k = 0; k < plan.pairs.size(); ++k) {
         const SubbandDev& si = L.sb[plan.pairs[k].in_sb];
-        plan.pair_sm[k] = PairSm{plan.pairs[k], si.off, si.rows, si.cols};
+        plan.pair_sm[k] = PairSm{plan.pairs[k], si.off, si.rows, si.cols, 0, {0, 0, 0}};
     }
     plan.buf_elems = std::max(max_bytes, 16) / esize;
     plan.smem_bytes = 2 * plan.buf_elems * esize;
@@ -434,8 +448,17 @@ __device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const T* __
     constexpr unsigned ES = sizeof(T);
     const unsigned S0 = smem_addr(S);
     const int np = bt.pair_end - bt.pair_begin;
-    if ((int)threadIdx.x < np) tab[threadIdx.x] = plan.pair_sm[bt.pair_begin + threadIdx.x];
+    if ((int)threadIdx.x < np) {
+        PairSm e = plan.pair_sm[bt.pair_begin + threadIdx.x];
+        if (e.p.vec) {   // this tile's region starts at staged column (first column mod 4)
+            const int X0 = (e.p.mode == kDown) ? ((w.tx0 << e.p.lg) + e.p.x0) : ((w.tx0 >> e.p.lg) + e.p.x0);
+            e.shift = pos_mod(X0, e.in_cols) & 3;
+        }
+        tab[threadIdx.x] = e;
+    }
     __syncthreads();
+    // 16-byte copies need a 16-byte aligned input vector (the library's own buffers are)
+    const bool in_aligned = (reinterpret_cast<unsigned long long>(in) & 15) == 0;
     for (int i = 0; i < np; ++i) {
         const TilePair P = tab[i].p;
         if (P.mode != kDown && P.mode != kUp) break;   // global pairs come last in a subband
@@ -448,7 +471,30 @@ __device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const T* __
         const int yb = pos_mod(Y0, si.rows), xb = pos_mod(X0, si.cols);
         const int plane = P.PS;
         const unsigned base = S0 + (unsigned)P.soff * ES;
-        if (!down || lg <= 5) {
+        if (P.vec) {
+            // rows of RCv = roundup4(RC + 3) columns starting at the 4-aligned column xb & ~3;
+            // input rows are 4-aligned and a chunk never straddles the periodic wrap
+            const int xa = xb & ~3, RCv = (P.RC + 6) & ~3;
+            for (int yr = warp; yr < P.RR; yr += NW) {
+                int gy = yb + yr;
+                while (gy >= si.rows) gy -= si.rows;
+                const T* __restrict__ row = src + (size_t)gy * si.cols;
+                const unsigned drow = base + (unsigned)(yr * P.PC) * ES;
+                if (in_aligned) {
+                    for (int c = lane; 4 * c < RCv; c += 32) {
+                        int gx = xa + 4 * c;
+                        while (gx >= si.cols) gx -= si.cols;
+                        cp_async_to<16>(drow + 16u * c, row + gx);
+                    }
+                } else {
+                    for (int xr = lane; xr < RCv; xr += 32) {
+                        int gx = xa + xr;
+                        while (gx >= si.cols) gx -= si.cols;
+                        cp_async_to<ES>(drow + (unsigned)xr * ES, row + gx);
+                    }
+                }
+            }
+        } else if (!down || lg <= 5) {
             const int colc = down ? ((lane & m) * plane + (lane >> lg)) : lane;
             const unsigned step = (unsigned)(down ? (32 >> lg) : 32) * ES;
             for (int yr = warp; yr < P.RR; yr += NW) {
@@ -578,11 +624,12 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
     const int np = bt.pair_end - bt.pair_begin;
     for (int i = 0; i < np; ++i) {
         const TilePair P = tab[i].p;
+        const int sh = tab[i].shift;   // staged column of the region's first column (vec pairs)
         const int lg = P.lg, r = 1 << lg, m = r - 1;
         if (P.mode == kDown) {
             const int* __restrict__ to = soffs + P.tap_begin;
             const T* __restrict__ tv = svals + P.tap_begin;
-            const T* __restrict__ Sb = S + tm.ly * P.PC + tm.lx;
+            const T* __restrict__ Sb = S + tm.ly * P.PC + tm.lx + sh;
             if (E == 4) {
                 if (tm.sx == 8) down_taps4<8, T>(to, tv, g, P.ntap, G, Sb, acc);
                 else if (tm.sx == 4) down_taps4<4, T>(to, tv, g, P.ntap, G, Sb, acc);
@@ -603,7 +650,7 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
             // reads the same table, so these loads are coalesced L1/L2 hits
             const int rr = r * r;
             const int py = w.ty0 + tm.ly, px = w.tx0 + tm.lx;
-            const int rowb = ((py >> lg) - (w.ty0 >> lg)) * P.PC;
+            const int rowb = ((py >> lg) - (w.ty0 >> lg)) * P.PC + sh;
             const bool st = lg <= kUpStagedLgDev;   // phase tables staged with the batch
             const int* __restrict__ gto = (st ? soffs : plan.tap_off) + P.tap_begin;
             const T* __restrict__ gtv = (st ? svals : gvals) + P.tap_begin;

@@ -35,6 +35,7 @@ struct alignas(16) TilePair {
     int y0, x0;       // region origin: down Y0 = (ty0 << lg) + y0; up Y0 = (ty0 >> lg) + y0
     int tap_begin;    // first tap (up: phase-interleaved, index tap_begin + j r^2 + phase)
     int ntap;         // down: taps; up: padded taps per phase
+    int vec;          // 1: rows staged in 16-byte chunks from a 4-aligned column (up or r = 1 pairs)
 };
 
 constexpr int kMaxBatchPairs = 16;   // pairs per batch (their descriptors sit in shared memory)
@@ -74,6 +75,8 @@ struct alignas(16) PairSm {
     TilePair p;
     long long in_off;
     int in_rows, in_cols;
+    int shift;        // vec pairs: staged column of the region's first column (0..3), set per tile
+    int pad[3];
 };
 
 struct TilePlanDev {
