@@ -224,7 +224,7 @@ wdb_status theta_workspace_public(wdb_theta* th, cudaStream_t st) {
 
 wdb_status theta_objective_dev(wdb_theta* th, const float* x, const float* x0, const float* w_dev, cudaStream_t st,
                                double* E, long long* support) {
-    StencilArgs F = stencil_args(th, false);
+    StencilArgs F = stencil_args(th);
     double* d_out = reinterpret_cast<double*>(&th->d_state->scratch[0]);
     WDB_TRY(tile_resnorm(tile_args(th, false, false), x, x0, th->d_r, d_out, th->d_red_part, st));
     WDB_TRY(launch_l1_terms(F, th->grid, x, w_dev, th_red(th, d_out + 1), st));

@@ -1,14 +1,11 @@
-// Gather kernels for Theta_K and Theta_K^T (Eq. gradientapprox), and the fused FISTA step
-// (Algorithm 3 with the diagonal Prox of Eq. defProxP).
+// Subband-walking elementwise kernels: the FFT path's fused FISTA step (Algorithm 3 with
+// the diagonal Prox of Eq. defProxP, gradient given), the l1 terms of the objective, the
+// per-phase-class diagonal scaling (Eq. defProxP's P) and the plain vector helpers of the
+// power iteration (Section 4.2). The Theta_K kernels themselves are in tile.cu.
 //
-// Every block Theta_{a,b} is circulant (Thm 3), so one output coefficient of subband o
-// gathers, for each input subband, a short list of taps at fixed offsets:
-//   down pair (input finer or equal, r = 2^lg):  out[o, p] += v_t * in[i, r p + d_t]
-//   up pair   (input coarser, r = 2^lg):          out[o, r P + phi] += v_t * in[i, P + d_t]
-//             (taps of phase phi only)
-// with periodic wrap. Outputs are scheduled in virtual blocks of 256 consecutive
-// coefficients of one subband; a CTA walks virtual blocks in a grid-stride loop so that the
-// per-CTA partial sums of the reductions stay few.
+// Outputs are scheduled in virtual blocks of 256 consecutive coefficients of one subband; a
+// CTA walks virtual blocks in a grid-stride loop so that the per-CTA partial sums of the
+// reductions stay few.
 //
 // Reductions: each thread keeps a compensated (Neumaier) FP32 sum of its terms, the warp
 // and CTA trees run in FP64, and the last CTA to finish sums the per-CTA partials in FP64
@@ -21,86 +18,6 @@
 namespace wdb {
 
 namespace {
-
-template <typename T>
-__device__ __forceinline__ const T* tap_vals(const OpDev& op);
-template <>
-__device__ __forceinline__ const float* tap_vals<float>(const OpDev& op) { return op.tap_v; }
-template <>
-__device__ __forceinline__ const double* tap_vals<double>(const OpDev& op) { return op.tap_v64; }
-
-template <typename T>
-__device__ __forceinline__ T gather(const OpDev& op, const SubbandDev* __restrict__ sb, const T* __restrict__ in,
-                                    int o, int py, int px) {
-    const T* __restrict__ vals = tap_vals<T>(op);
-    T acc = 0;
-    const int pb = __ldg(op.pair_start + o), pe = __ldg(op.pair_start + o + 1);
-    for (int pi = pb; pi < pe; ++pi) {
-        const PairDesc d = op.pairs[pi];
-        const int ib = d.in_sb;
-        const int up = d.meta >> 8, lg = d.meta & 0xff;
-        const int R = __ldg(&sb[ib].rows), C = __ldg(&sb[ib].cols);
-        const T* __restrict__ src = in + __ldg(&sb[ib].off);
-        int t0, t1, by, bx;
-        if (!up) {
-            by = py << lg;
-            bx = px << lg;
-            t0 = d.a;
-            t1 = d.b;
-        } else {
-            const int m = (1 << lg) - 1;
-            const int ph = ((py & m) << lg) | (px & m);
-            by = py >> lg;
-            bx = px >> lg;
-            t0 = __ldg(op.phase_idx + d.a + ph);
-            t1 = __ldg(op.phase_idx + d.a + ph + 1);
-        }
-        for (int t = t0; t < t1; ++t) {
-            const int pk = __ldg(op.tap_off + t);
-            int yy = by + (pk >> 16);
-            int xx = bx + (int)(short)(pk & 0xffff);
-            yy += (yy < 0) ? R : 0;
-            yy -= (yy >= R) ? R : 0;
-            xx += (xx < 0) ? C : 0;
-            xx -= (xx >= C) ? C : 0;
-            acc += __ldg(vals + t) * __ldg(src + (size_t)yy * C + xx);
-        }
-    }
-    return acc;
-}
-
-// ---------------------------------------------------------------------------------------
-// out = Op(in) [* scale per phase class], optional sum of out^2 -> red.out[0]
-// ---------------------------------------------------------------------------------------
-template <typename T, bool SCALE, bool NORM>
-__global__ void __launch_bounds__(kVB) apply_kernel(StencilArgs A, const T* __restrict__ in, T* __restrict__ out,
-                                                    const double* __restrict__ scale, RedTarget red) {
-    __shared__ int s_o;
-    double nrm = 0.0;
-    float ns = 0.f, nc = 0.f;
-    for (int vb = blockIdx.x; vb < A.nvb; vb += gridDim.x) {
-        if (threadIdx.x == 0) s_o = find_subband(A.vb_start, A.S, vb);
-        __syncthreads();
-        const int o = s_o;
-        const SubbandDev so = A.sb[o];
-        const int local = (vb - A.vb_start[o]) * kVB + threadIdx.x;
-        if (local < so.rows * so.cols) {
-            const int py = local / so.cols, px = local - py * so.cols;
-            T v = gather<T>(A.op, A.sb, in, o, py, px);
-            if (SCALE) v = (T)((double)v * scale[phase_class(so, py, px)]);
-            out[so.off + local] = v;
-            if (NORM) {
-                if (sizeof(T) == 8) nrm += (double)v * (double)v;
-                else neu_add(ns, nc, (float)v * (float)v);
-            }
-        }
-        __syncthreads();
-    }
-    if (NORM) {
-        double v[1] = {nrm + (double)ns + (double)nc}, tot[1];
-        if (grid_reduce<1>(v, 0u, red.part, red.counter, tot) && threadIdx.x == 0) red.out[0] = tot[0];
-    }
-}
 
 // elementwise out = in * scale[class]
 template <typename T>
@@ -121,85 +38,15 @@ __global__ void __launch_bounds__(kVB) scale_kernel(StencilArgs A, const T* __re
     }
 }
 
-// ---------------------------------------------------------------------------------------
-// Kernel 1: r = Theta_K y - x0; FP64 totals of ||r||^2 and <x0, r>
-// ---------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kVB) k1_residual(StencilArgs A, const float* __restrict__ y,
-                                                   const float* __restrict__ x0, float* __restrict__ r,
-                                                   double* part, SolveState* st) {
-    if (*(volatile int*)&st->stop) return;
-    __shared__ int s_o;
-    float rs = 0.f, rc = 0.f, xs = 0.f, xc = 0.f;
-    for (int vb = blockIdx.x; vb < A.nvb; vb += gridDim.x) {
-        if (threadIdx.x == 0) s_o = find_subband(A.vb_start, A.S, vb);
-        __syncthreads();
-        const int o = s_o;
-        const SubbandDev so = A.sb[o];
-        const int local = (vb - A.vb_start[o]) * kVB + threadIdx.x;
-        if (local < so.rows * so.cols) {
-            const int py = local / so.cols, px = local - py * so.cols;
-            const float acc = gather<float>(A.op, A.sb, y, o, py, px);
-            const size_t i = so.off + local;
-            const float xv = x0[i];
-            const float rv = acc - xv;
-            r[i] = rv;
-            neu_add(rs, rc, rv * rv);
-            neu_add(xs, xc, xv * rv);
-        }
-        __syncthreads();
-    }
-    double v[2] = {(double)rs + (double)rc, (double)xs + (double)xc}, tot[2];
-    if (grid_reduce<2>(v, 0u, part, &st->done[0], tot) && threadIdx.x == 0) {
-        st->rr = tot[0];
-        st->x0r = tot[1];
-    }
-}
-
-// ---------------------------------------------------------------------------------------
-// Kernel 2: g = Theta_K^T r fused with the step
-//   z = y - (tau/P) g ; x_new = soft(z, (tau/P) w) ; y_new = x_new + beta_k (x_new - x_old)
-// in place on x and y; FP64 totals of sum w|y| and max |g|/w.
-// ---------------------------------------------------------------------------------------
+// |g| / w with the w = 0 convention of the dual norm (0/0 = 0, g/0 = FLT_MAX).
 __device__ __forceinline__ float g_over_w(float g, float w) {
     const float ag = fabsf(g);
     return w > 0.f ? ag / w : (ag > 0.f ? FLT_MAX : 0.f);
 }
 
-__global__ void __launch_bounds__(kVB) k2_step(StencilArgs A, const float* __restrict__ r, float* __restrict__ y,
-                                               float* __restrict__ x, const float* __restrict__ step_tab,
-                                               const float* __restrict__ w_sb, double* part, SolveState* st) {
-    if (*(volatile int*)&st->stop) return;
-    __shared__ int s_o;
-    const int k = st->k;
-    const float beta = (float)(k - 1) / (float)(k + 2);
-    float ws = 0.f, wc = 0.f, gm = 0.f;
-    for (int vb = blockIdx.x; vb < A.nvb; vb += gridDim.x) {
-        if (threadIdx.x == 0) s_o = find_subband(A.vb_start, A.S, vb);
-        __syncthreads();
-        const int o = s_o;
-        const SubbandDev so = A.sb[o];
-        const int local = (vb - A.vb_start[o]) * kVB + threadIdx.x;
-        if (local < so.rows * so.cols) {
-            const int py = local / so.cols, px = local - py * so.cols;
-            const float g = gather<float>(A.op, A.sb, r, o, py, px);
-            const size_t i = so.off + local;
-            const float stp = step_tab[phase_class(so, py, px)];
-            const float wv = w_sb[o];
-            const float yv = y[i], xo = x[i];
-            const float z = yv - stp * g;
-            const float xn = copysignf(fmaxf(fabsf(z) - stp * wv, 0.f), z);
-            x[i] = xn;
-            y[i] = xn + beta * (xn - xo);
-            neu_add(ws, wc, wv * fabsf(yv));
-            gm = fmaxf(gm, g_over_w(g, wv));
-        }
-        __syncthreads();
-    }
-    double v[2] = {(double)ws + (double)wc, (double)gm}, tot[2];
-    if (grid_reduce<2>(v, 2u, part, &st->done[1], tot) && threadIdx.x == 0) finish_iteration(st, tot[0], tot[1]);
-}
-
-// FFT path step: g given (DWT of the image-domain gradient), same update and totals.
+// FFT path step, g given (the DWT of the image-domain gradient):
+//   z = y - (tau/P) g ; x_new = soft(z, (tau/P) w) ; y_new = x_new + beta_k (x_new - x_old)
+// in place on x and y; FP64 totals of sum w|y| and max |g|/w.
 __global__ void __launch_bounds__(kVB) fft_step(StencilArgs A, const float* __restrict__ g_in, float* __restrict__ y,
                                                 float* __restrict__ x, const float* __restrict__ step_tab,
                                                 const float* __restrict__ w_sb, double* part, SolveState* st) {
@@ -260,31 +107,6 @@ __global__ void __launch_bounds__(kVB) l1_terms(StencilArgs A, const float* __re
     }
 }
 
-// residual only (no state): r = Theta_K x - x0, ||r||^2 -> red.out[0]
-__global__ void __launch_bounds__(kVB) residual_norm(StencilArgs A, const float* __restrict__ x,
-                                                     const float* __restrict__ x0, float* __restrict__ r,
-                                                     RedTarget red) {
-    __shared__ int s_o;
-    float rs = 0.f, rc = 0.f;
-    for (int vb = blockIdx.x; vb < A.nvb; vb += gridDim.x) {
-        if (threadIdx.x == 0) s_o = find_subband(A.vb_start, A.S, vb);
-        __syncthreads();
-        const int o = s_o;
-        const SubbandDev so = A.sb[o];
-        const int local = (vb - A.vb_start[o]) * kVB + threadIdx.x;
-        if (local < so.rows * so.cols) {
-            const int py = local / so.cols, px = local - py * so.cols;
-            const size_t i = so.off + local;
-            const float rv = gather<float>(A.op, A.sb, x, o, py, px) - x0[i];
-            r[i] = rv;
-            neu_add(rs, rc, rv * rv);
-        }
-        __syncthreads();
-    }
-    double v[1] = {(double)rs + (double)rc}, tot[1];
-    if (grid_reduce<1>(v, 0u, red.part, red.counter, tot) && threadIdx.x == 0) red.out[0] = tot[0];
-}
-
 // splitmix64 (Steele, Lea & Flood 2014): output i of the stream seeded with s is
 // mix(s + (i+1) * 0x9E3779B97F4A7C15); value in [-1, 1) = 2 (z >> 11) 2^-53 - 1.
 template <typename T>
@@ -327,37 +149,8 @@ int ew_grid(long long n) {
 // Host launchers
 // ---------------------------------------------------------------------------------------
 template <typename T>
-wdb_status launch_apply(const StencilArgs& A, int grid, const T* in, T* out, const double* scale, RedTarget* red,
-                        cudaStream_t st) {
-    RedTarget r = red ? *red : RedTarget{};
-    if (scale && red) apply_kernel<T, true, true><<<grid, kVB, 0, st>>>(A, in, out, scale, r);
-    else if (scale) apply_kernel<T, true, false><<<grid, kVB, 0, st>>>(A, in, out, scale, r);
-    else if (red) apply_kernel<T, false, true><<<grid, kVB, 0, st>>>(A, in, out, scale, r);
-    else apply_kernel<T, false, false><<<grid, kVB, 0, st>>>(A, in, out, scale, r);
-    count_launch();
-    WDB_CK(cudaGetLastError());
-    return WDB_OK;
-}
-
-template <typename T>
 wdb_status launch_scale(const StencilArgs& A, int grid, const T* in, T* out, const double* scale, cudaStream_t st) {
     scale_kernel<T><<<grid, kVB, 0, st>>>(A, in, out, scale);
-    count_launch();
-    WDB_CK(cudaGetLastError());
-    return WDB_OK;
-}
-
-wdb_status launch_k1(const StencilArgs& A, int grid, const float* y, const float* x0, float* r, double* part,
-                     SolveState* s, cudaStream_t st) {
-    k1_residual<<<grid, kVB, 0, st>>>(A, y, x0, r, part, s);
-    count_launch();
-    WDB_CK(cudaGetLastError());
-    return WDB_OK;
-}
-
-wdb_status launch_k2(const StencilArgs& A, int grid, const float* r, float* y, float* x, const float* step_tab,
-                     const float* w_sb, double* part, SolveState* s, cudaStream_t st) {
-    k2_step<<<grid, kVB, 0, st>>>(A, r, y, x, step_tab, w_sb, part, s);
     count_launch();
     WDB_CK(cudaGetLastError());
     return WDB_OK;
@@ -375,14 +168,6 @@ wdb_status launch_fft_step(const StencilArgs& A, int grid, const float* g, float
 wdb_status launch_l1_terms(const StencilArgs& A, int grid, const float* x, const float* w_sb, RedTarget red,
                            cudaStream_t st) {
     l1_terms<<<grid, kVB, 0, st>>>(A, x, w_sb, red);
-    count_launch();
-    WDB_CK(cudaGetLastError());
-    return WDB_OK;
-}
-
-wdb_status launch_residual_norm(const StencilArgs& A, int grid, const float* x, const float* x0, float* r,
-                                RedTarget red, cudaStream_t st) {
-    residual_norm<<<grid, kVB, 0, st>>>(A, x, x0, r, red);
     count_launch();
     WDB_CK(cudaGetLastError());
     return WDB_OK;
@@ -427,7 +212,7 @@ int stencil_grid_limit() {
         int dev = 0, sms = 0, per = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2_step, kVB, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fft_step, kVB, 0);
         if (sms <= 0) sms = 1;
         if (per <= 0) per = 1;
         g = sms * per;
@@ -435,10 +220,6 @@ int stencil_grid_limit() {
     return g;
 }
 
-template wdb_status launch_apply<float>(const StencilArgs&, int, const float*, float*, const double*, RedTarget*,
-                                        cudaStream_t);
-template wdb_status launch_apply<double>(const StencilArgs&, int, const double*, double*, const double*,
-                                         RedTarget*, cudaStream_t);
 template wdb_status launch_scale<float>(const StencilArgs&, int, const float*, float*, const double*, cudaStream_t);
 template wdb_status launch_scale<double>(const StencilArgs&, int, const double*, double*, const double*,
                                          cudaStream_t);

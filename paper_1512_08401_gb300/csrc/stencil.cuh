@@ -1,11 +1,10 @@
-// Launch interface of the gather kernels (stencil.cu).
+// Launch interface of the subband-walking elementwise kernels (stencil.cu).
 #pragma once
 #include "wdb_internal.h"
 
 namespace wdb {
 
 struct StencilArgs {
-    OpDev op;
     const SubbandDev* sb;    // device, S entries
     const int* vb_start;     // device, S+1 entries
     int S;
@@ -21,14 +20,7 @@ struct RedTarget {
 int stencil_grid_limit();
 
 template <typename T>
-wdb_status launch_apply(const StencilArgs& A, int grid, const T* in, T* out, const double* scale, RedTarget* red,
-                        cudaStream_t st);
-template <typename T>
 wdb_status launch_scale(const StencilArgs& A, int grid, const T* in, T* out, const double* scale, cudaStream_t st);
-wdb_status launch_k1(const StencilArgs& A, int grid, const float* y, const float* x0, float* r, double* part,
-                     SolveState* s, cudaStream_t st);
-wdb_status launch_k2(const StencilArgs& A, int grid, const float* r, float* y, float* x, const float* step_tab,
-                     const float* w_sb, double* part, SolveState* s, cudaStream_t st);
 wdb_status launch_fft_step(const StencilArgs& A, int grid, const float* g, float* y, float* x,
                            const float* step_tab, const float* w_sb, double* part, SolveState* s,
                            cudaStream_t st);
@@ -40,7 +32,5 @@ template <typename T>
 wdb_status launch_splitmix(T* v, long long n, unsigned long long seed, cudaStream_t st);
 template <typename T>
 wdb_status launch_scale_const(const T* in, T* out, long long n, double s, cudaStream_t st);
-wdb_status launch_residual_norm(const StencilArgs& A, int grid, const float* x, const float* x0, float* r,
-                                RedTarget red, cudaStream_t st);
 
 }  // namespace wdb

@@ -9,7 +9,8 @@
 //     radix select over the 128-bit composite key (8-bit digits, histogram weights =
 //     multiplicities) finds the first tap whose entries would exceed K; everything before
 //     it in key order is kept. Numerical zeros (|v| <= 1e-14 max|v|) never enter.
-//  4. packing (host): kept taps -> gather stencils of Theta_K and Theta_K^T.
+//  4. packing (host): kept taps -> gather-form tap lists of Theta_K and Theta_K^T, tiled
+//     into the shared-memory plans of tile.cu (autotuned on the GPU).
 //  5. diag(M), diag(M^2), M = Theta_K^T Theta_K, per phase class by comb probes: impulses of
 //     one phase class spaced further apart than the reach of M^2, one Theta_K and one
 //     Theta_K^T application, norms divided by the number of impulses.
@@ -190,9 +191,8 @@ static wdb_status upload(wdb_theta* th, const std::vector<T>& h, T** d, cudaStre
     return WDB_OK;
 }
 
-StencilArgs stencil_args(const wdb_theta* th, bool adj) {
+StencilArgs stencil_args(const wdb_theta* th) {
     StencilArgs A;
-    A.op = adj ? th->adj : th->fwd;
     A.sb = th->d_sb;
     A.vb_start = th->d_vb_start;
     A.S = th->lay.S;
@@ -203,7 +203,9 @@ StencilArgs stencil_args(const wdb_theta* th, bool adj) {
 RedTarget th_red(const wdb_theta* th, double* out) { return RedTarget{th->d_counter, th->d_red_part, out}; }
 
 // ---------------------------------------------------------------------------------------
-// Packing kept taps into gather stencils
+// Kept taps in gather form, one list per operator (Theta_K, Theta_K^T)
+//   down pair (input finer or equal, ratio r = 2^lg): out[p] += v * in[r p + d]
+//   up pair   (input coarser, r = 2^lg):  out[r P + phi] += v * in[P + d] for taps of phase phi
 // ---------------------------------------------------------------------------------------
 struct PEntry {
     int out, in, up, lg, phase, dy, dx;
@@ -212,55 +214,6 @@ struct PEntry {
         return std::tie(out, in, up, lg, phase, dy, dx) < std::tie(o.out, o.in, o.up, o.lg, o.phase, o.dy, o.dx);
     }
 };
-
-static void pack_op(const Layout& L, std::vector<PEntry>& E, OpHost& op) {
-    std::sort(E.begin(), E.end());
-    op.pair_start.assign(L.S + 1, 0);
-    op.pairs.clear();
-    op.phase_idx.clear();
-    op.tap_off.clear();
-    op.tap_v.clear();
-    op.tap_v64.clear();
-    size_t i = 0;
-    for (int o = 0; o < L.S; ++o) {
-        op.pair_start[o] = (int)op.pairs.size();
-        while (i < E.size() && E[i].out == o) {
-            const int in = E[i].in, up = E[i].up, lg = E[i].lg;
-            size_t j = i;
-            while (j < E.size() && E[j].out == o && E[j].in == in) ++j;
-            PairDesc d;
-            d.in_sb = in;
-            d.meta = (up << 8) | lg;
-            if (!up) {
-                d.a = (int)op.tap_off.size();
-                for (size_t t = i; t < j; ++t) {
-                    op.tap_off.push_back((E[t].dy << 16) | (E[t].dx & 0xffff));
-                    op.tap_v.push_back((float)E[t].v);
-                    op.tap_v64.push_back(E[t].v);
-                }
-                d.b = (int)op.tap_off.size();
-            } else {
-                const int nph = 1 << (2 * lg);
-                d.a = (int)op.phase_idx.size();
-                d.b = d.a + nph;
-                size_t t = i;
-                for (int ph = 0; ph < nph; ++ph) {
-                    op.phase_idx.push_back((int)op.tap_off.size());
-                    while (t < j && E[t].phase == ph) {
-                        op.tap_off.push_back((E[t].dy << 16) | (E[t].dx & 0xffff));
-                        op.tap_v.push_back((float)E[t].v);
-                        op.tap_v64.push_back(E[t].v);
-                        ++t;
-                    }
-                }
-                op.phase_idx.push_back((int)op.tap_off.size());
-            }
-            op.pairs.push_back(d);
-            i = j;
-        }
-    }
-    op.pair_start[L.S] = (int)op.pairs.size();
-}
 
 static void build_ops(wdb_theta* th) {
     const Layout& L = th->lay;
@@ -289,8 +242,8 @@ static void build_ops(wdb_theta* th) {
                          t.v});
         }
     }
-    pack_op(L, F, th->fwd_h);
-    pack_op(L, A, th->adj_h);
+    std::sort(F.begin(), F.end());
+    std::sort(A.begin(), A.end());
     // the tiles are shared by about 3 resident CTAs per SM
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -340,6 +293,7 @@ wdb_status temp_plan(const wdb_theta* th, const TilePlanHost& h, TempPlan& d, cu
     WDB_TRY(temp_copy(d, h.tap_lin, &p.tap_lin, st));
     WDB_TRY(temp_copy(d, h.tap_v, &p.tap_v, st));
     WDB_TRY(temp_copy(d, h.tap_v64, &p.tap_v64, st));
+    WDB_TRY(temp_copy(d, h.tap_ov, &p.tap_ov, st));
     p.n_items = (int)h.items.size();
     p.buf_elems = h.buf_elems;
     p.smem_bytes = h.smem_bytes;
@@ -459,6 +413,7 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
     WDB_TRY(upload(th, h.tap_lin, const_cast<int**>(&a.plan.tap_lin), st));
     WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&a.plan.tap_v), st));
     WDB_TRY(upload(th, h.tap_v64, const_cast<double**>(&a.plan.tap_v64), st));
+    WDB_TRY(upload(th, h.tap_ov, const_cast<TapOV**>(&a.plan.tap_ov), st));
     a.plan.n_items = (int)h.items.size();
     a.plan.buf_elems = h.buf_elems;
     a.plan.smem_bytes = h.smem_bytes;
@@ -483,19 +438,6 @@ wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st) {
         WDB_TRY(upload_plan(th, th->bplan[op], th->bargs[op], st));
     }
     th->bplan_ok = true;
-    return WDB_OK;
-}
-
-static wdb_status upload_op(wdb_theta* th, const OpHost& h, OpDev& d, cudaStream_t st) {
-    WDB_TRY(upload(th, h.pair_start, const_cast<int**>(&d.pair_start), st));
-    WDB_TRY(upload(th, h.pairs, const_cast<PairDesc**>(&d.pairs), st));
-    WDB_TRY(upload(th, h.phase_idx, const_cast<int**>(&d.phase_idx), st));
-    WDB_TRY(upload(th, h.tap_off, const_cast<int**>(&d.tap_off), st));
-    WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&d.tap_v), st));
-    WDB_TRY(upload(th, h.tap_v64, const_cast<double**>(&d.tap_v64), st));
-    d.n_pairs = (int)h.pairs.size();
-    d.n_taps = (int)h.tap_off.size();
-    d.n_phase = (int)h.phase_idx.size();
     return WDB_OK;
 }
 
@@ -571,7 +513,7 @@ static wdb_status diag_tables(wdb_theta* th, cudaStream_t st) {
     return WDB_OK;
 }
 
-// Upload taps, build stencils, schedule, workspace for reductions, diag tables.
+// Tile plans, subband schedule, workspace for reductions, diag tables.
 wdb_status theta_finalize(wdb_theta* th, cudaStream_t st) {
     const Layout& L = th->lay;
     th->K_eff = 0;
@@ -580,8 +522,6 @@ wdb_status theta_finalize(wdb_theta* th, cudaStream_t st) {
         th->K_eff += std::min((long long)sa.rows * sa.cols, (long long)sb.rows * sb.cols);
     }
     build_ops(th);
-    WDB_TRY(upload_op(th, th->fwd_h, th->fwd, st));
-    WDB_TRY(upload_op(th, th->adj_h, th->adj, st));
     std::vector<SubbandDev> sbv(L.sb, L.sb + L.S);
     WDB_TRY(upload(th, sbv, &th->d_sb, st));
     th->sched = make_schedule(L);
@@ -782,7 +722,7 @@ static wdb_status power_iteration(wdb_theta* th, const std::vector<double>& P, c
     WDB_CK(cudaMalloc(&d_sc, sizeof(double) * sc.size()));
     WDB_CK(cudaMalloc(&d_out, sizeof(double)));
     WDB_CK(cudaMemcpyAsync(d_sc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
-    StencilArgs F = stencil_args(th, false);
+    StencilArgs F = stencil_args(th);
     const bool f64 = sizeof(T) == 8;
     TileArgs TF = tile_args(th, false, f64), TA = tile_args(th, true, f64);
     wdb_status s = WDB_OK;

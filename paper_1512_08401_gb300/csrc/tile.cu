@@ -341,9 +341,15 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             if (bt.tap_end < bt.tap_begin) bt.tap_end = bt.tap_begin;
             const int nt = bt.tap_end - bt.tap_begin;
             const int reg = batch_regions[bi - sub.batch_begin];
-            bt.tap_soff = reg * esize / 4;                                   // in ints
-            bt.val_soff = (int)(((long long)(bt.tap_soff + nt) * 4 + esize - 1) / esize);   // in T
-            const int total = (bt.val_soff + nt) * esize;
+            bt.tap_soff = reg * esize / 4;   // in ints (regions are whole 16-byte chunks)
+            int total;
+            if (esize == 4) {                // (offset, value) records
+                bt.val_soff = bt.tap_soff;
+                total = bt.tap_soff * 4 + nt * (int)sizeof(TapOV);
+            } else {                         // offsets, then the values
+                bt.val_soff = (int)(((long long)(bt.tap_soff + nt) * 4 + esize - 1) / esize);   // in T
+                total = (bt.val_soff + nt) * esize;
+            }
             max_bytes = std::max(max_bytes, (total + 15) / 16 * 16);
         }
         sub.pair_end = (int)plan.pairs.size();
@@ -369,6 +375,8 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         plan.items.push_back(ic.it);
         plan.item_cost.push_back(ic.cost);
     }
+    plan.tap_ov.resize(plan.tap_off.size());
+    for (size_t k = 0; k < plan.tap_off.size(); ++k) plan.tap_ov[k] = TapOV{plan.tap_off[k], plan.tap_v[k]};
     plan.pair_sm.resize(plan.pairs.size());
     for (size_t k = 0; k < plan.pairs.size(); ++k) {
         const SubbandDev& si = L.sb[plan.pairs[k].in_sb];
@@ -405,6 +413,55 @@ template <>
 __device__ __forceinline__ const float* tvals<float>(const TilePlanDev& p) { return p.tap_v; }
 template <>
 __device__ __forceinline__ const double* tvals<double>(const TilePlanDev& p) { return p.tap_v64; }
+
+// Taps of a batch as the inner loops read them: FP32 from (offset, value) records (one 8-byte
+// load), FP64 from the separate offset and value arrays.
+template <typename T>
+struct TapSrc;
+template <>
+struct TapSrc<float> {
+    const TapOV* ov;
+    __device__ __forceinline__ void get(int j, int& o, float& v) const {
+        const TapOV q = ov[j];
+        o = q.off;
+        v = q.v;
+    }
+    __device__ __forceinline__ TapSrc operator+(int k) const { return TapSrc{ov + k}; }
+};
+template <>
+struct TapSrc<double> {
+    const int* to;
+    const double* tv;
+    __device__ __forceinline__ void get(int j, int& o, double& v) const {
+        o = to[j];
+        v = tv[j];
+    }
+    __device__ __forceinline__ TapSrc operator+(int k) const { return TapSrc{to + k, tv + k}; }
+};
+
+// The batch's staged taps, indexed by plan tap index.
+template <typename T>
+__device__ __forceinline__ TapSrc<T> staged_taps(const T* S, const TileBatch& bt);
+template <>
+__device__ __forceinline__ TapSrc<float> staged_taps<float>(const float* S, const TileBatch& bt) {
+    return TapSrc<float>{reinterpret_cast<const TapOV*>(reinterpret_cast<const int*>(S) + bt.tap_soff) - bt.tap_begin};
+}
+template <>
+__device__ __forceinline__ TapSrc<double> staged_taps<double>(const double* S, const TileBatch& bt) {
+    return TapSrc<double>{reinterpret_cast<const int*>(S) + bt.tap_soff - bt.tap_begin, S + bt.val_soff - bt.tap_begin};
+}
+
+// The plan's taps in global memory.
+template <typename T>
+__device__ __forceinline__ TapSrc<T> global_taps(const TilePlanDev& p);
+template <>
+__device__ __forceinline__ TapSrc<float> global_taps<float>(const TilePlanDev& p) {
+    return TapSrc<float>{p.tap_ov};
+}
+template <>
+__device__ __forceinline__ TapSrc<double> global_taps<double>(const TilePlanDev& p) {
+    return TapSrc<double>{p.tap_off, p.tap_v64};
+}
 
 __device__ __forceinline__ int wrap1(int v, int n) {
     v += (v < 0) ? n : 0;
@@ -529,12 +586,18 @@ __device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const T* __
         }
     }
     const int nt = bt.tap_end - bt.tap_begin;
-    const unsigned toff = S0 + (unsigned)bt.tap_soff * 4u, tval = S0 + (unsigned)bt.val_soff * ES;
-    const T* __restrict__ vals = tvals<T>(plan) + bt.tap_begin;
-    const int* __restrict__ offs = plan.tap_off + bt.tap_begin;
-    for (int j = threadIdx.x; j < nt; j += kTileThreads) {
-        cp_async_to<4>(toff + 4u * j, offs + j);
-        cp_async_to<ES>(tval + ES * j, vals + j);
+    const unsigned toff = S0 + (unsigned)bt.tap_soff * 4u;
+    if (sizeof(T) == 4) {   // (offset, value) records, 8 bytes each
+        const TapOV* __restrict__ ov = plan.tap_ov + bt.tap_begin;
+        for (int j = threadIdx.x; j < nt; j += kTileThreads) cp_async_to<8>(toff + 8u * j, ov + j);
+    } else {
+        const unsigned tval = S0 + (unsigned)bt.val_soff * ES;
+        const T* __restrict__ vals = tvals<T>(plan) + bt.tap_begin;
+        const int* __restrict__ offs = plan.tap_off + bt.tap_begin;
+        for (int j = threadIdx.x; j < nt; j += kTileThreads) {
+            cp_async_to<4>(toff + 4u * j, offs + j);
+            cp_async_to<ES>(tval + ES * j, vals + j);
+        }
     }
 }
 
@@ -577,12 +640,14 @@ __device__ __forceinline__ ThreadMap thread_map(const TileItem& w) {
 
 // Down pair, 4 outputs SX words apart in the plane; taps j = j0, j0 + G, ...
 template <int SX, typename T>
-__device__ __forceinline__ void down_taps4(const int* __restrict__ to, const T* __restrict__ tv, int j0, int n, int G,
-                                           const T* __restrict__ Sb, T (&acc)[4]) {
+__device__ __forceinline__ void down_taps4(const TapSrc<T> ts, int j0, int n, int G, const T* __restrict__ Sb,
+                                           T (&acc)[4]) {
 #pragma unroll 2
     for (int j = j0; j < n; j += G) {
-        const T v = tv[j];
-        const T* s = Sb + to[j];
+        int o;
+        T v;
+        ts.get(j, o, v);
+        const T* s = Sb + o;
         acc[0] = fma(v, s[0], acc[0]);
         acc[1] = fma(v, s[SX], acc[1]);
         acc[2] = fma(v, s[2 * SX], acc[2]);
@@ -593,16 +658,15 @@ __device__ __forceinline__ void down_taps4(const int* __restrict__ to, const T* 
 // Up pair with staged phase tables and r dividing the output stride sx: the 4 outputs of a
 // thread share one phase and their coarse columns are STEP = sx / r apart; taps j0, j0 + G, ...
 template <int STEP, typename T>
-__device__ __forceinline__ void up_taps4(const int* __restrict__ to, const T* __restrict__ tv, int j0, int n, int G,
-                                         int rr, const T* __restrict__ Sb, T (&acc)[4]) {
-    to += j0 * rr;
-    tv += j0 * rr;
+__device__ __forceinline__ void up_taps4(TapSrc<T> ts, int j0, int n, int G, int rr, const T* __restrict__ Sb,
+                                         T (&acc)[4]) {
+    ts = ts + j0 * rr;
     const int stp = G * rr;
     for (int j = j0; j < n; j += G) {
-        const int o = *to;
-        const T v = *tv;
-        to += stp;
-        tv += stp;
+        int o;
+        T v;
+        ts.get(0, o, v);
+        ts = ts + stp;
         const T* s = Sb + o;
         acc[0] = fma(v, s[0], acc[0]);
         acc[1] = fma(v, s[STEP], acc[1]);
@@ -617,8 +681,7 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                                               const SubbandDev& so, int bi, const T* __restrict__ S,
                                               const PairSm* __restrict__ tab, const ThreadMap& tm, T (&acc)[4]) {
     const TileBatch bt = plan.batches[bi];
-    const int* __restrict__ soffs = reinterpret_cast<const int*>(S) + bt.tap_soff - bt.tap_begin;
-    const T* __restrict__ svals = S + bt.val_soff - bt.tap_begin;
+    const TapSrc<T> stap = staged_taps<T>(S, bt);
     const T* __restrict__ gvals = tvals<T>(plan);
     const int E = tm.E, G = tm.G, g = tm.g;
     const int np = bt.pair_end - bt.pair_begin;
@@ -627,21 +690,29 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
         const int sh = tab[i].shift;   // staged column of the region's first column (vec pairs)
         const int lg = P.lg, r = 1 << lg, m = r - 1;
         if (P.mode == kDown) {
-            const int* __restrict__ to = soffs + P.tap_begin;
-            const T* __restrict__ tv = svals + P.tap_begin;
+            const TapSrc<T> ts = stap + P.tap_begin;
             const T* __restrict__ Sb = S + tm.ly * P.PC + tm.lx + sh;
             if (E == 4) {
-                if (tm.sx == 8) down_taps4<8, T>(to, tv, g, P.ntap, G, Sb, acc);
-                else if (tm.sx == 4) down_taps4<4, T>(to, tv, g, P.ntap, G, Sb, acc);
-                else down_taps4<2, T>(to, tv, g, P.ntap, G, Sb, acc);
+                if (tm.sx == 8) down_taps4<8, T>(ts, g, P.ntap, G, Sb, acc);
+                else if (tm.sx == 4) down_taps4<4, T>(ts, g, P.ntap, G, Sb, acc);
+                else down_taps4<2, T>(ts, g, P.ntap, G, Sb, acc);
             } else {
                 T a0 = 0, a1 = 0;
                 int j = g;
                 for (; j + G < P.ntap; j += 2 * G) {
-                    a0 = fma(tv[j], Sb[to[j]], a0);
-                    a1 = fma(tv[j + G], Sb[to[j + G]], a1);
+                    int o0, o1;
+                    T v0, v1;
+                    ts.get(j, o0, v0);
+                    ts.get(j + G, o1, v1);
+                    a0 = fma(v0, Sb[o0], a0);
+                    a1 = fma(v1, Sb[o1], a1);
                 }
-                if (j < P.ntap) a0 = fma(tv[j], Sb[to[j]], a0);
+                if (j < P.ntap) {
+                    int o0;
+                    T v0;
+                    ts.get(j, o0, v0);
+                    a0 = fma(v0, Sb[o0], a0);
+                }
                 acc[0] += a0 + a1;
             }
         } else if (P.mode == kUp) {
@@ -652,43 +723,44 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
             const int py = w.ty0 + tm.ly, px = w.tx0 + tm.lx;
             const int rowb = ((py >> lg) - (w.ty0 >> lg)) * P.PC + sh;
             const bool st = lg <= kUpStagedLgDev;   // phase tables staged with the batch
-            const int* __restrict__ gto = (st ? soffs : plan.tap_off) + P.tap_begin;
-            const T* __restrict__ gtv = (st ? svals : gvals) + P.tap_begin;
+            const TapSrc<T> gts = (st ? stap : global_taps<T>(plan)) + P.tap_begin;
             if (E == 4 && st && lg <= tm.lgsx) {
                 const int ph = ((py & m) << lg) + (px & m);
                 const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
                 const int stepc = tm.lgsx - lg;   // log2 of the coarse column step
-                if (stepc == 2) up_taps4<4, T>(gto + ph, gtv + ph, g, P.ntap, G, rr, Sb, acc);
-                else if (stepc == 1) up_taps4<2, T>(gto + ph, gtv + ph, g, P.ntap, G, rr, Sb, acc);
-                else up_taps4<1, T>(gto + ph, gtv + ph, g, P.ntap, G, rr, Sb, acc);
+                if (stepc == 2) up_taps4<4, T>(gts + ph, g, P.ntap, G, rr, Sb, acc);
+                else if (stepc == 1) up_taps4<2, T>(gts + ph, g, P.ntap, G, rr, Sb, acc);
+                else up_taps4<1, T>(gts + ph, g, P.ntap, G, rr, Sb, acc);
             } else if (E == 4) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int pxe = px + tm.sx * e;
                     const int ph = ((py & m) << lg) + (pxe & m);
                     const T* __restrict__ Sb = S + rowb + ((pxe >> lg) - (w.tx0 >> lg));
-                    const int* __restrict__ to = gto + ph + g * rr;
-                    const T* __restrict__ tv = gtv + ph + g * rr;
+                    TapSrc<T> ts = gts + (ph + g * rr);
                     const int stp = G * rr;
                     T a = 0;
                     for (int j = g; j < P.ntap; j += G) {
-                        a = fma(*tv, Sb[*to], a);
-                        to += stp;
-                        tv += stp;
+                        int o;
+                        T v;
+                        ts.get(0, o, v);
+                        a = fma(v, Sb[o], a);
+                        ts = ts + stp;
                     }
                     acc[e] += a;
                 }
             } else {
                 const int ph = ((py & m) << lg) + (px & m);
                 const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
-                const int* __restrict__ to = gto + ph + g * rr;
-                const T* __restrict__ tv = gtv + ph + g * rr;
+                TapSrc<T> ts = gts + (ph + g * rr);
                 const int stp = G * rr;
                 T a = 0;
                 for (int j = g; j < P.ntap; j += G) {
-                    a = fma(*tv, Sb[*to], a);
-                    to += stp;
-                    tv += stp;
+                    int o;
+                    T v;
+                    ts.get(0, o, v);
+                    a = fma(v, Sb[o], a);
+                    ts = ts + stp;
                 }
                 acc[0] += a;
             }

@@ -57,8 +57,9 @@ struct TileTune {     // autotuner's choice for one output subband (ts = 0: the 
 struct alignas(16) TileBatch {    // pairs [pair_begin, pair_end) of one subband, staged together
     int pair_begin, pair_end;
     int tap_begin, tap_end;       // taps of the staged pairs, copied to shared memory
-    int tap_soff;                 // element offset of the tap offsets (ints) in the buffer
-    int val_soff;                 // element offset of the tap values in the buffer
+    int tap_soff;                 // int offset of the staged taps in the buffer (FP32: TapOV
+                                  // records there; FP64: the offsets, values at val_soff)
+    int val_soff;                 // FP64: element offset of the tap values (FP32: = tap_soff)
     int pad[2];
 };
 
@@ -67,6 +68,12 @@ struct alignas(16) TileItem {     // one tile; carries what the kernel needs wit
     int ty0, tx0;
     int batch_begin, batch_end;   // the subband's batches
     int TS, lgTS, e4;             // the subband's tile side and thread map
+};
+
+// One FP32 tap as the kernel reads it: offset and value in one 8-byte load.
+struct alignas(8) TapOV {
+    int off;
+    float v;
 };
 
 // A pair's descriptor with its input subband's geometry (the per-batch shared-memory table
@@ -89,6 +96,7 @@ struct TilePlanDev {
     const int* tap_lin;       // global pairs: dy * (input columns) + dx (interior fast path)
     const float* tap_v;
     const double* tap_v64;
+    const TapOV* tap_ov;      // (tap_off, tap_v) interleaved: the FP32 kernels' tap records
     int n_items;
     int buf_elems;            // elements of one staging buffer (two buffers per CTA)
     int smem_bytes;           // dynamic shared memory per CTA
@@ -104,6 +112,7 @@ struct TilePlanHost {
     std::vector<int> tap_lin;
     std::vector<float> tap_v;
     std::vector<double> tap_v64;
+    std::vector<TapOV> tap_ov;
     std::vector<double> item_cost;   // estimated cost of every item (items are sorted by it)
     int buf_elems = 0;
     int smem_bytes = 0;

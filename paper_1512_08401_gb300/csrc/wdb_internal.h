@@ -55,36 +55,6 @@ struct RedSlot {
     double sum[4];
 };
 
-// ---------------------------------------------------------------------------------------
-// Stencil representation of Theta_K / Theta_K^T as gather operators
-//   down pair (input finer or equal, ratio r = 2^lg): out[p] += v * in[r p + d]
-//   up pair   (input coarser, r = 2^lg):  out[r P + phi] += v * in[P + d] for taps of phase phi
-// ---------------------------------------------------------------------------------------
-struct PairDesc {
-    int in_sb;
-    int meta;       // (up << 8) | lg
-    int a, b;       // down: taps [a, b);  up: phase table at phase_idx[a .. a + r*r]
-};
-
-struct OpDev {
-    const int* pair_start;   // [S+1] pairs of output subband o: [pair_start[o], pair_start[o+1])
-    const PairDesc* pairs;
-    const int* phase_idx;
-    const int* tap_off;      // (dy << 16) | (dx & 0xffff)
-    const float* tap_v;
-    const double* tap_v64;
-    int n_pairs, n_taps, n_phase;
-};
-
-struct OpHost {
-    std::vector<int> pair_start;
-    std::vector<PairDesc> pairs;
-    std::vector<int> phase_idx;
-    std::vector<int> tap_off;
-    std::vector<float> tap_v;
-    std::vector<double> tap_v64;
-};
-
 // Virtual-block schedule: blocks of kVB consecutive outputs that stay inside one subband.
 constexpr int kVB = 256;
 struct Schedule {
@@ -153,8 +123,6 @@ struct wdb_theta {
     long long K_requested = 0, K_eff = 0, n_candidates = 0;
     double theta_max_abs = 0.0, build_ms = 0.0;
     std::vector<wdb::Tap> taps;            // sorted (a, b, oy, ox)
-    wdb::OpHost fwd_h, adj_h;
-    wdb::OpDev fwd{}, adj{};
     wdb::TilePlanHost tplan[2][2];         // [0 Theta_K, 1 Theta_K^T][0 FP32, 1 FP64]
     std::vector<wdb::TileEntry> tent[2];   // gather-form taps of Theta_K and Theta_K^T (plan input)
     int plan_ctas = 0;                     // CTAs the plans are balanced for
