@@ -269,8 +269,9 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     const float* step = pc.d_step;
     E.enqueue = [=](int iters) -> wdb_status {
         for (int i = 0; i < iters; ++i) {
-            WDB_TRY(tile_k1(F, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st));
-            WDB_TRY(tile_k2(A, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st));
+            // each kernel after the first is a programmatic dependent of the one before it
+            WDB_TRY(tile_k1(F, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st, i > 0));
+            WDB_TRY(tile_k2(A, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st, true));
         }
         return WDB_OK;
     };

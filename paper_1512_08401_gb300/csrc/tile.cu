@@ -886,6 +886,9 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
     T* const buf0 = reinterpret_cast<T*>(smem_raw);
     T* const buf1 = buf0 + A.plan.buf_elems;
     __shared__ T red_buf[4 * kTileThreads];
+    // launched as a programmatic dependent of the previous FISTA kernel: nothing it wrote is
+    // read before that grid has completed (a no-op for ordinary launches)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     if (EPI == kK1 || EPI == kK2) {
         if (*(volatile int*)&ep.st->stop) return;
     }
@@ -948,6 +951,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         tab = tab_next;
         tab_next = tt;
     }
+    // this CTA has no more tiles: the next kernel of the stream may start its CTAs
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     cp_async_wait<0>();
     __syncthreads();
     double v[2] = {pt.d0 + (double)pt.s0 + (double)pt.c0, EPI == kK2 ? (double)pt.mx : (double)pt.s1 + (double)pt.c1}, tot[2];
@@ -1141,14 +1146,30 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
     }
 }
 
+// pdl: programmatic dependent launch, so that this grid's CTAs are scheduled while the
+// previous kernel of the stream drains (the kernel waits for that grid before its work)
 template <typename T, int EPI>
-wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st) {
+wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl = false) {
     static bool attr = false;
     if (!attr) {
         WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         attr = true;
     }
-    tile_kernel<T, EPI><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
+    if (pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)A.grid);
+        cfg.blockDim = dim3(kTileThreads);
+        cfg.dynamicSmemBytes = (size_t)A.plan.smem_bytes;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        WDB_CK(cudaLaunchKernelEx(&cfg, tile_kernel<T, EPI>, A, in, out, ep));
+    } else {
+        tile_kernel<T, EPI><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
+    }
     count_launch();
     WDB_CK(cudaGetLastError());
     return WDB_OK;
@@ -1203,16 +1224,16 @@ wdb_status tile_apply(const TileArgs& A, const T* in, T* out, const double* scal
 }
 
 wdb_status tile_k1(const TileArgs& A, const float* y, const float* x0, float* r, double* part, SolveState* s,
-                   cudaStream_t st) {
+                   cudaStream_t st, bool pdl) {
     EpiArgs ep{};
     ep.x0 = x0;
     ep.part = part;
     ep.st = s;
-    return launch_tile<float, kK1>(A, y, r, ep, st);
+    return launch_tile<float, kK1>(A, y, r, ep, st, pdl);
 }
 
 wdb_status tile_k2(const TileArgs& A, const float* r, float* y, float* x, const float* step_tab, const float* w_sb,
-                   double* part, SolveState* s, cudaStream_t st) {
+                   double* part, SolveState* s, cudaStream_t st, bool pdl) {
     EpiArgs ep{};
     ep.y = y;
     ep.x = x;
@@ -1220,7 +1241,7 @@ wdb_status tile_k2(const TileArgs& A, const float* r, float* y, float* x, const 
     ep.w_sb = w_sb;
     ep.part = part;
     ep.st = s;
-    return launch_tile<float, kK2>(A, r, nullptr, ep, st);
+    return launch_tile<float, kK2>(A, r, nullptr, ep, st, pdl);
 }
 
 wdb_status tile_resnorm(const TileArgs& A, const float* x, const float* x0, float* r, double* out, double* part,

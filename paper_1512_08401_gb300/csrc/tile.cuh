@@ -180,10 +180,12 @@ wdb_status batch_objective(const BatchArgs& B, cudaStream_t st);
 template <typename T>
 wdb_status tile_apply(const TileArgs& A, const T* in, T* out, const double* scale, double* norm_out,
                       double* part, cudaStream_t st);
+// pdl: launch as a programmatic dependent of the previous kernel in the stream (the FISTA
+// loop's K1 / K2 alternation)
 wdb_status tile_k1(const TileArgs& A, const float* y, const float* x0, float* r, double* part, SolveState* s,
-                   cudaStream_t st);
+                   cudaStream_t st, bool pdl = false);
 wdb_status tile_k2(const TileArgs& A, const float* r, float* y, float* x, const float* step_tab,
-                   const float* w_sb, double* part, SolveState* s, cudaStream_t st);
+                   const float* w_sb, double* part, SolveState* s, cudaStream_t st, bool pdl = false);
 wdb_status tile_resnorm(const TileArgs& A, const float* x, const float* x0, float* r, double* out, double* part,
                         cudaStream_t st);
 int tile_grid(int smem_bytes);
