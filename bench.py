@@ -154,20 +154,6 @@ def measured_peaks():
         return 6800.0, "of fallback"
 
 
-def kernel_sources_sha256(files) -> str:
-    """sha256 over the given csrc files (the sources a kernel is compiled from)."""
-    import hashlib
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1512_08401_gb300", "csrc")
-    for f in sorted(files):
-        h.update(f.encode())
-        h.update(open(os.path.join(csrc, f), "rb").read())
-    return h.hexdigest()
-
-
-TILE_SOURCES = ["tile.cu", "tile.cuh", "device_util.cuh", "layout_types.h", "wdb_internal.h"]
-
-
 def traffic_record(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` on `workload` from the committed ncu summary
     (profiles/traffic.json), if the kernel's sources are unchanged since (else None)."""
@@ -181,6 +167,7 @@ def traffic_record(kernel: str, workload: str):
     if not entry:
         return None
     try:
+        from paper_1512_08401_gb300.ncu_summary import kernel_sources_sha256
         if entry.get("sources_sha256") != kernel_sources_sha256(entry["sources"]):
             return None
     except (KeyError, OSError):

@@ -1,14 +1,40 @@
-"""Summarise an ncu launch list (--metrics gpu__time_duration.sum --csv) per kernel:
-launches, total device time and share, split by NVTX range when ncu recorded one.
+"""ncu output helpers.
+
+Summarise a launch list (--metrics gpu__time_duration.sum --csv) per kernel: launches,
+total device time and share, split by NVTX range when ncu recorded one:
 
     python -m paper_1512_08401_gb300.ncu_summary launches.csv
+
+Record the DRAM bytes per launch of the two FISTA kernels from a capture that holds
+dram__bytes_read.sum and dram__bytes_write.sum (the first launch of each kernel), with the
+hash of the sources they were compiled from, in profiles/traffic.json (bench.py reports the
+record only while the sources still hash the same):
+
+    ncu -i capture.ncu-rep --page raw --csv > raw.csv      (or an ncu --csv metrics log)
+    python -m paper_1512_08401_gb300.ncu_summary traffic raw.csv 4096 profiles/tile_kernels_4096_full.md
 """
 from __future__ import annotations
 
 import csv
+import hashlib
+import json
+import os
 import re
 import sys
 from collections import defaultdict
+
+CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+TILE_SOURCES = ["tile.cu", "tile.cuh", "device_util.cuh", "layout_types.h", "wdb_internal.h"]
+FISTA_KERNELS = {"k1_residual": "tile_kernel<float, 2>", "k2_step": "tile_kernel<float, 3>"}
+
+
+def kernel_sources_sha256(files) -> str:
+    """sha256 over the given csrc files (the sources a kernel is compiled from)."""
+    h = hashlib.sha256()
+    for f in sorted(files):
+        h.update(f.encode())
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()
 
 
 def short(name: str) -> str:
@@ -48,5 +74,76 @@ def summarise(path: str) -> str:
     return "\n".join(out)
 
 
+def _kernel_label(name: str) -> str:
+    n = name.replace("(int)", "")
+    n = re.sub(r"wdb::(\(anonymous namespace\)|_GLOBAL__N__\w+)::", "", n)
+    return short(n)
+
+
+# to bytes and microseconds
+_UNIT = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "nsecond": 1e-3, "usecond": 1, "msecond": 1e3,
+         "ns": 1e-3, "us": 1, "ms": 1e3}
+
+
+def fista_dram(path: str) -> dict:
+    """DRAM bytes and duration of the first launch of each FISTA kernel in an ncu CSV: either
+    a raw page (one row per launch, one column per metric) or a --csv metrics log (one row
+    per launch and metric)."""
+    rows = list(csv.reader(line for line in open(path) if not line.startswith("==")))
+    head = rows[0]
+    per = defaultdict(dict)   # (launch id, kernel) -> metric -> value
+    if "Metric Name" in head:
+        ki, ni, vi = head.index("Kernel Name"), head.index("Metric Name"), head.index("Metric Value")
+        ii, ui = head.index("ID"), head.index("Metric Unit")
+        for r in rows[1:]:
+            if len(r) > max(ki, ni, vi, ui):
+                per[(int(r[ii]), r[ki])][r[ni]] = float(r[vi].replace(",", "")) * _UNIT.get(r[ui], 1)
+    else:
+        ki, ii = head.index("Kernel Name"), head.index("ID")
+        cols = {m: head.index(m) for m in ("dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum")
+                if m in head}
+        units = rows[1]
+        for r in rows[2:]:
+            if len(r) > ki:
+                d = {}
+                for m, c in cols.items():
+                    v = float(r[c].replace(",", ""))
+                    d[m] = v * _UNIT.get(units[c], 1)
+                per[(int(r[ii]), r[ki])] = d
+    out = {}
+    for (lid, kname), d in sorted(per.items()):
+        label = _kernel_label(kname)
+        for key, want in FISTA_KERNELS.items():
+            if key not in out and label.endswith(want):
+                out[key] = d
+    return out
+
+
+def write_traffic(csv_path: str, workload: str, profile: str, record: str) -> dict:
+    """Update `record` (profiles/traffic.json) for `workload` from the capture in `csv_path`."""
+    got = fista_dram(csv_path)
+    rec = json.load(open(record)) if os.path.exists(record) else {}
+    rec.setdefault("_about", "DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the "
+                             "FISTA kernels from ncu captures; valid while the listed sources hash to "
+                             "sources_sha256.")
+    sha = kernel_sources_sha256(TILE_SOURCES)
+    ent = rec.setdefault(workload, {})
+    for key, d in got.items():
+        rd, wr = d.get("dram__bytes_read.sum", 0.0), d.get("dram__bytes_write.sum", 0.0)
+        ent[key] = {"kernel": FISTA_KERNELS[key], "dram_bytes_per_launch": int(round(rd + wr)),
+                    "dram_read": int(round(rd)), "dram_write": int(round(wr)),
+                    "duration_us_under_ncu": round(d.get("gpu__time_duration.sum", 0.0), 2),
+                    "sources": TILE_SOURCES, "sources_sha256": sha, "profile": profile}
+    with open(record, "w") as fh:
+        json.dump(rec, fh, indent=1)
+        fh.write("\n")
+    return got
+
+
 if __name__ == "__main__":
-    print(summarise(sys.argv[1]))
+    if len(sys.argv) >= 2 and sys.argv[1] == "traffic":
+        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        print(json.dumps(write_traffic(sys.argv[2], sys.argv[3], sys.argv[4],
+                                       os.path.join(root, "profiles", "traffic.json")), indent=1))
+    else:
+        print(summarise(sys.argv[1]))
