@@ -171,7 +171,19 @@ wdb_status wdb_theta_info_get(const wdb_theta* th, wdb_theta_info* info) {
     info->theta_max_abs = th->theta_max_abs;
     info->phase_table_len = th->lay.tab_len;
     info->build_ms = th->build_ms;
+    info->plan_tuned = th->tuned;
+    for (int op = 0; op < 2; ++op) {
+        info->plan_items[op] = (int)th->tplan[op][0].items.size();
+        info->plan_split_tiles[op] = th->tplan[op][0].n_split;
+    }
     return WDB_OK;
+}
+
+wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, void* stream) {
+    if (!th) return set_error(WDB_EINVAL, "NULL handle");
+    if (smem_budget > 98304) return set_error(WDB_EINVAL, "smem_budget %d > 98304", smem_budget);
+    return theta_replan(th, smem_budget > 0 ? smem_budget : 32768, cap_share > 0.0 ? cap_share : 2.0,
+                        split_share > 0.0 ? split_share : 0.0, static_cast<cudaStream_t>(stream));
 }
 
 wdb_status wdb_theta_export_taps(const wdb_theta* th, long long cap, int* a, int* b, int* oy, int* ox, double* v) {

@@ -294,6 +294,18 @@ wdb_status temp_plan(const wdb_theta* th, const TilePlanHost& h, TempPlan& d, cu
     WDB_TRY(temp_copy(d, h.tap_v, &p.tap_v, st));
     WDB_TRY(temp_copy(d, h.tap_v64, &p.tap_v64, st));
     WDB_TRY(temp_copy(d, h.tap_ov, &p.tap_ov, st));
+    if (h.n_split > 0) {   // split tiles: zeroed arrival counters and the partial sums
+        void* c = nullptr;
+        void* b = nullptr;
+        WDB_CK(cudaMalloc(&c, sizeof(unsigned int) * h.n_split));
+        d.bufs.push_back(c);
+        WDB_CK(cudaMemsetAsync(c, 0, sizeof(unsigned int) * h.n_split, st));
+        WDB_CK(cudaMalloc(&b, (size_t)h.esize * h.split_elems));
+        d.bufs.push_back(b);
+        p.split_ctr = static_cast<unsigned int*>(c);
+        p.split_buf = b;
+        WDB_TRY(temp_copy(d, h.split_base, &p.split_base, st));
+    }
     p.n_items = (int)h.items.size();
     p.buf_elems = h.buf_elems;
     p.smem_bytes = h.smem_bytes;
@@ -385,6 +397,11 @@ static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
         for (int budget : {kTileSmemBudget * 3 / 4, kTileSmemBudget, kTileSmemBudget * 3 / 2})
             for (double cap : {1.0, 2.0, 4.0})
                 whole.push_back(make_tile_plan(L, th->tent[op], 4, budget, th->plan_ctas, nullptr, 0, cap));
+        // the same with the heaviest tiles split over several CTAs
+        for (double split : {0.5, 1.0})
+            whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, &best, 0, 2.0, split));
+        for (double cap : {2.0, 4.0})
+            whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, cap, 1.0));
         float best_ms = 1e30f;
         for (size_t k = 0; k < whole.size() && s == WDB_OK; ++k) {
             const float ms = time_plan(whole[k]);
@@ -414,6 +431,18 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
     WDB_TRY(upload(th, h.tap_v, const_cast<float**>(&a.plan.tap_v), st));
     WDB_TRY(upload(th, h.tap_v64, const_cast<double**>(&a.plan.tap_v64), st));
     WDB_TRY(upload(th, h.tap_ov, const_cast<TapOV**>(&a.plan.tap_ov), st));
+    a.plan.split_ctr = nullptr;
+    a.plan.split_base = nullptr;
+    a.plan.split_buf = nullptr;
+    if (h.n_split > 0) {   // split tiles: zeroed arrival counters and the partial sums
+        std::vector<unsigned int> zero(h.n_split, 0u);
+        WDB_TRY(upload(th, zero, &a.plan.split_ctr, st));
+        WDB_TRY(upload(th, h.split_base, const_cast<long long**>(&a.plan.split_base), st));
+        void* b = nullptr;
+        WDB_CK(cudaMalloc(&b, (size_t)h.esize * h.split_elems));
+        th->allocs.push_back(b);
+        a.plan.split_buf = b;
+    }
     a.plan.n_items = (int)h.items.size();
     a.plan.buf_elems = h.buf_elems;
     a.plan.smem_bytes = h.smem_bytes;
@@ -438,6 +467,20 @@ wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st) {
         WDB_TRY(upload_plan(th, th->bplan[op], th->bargs[op], st));
     }
     th->bplan_ok = true;
+    return WDB_OK;
+}
+
+// Planner plans in place of the FP32 plans (no autotuning); captured solve graphs hold the
+// old plans' arguments and are dropped.
+wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, cudaStream_t st) {
+    for (int op = 0; op < 2; ++op) {
+        th->tplan[op][0] =
+            make_tile_plan(th->lay, th->tent[op], 4, budget, th->plan_ctas, nullptr, 0, cap_share, split_share);
+        WDB_TRY(upload_plan(th, th->tplan[op][0], th->targs[op][0], st));
+    }
+    th->tuned = 0;
+    for (auto& e : th->engine) e.release();
+    WDB_CK(cudaStreamSynchronize(st));
     return WDB_OK;
 }
 

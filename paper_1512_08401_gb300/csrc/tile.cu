@@ -31,6 +31,7 @@ constexpr double kCostStage = 8.0;       // per staged input element (cp.async, 
 constexpr double kCostTapStage = 6.0;    // per staged tap (offset + value)
 constexpr double kCostMacGlobal = 60.0;  // per multiply-add gathered from global memory (latency bound)
 constexpr double kCostItem = 20000.0;    // per tile (scheduling, descriptors, barriers, epilogue)
+constexpr double kCostBatch = 6000.0;    // per batch (staging round trip, barriers)
 constexpr int kUpStagedLg = 3;           // up pairs with r <= 8 stage their phase tables
 
 int next_pow2(int v) {
@@ -112,8 +113,9 @@ double subband_cost(const SubbandDev& so, const std::vector<PairBuild*>& prs, in
 }  // namespace
 
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int budget, int ctas,
-                            const std::vector<TileTune>* tune, int level_only, double cap_share) {
+                            const std::vector<TileTune>* tune, int level_only, double cap_share, double split_share) {
     TilePlanHost plan;
+    plan.esize = esize;
     std::map<std::pair<int, int>, PairBuild> pairs;
     for (const TileEntry& e : entries) {
         PairBuild& p = pairs[{e.out, e.in}];
@@ -136,6 +138,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         double cost;
     };
     std::vector<ItemCost> items;
+    std::vector<std::vector<double>> sub_bcost(L.S);
     for (int o = 0; o < L.S; ++o)
         for (PairBuild* pb : by_out[o]) {
             if (!pb->up) {
@@ -253,6 +256,24 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             batch_regions.back() += need;
             batch_taps.back() += nt;
         }
+        // modelled cost of each batch for a full tile (splitting tiles at batch boundaries)
+        {
+            const double outs_full = (double)std::min(TS, so.rows) * std::min(TS, so.cols);
+            const double mac_smem = e4 ? 2.75 : 5.0;
+            std::vector<double>& bc = sub_bcost[o];
+            bc.assign(batch_regions.size(), kCostBatch);
+            for (size_t q = 0; q < order.size(); ++q) {
+                const PairBuild& pb = *by_out[o][order[q]];
+                const double macs = outs_full * pb.maxph;
+                double c = macs * kCostMacGlobal;
+                if (!global[order[q]]) {
+                    const Geometry g = geometry(pb, TS, esize, e4, vecf[order[q]]);
+                    const int nt = !pb.up ? (int)pb.taps.size() : (pb.lg <= kUpStagedLg ? pb.maxph << (2 * pb.lg) : 0);
+                    c = (double)g.RR * g.RC * kCostStage + macs * mac_smem + kCostTapStage * nt;
+                }
+                bc[batch_of[q]] += c;
+            }
+        }
         sub.batch_begin = (int)plan.batches.size();
         for (size_t bi = 0; bi < batch_regions.size(); ++bi) {
             TileBatch bt{};
@@ -366,9 +387,60 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 const double cost = best * outs;
                 plan.macs += (long long)(outs * taps_per_out);
                 if (level_only <= 0 || so.level == level_only)
-                    items.push_back({TileItem{o, a * TS, b * TS, sub.batch_begin, sub.batch_end, TS, sub.lgTS, sub.e4},
+                    items.push_back({TileItem{o, a * TS, b * TS, sub.batch_begin, sub.batch_end,
+                                              sub.lgTS | (sub.e4 << 8), 1 << 16, -1},
                                      cost});
             }
+    }
+    if (split_share > 0.0 && !items.empty()) {
+        // split the tiles that would dominate one CTA's share into parts of whole batches
+        double sum = 0.0;
+        for (const ItemCost& ic : items) sum += ic.cost;
+        const double thr = std::max(split_share * sum / std::max(1, ctas), 2.0 * kCostItem);
+        std::vector<ItemCost> out;
+        for (const ItemCost& ic : items) {
+            const TileItem& w = ic.it;
+            const int nb = w.batch_end - w.batch_begin;
+            const int np = std::min(nb, (int)std::ceil(ic.cost / thr));
+            if (np < 2) {
+                out.push_back(ic);
+                continue;
+            }
+            const SubbandDev& so = L.sb[w.o];
+            const int TS = w.TS();
+            const double f = (double)std::min(TS, so.rows - w.ty0) * std::min(TS, so.cols - w.tx0) /
+                             ((double)std::min(TS, so.rows) * std::min(TS, so.cols));
+            const std::vector<double>& bc = sub_bcost[w.o];
+            const int b0 = w.batch_begin - plan.subs[w.o].batch_begin;
+            double tot = 0.0;
+            for (int b = 0; b < nb; ++b) tot += bc[b0 + b];
+            // contiguous parts: cut where the running cost passes the next multiple of tot / np,
+            // leaving at least one batch for every later part
+            int begin = 0, part = 0;
+            double run = 0.0;
+            const int sid = plan.n_split++;
+            plan.split_base.push_back(plan.split_elems);
+            plan.split_elems += (long long)np * TS * TS;
+            for (int b = 0; b < nb; ++b) {
+                run += bc[b0 + b];
+                const bool last = b == nb - 1;
+                const bool cut = !last && part < np - 1 &&
+                                 (run >= tot * (part + 1) / np || nb - (b + 1) == np - (part + 1));
+                if (cut || last) {
+                    double c = kCostItem;
+                    for (int k = begin; k <= b; ++k) c += bc[b0 + k];
+                    TileItem pw = w;
+                    pw.batch_begin = w.batch_begin + begin;
+                    pw.batch_end = w.batch_begin + b + 1;
+                    pw.split = part | (np << 16);
+                    pw.sid = sid;
+                    out.push_back({pw, c * f});
+                    ++part;
+                    begin = b + 1;
+                }
+            }
+        }
+        items.swap(out);
     }
     std::stable_sort(items.begin(), items.end(), [](const ItemCost& x, const ItemCost& y) { return x.cost > y.cost; });
     for (auto& ic : items) {
@@ -614,9 +686,9 @@ struct ThreadMap {
 
 __device__ __forceinline__ ThreadMap thread_map(const TileItem& w) {
     ThreadMap tm;
-    const int t = threadIdx.x, TS = w.TS, lgTS = w.lgTS;
+    const int t = threadIdx.x, TS = w.TS(), lgTS = w.lgTS();
     tm.nout = TS * TS;
-    if (TS == 32 || (TS >= 8 && w.e4)) {
+    if (TS == 32 || (TS >= 8 && w.e4())) {
         tm.E = 4;
         tm.lgsx = lgTS - 2;
         tm.sx = 1 << tm.lgsx;
@@ -824,6 +896,41 @@ __device__ __forceinline__ void group_reduce(const ThreadMap& tm, T (&acc)[4], T
     }
 }
 
+// Split tile (w.nparts() > 1): store this part's sums (threads of group 0), count the part as
+// finished, and let the last part to finish sum all parts' sums in part order (the result
+// does not depend on which part finishes last). Returns true in the CTA that runs the
+// epilogue; every thread of the CTA calls it.
+template <typename T>
+__device__ __forceinline__ bool combine_parts(const TilePlanDev& plan, const TileItem& w, const ThreadMap& tm,
+                                              T (&acc)[4]) {
+    __shared__ int s_last;
+    T* const buf = static_cast<T*>(plan.split_buf) + plan.split_base[w.sid];
+    const int nout = tm.nout, np = w.nparts();
+    const int q0 = (tm.ly << w.lgTS()) + tm.lx;
+    if (tm.g == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (e < tm.E) buf[w.part() * nout + q0 + tm.sx * e] = acc[e];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(plan.split_ctr + w.sid, 1u) == (unsigned)(np - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    if (tm.g == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (e >= tm.E) continue;
+            T a = 0;
+            for (int p = 0; p < np; ++p) a += __ldcg(buf + p * nout + q0 + tm.sx * e);
+            acc[e] = a;
+        }
+    }
+    if (threadIdx.x == 0) plan.split_ctr[w.sid] = 0u;   // ready for the next launch
+    return true;
+}
+
 // Per-thread partial sums of the epilogues.
 struct Partials {
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, mx = 0.f;
@@ -937,7 +1044,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc);
         if (bi + 1 == w.batch_end) {
             group_reduce<T>(tm, acc, red_buf);
-            epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
+            if (w.split < (2 << 16) || combine_parts<T>(plan, w, tm, acc))
+                epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[e] = 0;
         }

@@ -63,11 +63,34 @@ struct alignas(16) TileBatch {    // pairs [pair_begin, pair_end) of one subband
     int pad[2];
 };
 
-struct alignas(16) TileItem {     // one tile; carries what the kernel needs without further lookups
+struct alignas(16) TileItem {     // one tile (or one part of it); carries what the kernel needs
     int o;
     int ty0, tx0;
-    int batch_begin, batch_end;   // the subband's batches
-    int TS, lgTS, e4;             // the subband's tile side and thread map
+    int batch_begin, batch_end;   // batches of the subband this item accumulates
+    int geo;                      // the subband's tile side and thread map: lgTS | e4 << 8
+    int split;                    // part | nparts << 16 (nparts > 1: the tile's batches are split
+                                  // over nparts items)
+    int sid;                      // split tiles: index of the arrival counter and partial sums
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    int lgTS() const { return geo & 0xff; }
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    int TS() const { return 1 << (geo & 0xff); }
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    int e4() const { return geo >> 8; }
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    int part() const { return split & 0xffff; }
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    int nparts() const { return split >> 16; }
 };
 
 // One FP32 tap as the kernel reads it: offset and value in one 8-byte load.
@@ -97,6 +120,9 @@ struct TilePlanDev {
     const float* tap_v;
     const double* tap_v64;
     const TapOV* tap_ov;      // (tap_off, tap_v) interleaved: the FP32 kernels' tap records
+    unsigned int* split_ctr;  // per split tile: parts finished (zero between launches)
+    const long long* split_base;   // per split tile: first element of its partial sums
+    void* split_buf;          // per split tile: nparts x TS^2 partial sums (element type of the plan)
     int n_items;
     int buf_elems;            // elements of one staging buffer (two buffers per CTA)
     int smem_bytes;           // dynamic shared memory per CTA
@@ -114,6 +140,10 @@ struct TilePlanHost {
     std::vector<double> tap_v64;
     std::vector<TapOV> tap_ov;
     std::vector<double> item_cost;   // estimated cost of every item (items are sorted by it)
+    int esize = 4;                   // element size (4: FP32, 8: FP64)
+    int n_split = 0;                 // split tiles
+    std::vector<long long> split_base;   // first partial-sum element of each split tile
+    long long split_elems = 0;       // partial-sum elements of all split tiles
     int buf_elems = 0;
     int smem_bytes = 0;
     long long macs = 0;        // MACs per application (taps x outputs, padding included)
@@ -126,10 +156,13 @@ struct TileEntry {             // one tap of one pair, in gather form
 
 // Build the plan of one operator for element size `esize` and a per-buffer shared-memory
 // budget (a batch of staged regions shares one buffer; a CTA holds two buffers); `ctas` is
-// the number of CTAs that will share the tiles (it caps the cost of one tile).
+// the number of CTAs that will share the tiles (it caps the cost of one tile). split_share >
+// 0: a tile of several batches whose modelled cost exceeds split_share times one CTA's share
+// is split at batch boundaries into parts that different CTAs run concurrently; the last
+// part to finish sums the parts' partial sums in part order and runs the epilogue.
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget,
                             int ctas = 456, const std::vector<TileTune>* tune = nullptr, int level_only = 0,
-                            double cap_share = 2.0);
+                            double cap_share = 2.0, double split_share = 0.0);
 
 struct TileQueue {             // device counters of one operator launch
     unsigned int next;         // next work item

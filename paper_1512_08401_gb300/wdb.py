@@ -34,7 +34,8 @@ class ThetaInfo(C.Structure):
     _fields_ = [("n_rows", C.c_int), ("n_cols", C.c_int), ("levels", C.c_int), ("n_subbands", C.c_int),
                 ("wavelet_taps", C.c_int), ("rule", C.c_int), ("K_requested", C.c_longlong),
                 ("K_eff", C.c_longlong), ("n_taps", C.c_longlong), ("n_candidates", C.c_longlong),
-                ("theta_max_abs", C.c_double), ("phase_table_len", C.c_int), ("build_ms", C.c_double)]
+                ("theta_max_abs", C.c_double), ("phase_table_len", C.c_int), ("build_ms", C.c_double),
+                ("plan_tuned", C.c_int), ("plan_items", C.c_int * 2), ("plan_split_tiles", C.c_int * 2)]
 
 
 class SolveParams(C.Structure):
@@ -70,6 +71,7 @@ _SIGS = {
     "wdb_theta_load": (i32, [C.c_char_p, vp, C.POINTER(vp)]),
     "wdb_theta_free": (None, [vp]),
     "wdb_theta_apply": (i32, [vp, vp, vp, i32, vp]),
+    "wdb_theta_replan": (i32, [vp, i32, f64, f64, vp]),
     "wdb_solve": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_solve_coeffs": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_theta_objective": (i32, [vp, vp, vp, f64, pd, vp, pd]),
@@ -252,6 +254,11 @@ class Theta:
 
     def save(self, path):
         _check(lib().wdb_theta_save(self._h, path.encode()))
+
+    def replan(self, smem_budget=0, cap_share=0.0, split_share=0.0, stream=None):
+        """Planner plans for the FP32 kernels in place of the autotuned ones (wdb_theta_replan)."""
+        _check(lib().wdb_theta_replan(self._h, int(smem_budget), float(cap_share), float(split_share),
+                                      _stream(stream)))
 
     def apply(self, x, out, transpose=False, stream=None):
         _check(lib().wdb_theta_apply(self._h, _dev(x, self.N), _dev(out, self.N), 1 if transpose else 0,

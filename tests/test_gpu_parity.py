@@ -158,6 +158,58 @@ def test_apply_parity(wdb, name):
     assert rel_max(host(out), case.th.matT @ y) < 2e-6
 
 
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("budget,cap,split", [(32768, 2.0, 0.25), (8192, 1.0, 0.05), (98304, 4.0, 0.0)])
+def test_planner_plans_and_split_tiles_match_oracle(wdb, name, budget, cap, split):
+    """Planner plans in place of the autotuned ones, with the heaviest tiles split at batch
+    boundaries over several CTAs (the last part to finish adds the parts' partial sums in
+    part order): the same operator, and run-to-run identical results."""
+    psf, nr, nc, J = CASES[name]
+    rng = np.random.default_rng(15)
+    case = build_case(psf, nr, nc, J, 30 * nr * nc, rng.standard_normal((nr, nc)))
+    g = gpu_from_oracle(wdb, case, nr, nc, J)
+    g.replan(budget, cap, split)
+    info = g.info
+    assert info.plan_tuned == 0
+    if split == 0.0:
+        assert list(info.plan_split_tiles) == [0, 0]
+    if budget == 8192:
+        assert sum(info.plan_split_tiles) > 0   # small buffers: several batches per tile
+    y = rng.standard_normal(nr * nc)
+    out = torch.zeros(nr * nc, device="cuda")
+    again = torch.zeros(nr * nc, device="cuda")
+    for tr, ref in ((False, case.th.mat @ y), (True, case.th.matT @ y)):
+        g.apply(dev(y), out, transpose=tr)
+        assert rel_max(host(out), ref) < 2e-6
+        g.apply(dev(y), again, transpose=tr)
+        assert torch.equal(out, again)
+    with pytest.raises(wdb.WdbError):
+        g.replan(98305, 2.0, 0.0)
+
+
+def test_split_tiles_fista_trajectory_parity(wdb):
+    """Kernels 1 and 2 over plans with split tiles: the FISTA trajectory of the oracle, and
+    the same iterate from a solve without graphs."""
+    prob = synthetic.small_problem()
+    n, J, lam, kind = 128, 4, prob.lam, "spai"
+    case = build_case(prob.psf, n, n, J, 30 * n * n, prob.u0)
+    Ptab, P, tau, _ = precond_and_step(case, kind)
+    ref = fista(case, lam, P, tau, 120)
+    g = gpu_from_oracle(wdb, case, n, n, J)
+    g.set_precond(kind, Ptab, tau)
+    g.replan(8192, 1.0, 0.05)
+    assert min(g.info.plan_split_tiles) > 0
+    x = torch.zeros(n * n, device="cuda")
+    r = g.solve_coeffs(dev(case.x0), x, lam=lam, max_iters=120, tol=0.0, precond=kind)
+    assert r["iters"] == 120
+    xg = host(x)
+    assert np.linalg.norm(xg - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    assert abs(r["objective"] - ref.objective) <= 1e-5 * ref.objective
+    x2 = torch.zeros(n * n, device="cuda")
+    g.solve_coeffs(dev(case.x0), x2, lam=lam, max_iters=120, tol=0.0, precond=kind, no_graph=True)
+    assert torch.equal(x, x2)
+
+
 @pytest.mark.parametrize("kind", ["none", "jacobi", "spai"])
 def test_precond_and_step_parity(wdb, kind):
     psf, nr, nc, J = CASES["motion64"]
