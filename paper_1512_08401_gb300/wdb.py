@@ -259,6 +259,7 @@ class Theta:
         """Planner plans for the FP32 kernels in place of the autotuned ones (wdb_theta_replan)."""
         _check(lib().wdb_theta_replan(self._h, int(smem_budget), float(cap_share), float(split_share),
                                       _stream(stream)))
+        self.info = self._info()
 
     def apply(self, x, out, transpose=False, stream=None):
         _check(lib().wdb_theta_apply(self._h, _dev(x, self.N), _dev(out, self.N), 1 if transpose else 0,
