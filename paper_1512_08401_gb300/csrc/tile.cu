@@ -986,7 +986,9 @@ __device__ __forceinline__ void epilogue(const TileItem& w, const SubbandDev& so
 // ---------------------------------------------------------------------------------------
 // Single problem: persistent CTAs, heaviest tiles first, (tile, batch) double buffering
 // ---------------------------------------------------------------------------------------
-template <typename T, int EPI>
+// SPLIT: the plan has split tiles (a separate instance, so that plans without them run code
+// that carries none of the combining step)
+template <typename T, int EPI, bool SPLIT>
 __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const T* __restrict__ in,
                                                             T* __restrict__ out, EpiArgs ep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1044,7 +1046,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc);
         if (bi + 1 == w.batch_end) {
             group_reduce<T>(tm, acc, red_buf);
-            if (w.split < (2 << 16) || combine_parts<T>(plan, w, tm, acc))
+            if (!SPLIT || w.split < (2 << 16) || combine_parts<T>(plan, w, tm, acc))
                 epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[e] = 0;
@@ -1256,11 +1258,12 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
 
 // pdl: programmatic dependent launch, so that this grid's CTAs are scheduled while the
 // previous kernel of the stream drains (the kernel waits for that grid before its work)
-template <typename T, int EPI>
-wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl = false) {
+template <typename T, int EPI, bool SPLIT>
+wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl) {
     static bool attr = false;
     if (!attr) {
-        WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
         attr = true;
     }
     if (pdl) {
@@ -1274,13 +1277,20 @@ wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        WDB_CK(cudaLaunchKernelEx(&cfg, tile_kernel<T, EPI>, A, in, out, ep));
+        WDB_CK(cudaLaunchKernelEx(&cfg, tile_kernel<T, EPI, SPLIT>, A, in, out, ep));
     } else {
-        tile_kernel<T, EPI><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
+        tile_kernel<T, EPI, SPLIT><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
     }
     count_launch();
     WDB_CK(cudaGetLastError());
     return WDB_OK;
+}
+
+// Plans with split tiles (FP32 only) run the instance with the combining step.
+template <typename T, int EPI>
+wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl = false) {
+    if (sizeof(T) == 4 && A.plan.split_ctr) return launch_tile_as<T, EPI, sizeof(T) == 4>(A, in, out, ep, st, pdl);
+    return launch_tile_as<T, EPI, false>(A, in, out, ep, st, pdl);
 }
 
 template <int EPI>
@@ -1302,8 +1312,8 @@ int tile_grid(int smem_bytes) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(tile_kernel<float, kK2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2>, kTileThreads, smem_bytes);
+    cudaFuncSetAttribute(tile_kernel<float, kK2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2, false>, kTileThreads, smem_bytes);
     if (sms <= 0) sms = 1;
     if (per <= 0) per = 1;
     return sms * per;
