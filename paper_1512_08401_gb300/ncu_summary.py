@@ -25,7 +25,8 @@ from collections import defaultdict
 
 CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
 TILE_SOURCES = ["tile.cu", "tile.cuh", "device_util.cuh", "layout_types.h", "wdb_internal.h"]
-FISTA_KERNELS = {"k1_residual": "tile_kernel<float, 2>", "k2_step": "tile_kernel<float, 3>"}
+# name prefixes of the two FISTA kernels (tile_kernel<float, EPI[, SPLIT]>)
+FISTA_KERNELS = {"k1_residual": "tile_kernel<float, 2", "k2_step": "tile_kernel<float, 3"}
 
 
 def kernel_sources_sha256(files) -> str:
@@ -75,8 +76,8 @@ def summarise(path: str) -> str:
 
 
 def _kernel_label(name: str) -> str:
-    n = name.replace("(int)", "")
-    n = re.sub(r"wdb::(\(anonymous namespace\)|_GLOBAL__N__\w+)::", "", n)
+    n = name.replace("(int)", "").replace("(bool)", "")
+    n = re.sub(r"(wdb::)?(\(anonymous namespace\)|_GLOBAL__N__\w+|unnamed>)::", "", n)
     return short(n)
 
 
@@ -114,8 +115,8 @@ def fista_dram(path: str) -> dict:
     for (lid, kname), d in sorted(per.items()):
         label = _kernel_label(kname)
         for key, want in FISTA_KERNELS.items():
-            if key not in out and label.endswith(want):
-                out[key] = d
+            if key not in out and re.search(re.escape(want) + r"[,>]", label):
+                out[key] = dict(d, kernel=label)
     return out
 
 
@@ -130,7 +131,7 @@ def write_traffic(csv_path: str, workload: str, profile: str, record: str) -> di
     ent = rec.setdefault(workload, {})
     for key, d in got.items():
         rd, wr = d.get("dram__bytes_read.sum", 0.0), d.get("dram__bytes_write.sum", 0.0)
-        ent[key] = {"kernel": FISTA_KERNELS[key], "dram_bytes_per_launch": int(round(rd + wr)),
+        ent[key] = {"kernel": d["kernel"], "dram_bytes_per_launch": int(round(rd + wr)),
                     "dram_read": int(round(rd)), "dram_write": int(round(wr)),
                     "duration_us_under_ncu": round(d.get("gpu__time_duration.sum", 0.0), 2),
                     "sources": TILE_SOURCES, "sources_sha256": sha, "profile": profile}
