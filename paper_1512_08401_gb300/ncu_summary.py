@@ -39,7 +39,9 @@ def kernel_sources_sha256(files) -> str:
 
 
 def short(name: str) -> str:
-    n = re.sub(r"\(.*", "", name)
+    # template casts and anonymous namespaces first, then the parameter list
+    n = re.sub(r"\((unsigned )?(int|bool|long|char)\)|\(anonymous namespace\)::", "", name)
+    n = re.sub(r"\(.*", "", n)
     n = re.sub(r"^void ", "", n)
     n = re.sub(r"wdb::(\(anonymous namespace\)|_GLOBAL__N__\w+)::", "", n)
     return n[:90]
