@@ -18,9 +18,11 @@ namespace {
 
 constexpr int kTile = 16;  // outputs per tile side (per subband)
 
+// v mod n for v within a few periods of [0, n) (tile origins plus a halo): no division
 __device__ __forceinline__ int wrapi(int v, int n) {
-    v %= n;
-    return v < 0 ? v + n : v;
+    while (v < 0) v += n;
+    while (v >= n) v -= n;
+    return v;
 }
 
 template <typename T>
@@ -45,10 +47,15 @@ __global__ void __launch_bounds__(256) dwt_level_kernel(const T* __restrict__ in
     T* s_hi = s_lo + IY * kTile;
     const int oy0 = blockIdx.y * kTile, ox0 = blockIdx.x * kTile;
     const int R2 = R >> 1, C2 = C >> 1;
-    for (int t = threadIdx.x; t < IY * IX; t += blockDim.x) {
-        int iy = t / IX, ix = t - iy * IX;
-        int gy = wrapi(2 * oy0 + iy, R), gx = wrapi(2 * ox0 + ix, C);
-        s_in[t] = in[(size_t)gy * C + gx];
+    // one warp per input row, lanes along the row (coalesced), wrap per row and per lane
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const int gx0 = wrapi(2 * ox0 + lane, C), gx1 = wrapi(2 * ox0 + lane + 32, C);
+        for (int iy = warp; iy < IY; iy += nw) {
+            const T* __restrict__ row = in + (size_t)wrapi(2 * oy0 + iy, R) * C;
+            if (lane < IX) s_in[iy * IX + lane] = row[gx0];
+            if (lane + 32 < IX) s_in[iy * IX + lane + 32] = row[gx1];
+        }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < IY * kTile; t += blockDim.x) {
@@ -111,18 +118,31 @@ __global__ void __launch_bounds__(256) idwt_level_kernel(const T* __restrict__ c
     T* sHx = sLx + OY * CX;
     const int cy0 = blockIdx.y * kTile, cx0 = blockIdx.x * kTile;
     const int by = cy0 - H2 + 1, bx = cx0 - H2 + 1;
-    for (int t = threadIdx.x; t < CY * CX; t += blockDim.x) {
-        int iy = t / CX, ix = t - iy * CX;
-        size_t g = (size_t)wrapi(by + iy, R2) * C2 + wrapi(bx + ix, C2);
-        sLL[t] = cA[g];
-        sLH[t] = c01[g];
-        sHL[t] = c10[g];
-        sHH[t] = c11[g];
+    // one warp per coefficient row, lanes along the row (CX <= 32 + H2 - 1 < 64)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    {
+        const int gx0 = wrapi(bx + lane, C2), gx1 = wrapi(bx + lane + 32, C2);
+        for (int iy = warp; iy < CY; iy += nw) {
+            const size_t r = (size_t)wrapi(by + iy, R2) * C2;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int ix = lane + 32 * h;
+                if (ix >= CX) break;
+                const size_t g = r + (h ? gx1 : gx0);
+                const int t = iy * CX + ix;
+                sLL[t] = cA[g];
+                sLH[t] = c01[g];
+                sHL[t] = c10[g];
+                sHH[t] = c11[g];
+            }
+        }
     }
     __syncthreads();
-    // synthesis along y: Lx from (LL, HL), Hx from (LH, HH)
+    // synthesis along y: Lx from (LL, HL), Hx from (LH, HH); t / CX through a multiply-high
+    // by ceil(2^32 / CX) (exact for t < 2^16)
+    const unsigned mCX = 0xffffffffu / (unsigned)CX + 1u;
     for (int t = threadIdx.x; t < OY * CX; t += blockDim.x) {
-        int yl = t / CX, cx = t - yl * CX;
+        const int yl = (int)__umulhi((unsigned)t, mCX), cx = t - yl * CX;
         T lx = 0, hx = 0;
         for (int k = (yl & 1); k < L; k += 2) {
             int ci = ((yl - k) >> 1) + H2 - 1;   // (yl - k) even
@@ -130,8 +150,8 @@ __global__ void __launch_bounds__(256) idwt_level_kernel(const T* __restrict__ c
             lx += sh[k] * sLL[s] + sg[k] * sHL[s];
             hx += sh[k] * sLH[s] + sg[k] * sHH[s];
         }
-        sLx[t] = lx;
-        sHx[t] = hx;
+        sLx[yl * CX + cx] = lx;
+        sHx[yl * CX + cx] = hx;
     }
     __syncthreads();
     const int R = 2 * R2, C = 2 * C2;
