@@ -452,7 +452,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
     plan.pair_sm.resize(plan.pairs.size());
     for (size_t k = 0; k < plan.pairs.size(); ++k) {
         const SubbandDev& si = L.sb[plan.pairs[k].in_sb];
-        plan.pair_sm[k] = PairSm{plan.pairs[k], si.off, si.rows, si.cols, 0, {0, 0, 0}};
+        plan.pair_sm[k] = PairSm{plan.pairs[k], si.off, si.rows, si.cols, 0, 0, 0, 0};
     }
     plan.buf_elems = std::max(max_bytes, 16) / esize;
     plan.smem_bytes = 2 * plan.buf_elems * esize;
@@ -578,10 +578,16 @@ __device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const T* __
     const unsigned S0 = smem_addr(S);
     const int np = bt.pair_end - bt.pair_begin;
     if ((int)threadIdx.x < np) {
+        // this tile's region origin, wrapped once here for every warp that stages the pair;
+        // vec pairs start at staged column (first column mod 4)
         PairSm e = plan.pair_sm[bt.pair_begin + threadIdx.x];
-        if (e.p.vec) {   // this tile's region starts at staged column (first column mod 4)
-            const int X0 = (e.p.mode == kDown) ? ((w.tx0 << e.p.lg) + e.p.x0) : ((w.tx0 >> e.p.lg) + e.p.x0);
-            e.shift = pos_mod(X0, e.in_cols) & 3;
+        const bool dn = e.p.mode == kDown || e.p.mode == kDownGlobal;
+        const int Y0 = dn ? ((w.ty0 << e.p.lg) + e.p.y0) : ((w.ty0 >> e.p.lg) + e.p.y0);
+        const int X0 = dn ? ((w.tx0 << e.p.lg) + e.p.x0) : ((w.tx0 >> e.p.lg) + e.p.x0);
+        if (e.p.mode == kDown || e.p.mode == kUp) {
+            e.yb = pos_mod(Y0, e.in_rows);
+            e.xb = pos_mod(X0, e.in_cols);
+            if (e.p.vec) e.shift = e.xb & 3;
         }
         tab[threadIdx.x] = e;
     }
@@ -595,9 +601,7 @@ __device__ __forceinline__ void stage_batch(const TilePlanDev& plan, const T* __
         const T* __restrict__ src = in + si.off;
         const int lg = P.lg, m = (1 << lg) - 1;
         const bool down = P.mode == kDown;
-        const int Y0 = down ? ((w.ty0 << lg) + P.y0) : ((w.ty0 >> lg) + P.y0);
-        const int X0 = down ? ((w.tx0 << lg) + P.x0) : ((w.tx0 >> lg) + P.x0);
-        const int yb = pos_mod(Y0, si.rows), xb = pos_mod(X0, si.cols);
+        const int yb = tab[i].yb, xb = tab[i].xb;
         const int plane = P.PS;
         const unsigned base = S0 + (unsigned)P.soff * ES;
         if (P.vec) {

@@ -106,7 +106,8 @@ struct alignas(16) PairSm {
     long long in_off;
     int in_rows, in_cols;
     int shift;        // vec pairs: staged column of the region's first column (0..3), set per tile
-    int pad[3];
+    int yb, xb;       // staged pairs: the region's first input row and column (wrapped), set per tile
+    int pad;
 };
 
 struct TilePlanDev {
