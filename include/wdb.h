@@ -74,6 +74,7 @@ typedef struct {
     int plan_tuned;             /* 1: the FP32 kernels' plans were autotuned on this GPU */
     int plan_items[2];          /* work items of the FP32 plans of Theta_K and Theta_K^T */
     int plan_split_tiles[2];    /* tiles of those plans split over several CTAs */
+    int plan_super_subbands[2]; /* subbands of those plans worked in 2 x 2 super tiles */
 } wdb_theta_info;
 
 /* Parameters of one solve. Zero-initialise and set what you need. */
@@ -156,12 +157,15 @@ wdb_status wdb_theta_set_precond(wdb_theta* th, int precond, const double* P_hos
 /* Replace the plans of the FP32 Theta_K / Theta_K^T kernels (autotuned on the GPU by
  * wdb_build_theta and wdb_theta_from_taps) by the planner's plans for a staging buffer of
  * smem_budget bytes (<= 0: 32768; at most 98304), tiles whose modelled cost stays under
- * cap_share CTA shares (<= 0: 2), and tiles above split_share CTA shares split at batch
- * boundaries over several CTAs (<= 0: none), whose partial sums the last part to finish adds
- * in part order. Results change only by the FP32 summation order. Captured solve graphs of
- * the handle are dropped; the replaced plans' device memory is released with the handle.
- * WDB_EINVAL for a NULL handle or smem_budget > 98304. Synchronises `stream`. */
-wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, void* stream);
+ * cap_share CTA shares (<= 0: 2), and either tiles above split_share CTA shares split at
+ * batch boundaries over several CTAs (<= 0: none), whose partial sums the last part to
+ * finish adds in part order, or (super_tiles != 0) work items of 2 x 2 tiles of side 32
+ * staged together wherever all their regions fit one buffer. Results change only by the
+ * FP32 summation order. Captured solve graphs of the handle are dropped; the replaced plans'
+ * device memory is released with the handle. WDB_EINVAL for a NULL handle, smem_budget >
+ * 98304, or split_share > 0 together with super_tiles. Synchronises `stream`. */
+wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, int super_tiles,
+                            void* stream);
 
 /* Serialise / restore a handle (taps, layout, wavelet; preconditioners are recomputed). */
 wdb_status wdb_theta_save(const wdb_theta* th, const char* path);

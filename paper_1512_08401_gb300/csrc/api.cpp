@@ -175,15 +175,18 @@ wdb_status wdb_theta_info_get(const wdb_theta* th, wdb_theta_info* info) {
     for (int op = 0; op < 2; ++op) {
         info->plan_items[op] = (int)th->tplan[op][0].items.size();
         info->plan_split_tiles[op] = th->tplan[op][0].n_split;
+        info->plan_super_subbands[op] = th->tplan[op][0].n_sup;
     }
     return WDB_OK;
 }
 
-wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, void* stream) {
+wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, int super_tiles,
+                            void* stream) {
     if (!th) return set_error(WDB_EINVAL, "NULL handle");
     if (smem_budget > 98304) return set_error(WDB_EINVAL, "smem_budget %d > 98304", smem_budget);
+    if (super_tiles && split_share > 0.0) return set_error(WDB_EINVAL, "split tiles and super tiles together");
     return theta_replan(th, smem_budget > 0 ? smem_budget : 32768, cap_share > 0.0 ? cap_share : 2.0,
-                        split_share > 0.0 ? split_share : 0.0, static_cast<cudaStream_t>(stream));
+                        split_share > 0.0 ? split_share : 0.0, super_tiles != 0, static_cast<cudaStream_t>(stream));
 }
 
 wdb_status wdb_theta_export_taps(const wdb_theta* th, long long cap, int* a, int* b, int* oy, int* ox, double* v) {

@@ -307,6 +307,7 @@ wdb_status temp_plan(const wdb_theta* th, const TilePlanHost& h, TempPlan& d, cu
         WDB_TRY(temp_copy(d, h.split_base, &p.split_base, st));
     }
     p.n_items = (int)h.items.size();
+    p.n_sup = h.n_sup;
     p.buf_elems = h.buf_elems;
     p.smem_bytes = h.smem_bytes;
     d.a.sb = th->d_sb;
@@ -353,7 +354,9 @@ static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
         }
         for (int rep = 0; rep < 4 && s == WDB_OK; ++rep) {
             if (cudaEventRecord(e0, st) != cudaSuccess) fail(set_error(WDB_ECUDA, "event"));
-            r = tile_apply<float>(d.a, in, out, nullptr, nullptr, part, st);
+            // timed with kernel 1's epilogue (read x0, write r, reduce ||r||^2), so that plans
+            // are ranked with a solve's per-output loads and stores
+            r = tile_resnorm(d.a, in, in, out, part + 2 * 8192 - 1, part, st);
             if (r != WDB_OK) fail(r);
             if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
                 fail(set_error(WDB_ECUDA, "autotune timing"));
@@ -402,6 +405,12 @@ static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
             whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, &best, 0, 2.0, split));
         for (double cap : {2.0, 4.0})
             whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, cap, 1.0));
+        // and with super tiles (2 x 2 tiles staged together) where they fit one buffer
+        for (int budget : {kTileSmemBudget, kTileSmemBudget * 3 / 2})
+            whole.push_back(make_tile_plan(L, th->tent[op], 4, budget, th->plan_ctas, &best, 0, 2.0, 0.0, true));
+        for (double cap : {2.0, 4.0})
+            whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, cap, 0.0,
+                                           true));
         float best_ms = 1e30f;
         for (size_t k = 0; k < whole.size() && s == WDB_OK; ++k) {
             const float ms = time_plan(whole[k]);
@@ -444,6 +453,7 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
         a.plan.split_buf = b;
     }
     a.plan.n_items = (int)h.items.size();
+    a.plan.n_sup = h.n_sup;
     a.plan.buf_elems = h.buf_elems;
     a.plan.smem_bytes = h.smem_bytes;
     a.sb = th->d_sb;
@@ -472,10 +482,11 @@ wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st) {
 
 // Planner plans in place of the FP32 plans (no autotuning); captured solve graphs hold the
 // old plans' arguments and are dropped.
-wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, cudaStream_t st) {
+wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, bool super_tiles,
+                        cudaStream_t st) {
     for (int op = 0; op < 2; ++op) {
-        th->tplan[op][0] =
-            make_tile_plan(th->lay, th->tent[op], 4, budget, th->plan_ctas, nullptr, 0, cap_share, split_share);
+        th->tplan[op][0] = make_tile_plan(th->lay, th->tent[op], 4, budget, th->plan_ctas, nullptr, 0, cap_share,
+                                          split_share, super_tiles);
         WDB_TRY(upload_plan(th, th->tplan[op][0], th->targs[op][0], st));
     }
     th->tuned = 0;

@@ -64,14 +64,17 @@ bool vec_pair(const PairBuild& p, const Layout& L, int TS, bool e4, int esize) {
     return esize == 4 && e4 && TS >= 16 && (p.up || p.lg == 0) && si.cols % 4 == 0 && si.off % 4 == 0;
 }
 
-Geometry geometry(const PairBuild& p, int TS, int esize, bool e4, bool vec = false) {
+// Region of pair p for a staged tile of side TS; the row pitch suits the thread map of tiles
+// of side pts (<= 0: TS; super tiles stage 2 x 2 tiles of side pts = TS / 2 together).
+Geometry geometry(const PairBuild& p, int TS, int esize, bool e4, bool vec = false, int pts = 0) {
     Geometry g;
     const int r = 1 << p.lg;
+    const int PT = pts > 0 ? pts : TS;
     if (!p.up) {
         g.RR = r * (TS - 1) + (p.dy1 - p.dy0) + 1;
         g.RC = r * (TS - 1) + (p.dx1 - p.dx0) + 1;
         g.PR = (g.RR + r - 1) / r;
-        g.PC = pitch(vec ? (g.RC + 6) & ~3 : (g.RC + r - 1) / r, TS, e4);
+        g.PC = pitch(vec ? (g.RC + 6) & ~3 : (g.RC + r - 1) / r, PT, e4);
         g.PS = g.PR * g.PC;
         g.bytes = (long long)r * r * g.PS * esize;
     } else {
@@ -79,7 +82,7 @@ Geometry geometry(const PairBuild& p, int TS, int esize, bool e4, bool vec = fal
         g.RR = rows + (p.dy1 - p.dy0);
         g.RC = rows + (p.dx1 - p.dx0);
         g.PR = g.RR;
-        g.PC = pitch(vec ? (g.RC + 6) & ~3 : g.RC, TS, e4);
+        g.PC = pitch(vec ? (g.RC + 6) & ~3 : g.RC, PT, e4);
         g.PS = g.PR * g.PC;
         g.bytes = (long long)g.PR * g.PC * esize;
     }
@@ -113,7 +116,9 @@ double subband_cost(const SubbandDev& so, const std::vector<PairBuild*>& prs, in
 }  // namespace
 
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int budget, int ctas,
-                            const std::vector<TileTune>* tune, int level_only, double cap_share, double split_share) {
+                            const std::vector<TileTune>* tune, int level_only, double cap_share, double split_share,
+                            bool super_tiles) {
+    if (super_tiles) split_share = 0.0;   // a plan has split tiles or super tiles, not both
     TilePlanHost plan;
     plan.esize = esize;
     std::map<std::pair<int, int>, PairBuild> pairs;
@@ -201,6 +206,27 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         for (int k = 0; k < np; ++k)
             vecf[k] = !global[k] && vec_pair(*by_out[o][k], L, TS, e4, esize) &&
                       geometry(*by_out[o][k], TS, esize, e4, true).bytes <= budget;
+        // super tiles: 2 x 2 tiles of side 32 staged together in one batch (every pair staged,
+        // all regions in one buffer) and computed one after the other, so that the set-up of
+        // a work item and of its pairs' staging serves four tiles
+        int ST = TS;   // side of the staged tile
+        bool sup = false;
+        if (super_tiles && TS == 32 && e4 && so.rows >= 64 && so.cols >= 64 && np <= kMaxBatchPairs) {
+            bool ok = true;
+            long long regs = 0, ntaps = 0;
+            for (int k = 0; k < np && ok; ++k) {
+                const PairBuild& pb = *by_out[o][k];
+                if (global[k]) ok = false;
+                const Geometry g = geometry(pb, 64, esize, e4, vecf[k], 32);
+                regs += (g.bytes + 15) / 16 * 16 / esize;
+                ntaps += !pb.up ? (long long)pb.taps.size() : (pb.lg <= kUpStagedLg ? (long long)pb.maxph << (2 * pb.lg) : 0);
+            }
+            const long long tapel = (ntaps * (4 + esize) + 15) / 16 * 16 / esize;
+            if (ok && regs + tapel <= budget / esize) {
+                sup = true;
+                ST = 64;
+            }
+        }
         // staged down pairs, staged up pairs (in batches that fill a buffer), then the global
         // ones; within a batch the staged taps (down pairs only) are contiguous
         std::vector<int> order;
@@ -236,7 +262,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 continue;
             }
             const PairBuild& pb = *by_out[o][k];
-            const Geometry g = geometry(pb, TS, esize, e4, vecf[k]);
+            const Geometry g = geometry(pb, ST, esize, e4, vecf[k], TS);
             const int need = (int)((g.bytes + 15) / 16 * 16 / esize);
             // staged taps: down pairs and up pairs with r <= 8 (larger phase tables are read
             // from global memory)
@@ -267,7 +293,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 const double macs = outs_full * pb.maxph;
                 double c = macs * kCostMacGlobal;
                 if (!global[order[q]]) {
-                    const Geometry g = geometry(pb, TS, esize, e4, vecf[order[q]]);
+                    const Geometry g = geometry(pb, ST, esize, e4, vecf[order[q]], TS);
                     const int nt = !pb.up ? (int)pb.taps.size() : (pb.lg <= kUpStagedLg ? pb.maxph << (2 * pb.lg) : 0);
                     c = (double)g.RR * g.RC * kCostStage + macs * mac_smem + kCostTapStage * nt;
                 }
@@ -283,7 +309,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         for (size_t q = 0; q < order.size(); ++q) {
             const int k = order[q];
             const PairBuild& pb = *by_out[o][k];
-            const Geometry g = geometry(pb, TS, esize, e4, vecf[k]);
+            const Geometry g = geometry(pb, ST, esize, e4, vecf[k], TS);
             const int r = 1 << pb.lg, m = r - 1;
             TileBatch& bt = plan.batches[sub.batch_begin + batch_of[q]];
             if (bt.pair_end == bt.pair_begin) {
@@ -375,22 +401,24 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         }
         sub.pair_end = (int)plan.pairs.size();
         sub.batch_end = (int)plan.batches.size();
-        sub.pad = 0;
+        sub.sup = sup ? 1 : 0;
         sub.lgTS = 0;
         while ((1 << sub.lgTS) < TS) ++sub.lgTS;
-        const int ty = (so.rows + TS - 1) / TS, tx = (so.cols + TS - 1) / TS;
+        const int ty = (so.rows + ST - 1) / ST, tx = (so.cols + ST - 1) / ST;
         for (int a = 0; a < ty; ++a)
             for (int b = 0; b < tx; ++b) {
-                const int vy = std::min(TS, so.rows - a * TS), vx = std::min(TS, so.cols - b * TS);
+                const int vy = std::min(ST, so.rows - a * ST), vx = std::min(ST, so.cols - b * ST);
                 const double outs = (double)vy * vx;
-                // MACs per thread-slot plus staging; small tiles leave threads in groups
-                const double cost = best * outs;
+                // MACs per thread-slot plus staging; small tiles leave threads in groups (a super
+                // tile pays the per-tile cost once for its four tiles)
+                const double cost = best * outs - (sup ? 0.75 * kCostItem * outs / (TS * TS) : 0.0);
                 plan.macs += (long long)(outs * taps_per_out);
                 if (level_only <= 0 || so.level == level_only)
-                    items.push_back({TileItem{o, a * TS, b * TS, sub.batch_begin, sub.batch_end,
-                                              sub.lgTS | (sub.e4 << 8), 1 << 16, -1},
+                    items.push_back({TileItem{o, a * ST, b * ST, sub.batch_begin, sub.batch_end,
+                                              sub.lgTS | (sub.e4 << 8) | (sub.sup << 9), 1 << 16, -1},
                                      cost});
             }
+        plan.n_sup += sup ? 1 : 0;
     }
     if (split_share > 0.0 && !items.empty()) {
         // split the tiles that would dominate one CTA's share into parts of whole batches
@@ -752,10 +780,13 @@ __device__ __forceinline__ void up_taps4(TapSrc<T> ts, int j0, int n, int G, int
 }
 
 // Accumulate the pairs of batch `bi` of tile `w` (staged in S) into acc.
+// (oy, ox): offset of the computed tile inside the staged one (a super tile's quarter; 0, 0
+// for ordinary tiles)
 template <typename T>
 __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* __restrict__ in, const TileItem& w,
                                               const SubbandDev& so, int bi, const T* __restrict__ S,
-                                              const PairSm* __restrict__ tab, const ThreadMap& tm, T (&acc)[4]) {
+                                              const PairSm* __restrict__ tab, const ThreadMap& tm, T (&acc)[4],
+                                              int oy = 0, int ox = 0) {
     const TileBatch bt = plan.batches[bi];
     const TapSrc<T> stap = staged_taps<T>(S, bt);
     const T* __restrict__ gvals = tvals<T>(plan);
@@ -767,7 +798,7 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
         const int lg = P.lg, r = 1 << lg, m = r - 1;
         if (P.mode == kDown) {
             const TapSrc<T> ts = stap + P.tap_begin;
-            const T* __restrict__ Sb = S + tm.ly * P.PC + tm.lx + sh;
+            const T* __restrict__ Sb = S + (tm.ly + oy) * P.PC + tm.lx + ox + sh;
             if (E == 4) {
                 if (tm.sx == 8) down_taps4<8, T>(ts, g, P.ntap, G, Sb, acc);
                 else if (tm.sx == 4) down_taps4<4, T>(ts, g, P.ntap, G, Sb, acc);
@@ -796,7 +827,7 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
             // neighbouring outputs read neighbouring phases, and every tile of the subband
             // reads the same table, so these loads are coalesced L1/L2 hits
             const int rr = r * r;
-            const int py = w.ty0 + tm.ly, px = w.tx0 + tm.lx;
+            const int py = w.ty0 + oy + tm.ly, px = w.tx0 + ox + tm.lx;
             const int rowb = ((py >> lg) - (w.ty0 >> lg)) * P.PC + sh;
             const bool st = lg <= kUpStagedLgDev;   // phase tables staged with the batch
             const TapSrc<T> gts = (st ? stap : global_taps<T>(plan)) + P.tap_begin;
@@ -848,7 +879,7 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (e >= E) continue;
-                const int py = w.ty0 + tm.ly, px = w.tx0 + tm.lx + tm.sx * e;
+                const int py = w.ty0 + oy + tm.ly, px = w.tx0 + ox + tm.lx + tm.sx * e;
                 if (py >= so.rows || px >= so.cols) continue;
                 int by, bx, tb, step;
                 if (P.mode == kDownGlobal) {
@@ -992,7 +1023,8 @@ __device__ __forceinline__ void epilogue(const TileItem& w, const SubbandDev& so
 // ---------------------------------------------------------------------------------------
 // SPLIT: the plan has split tiles (a separate instance, so that plans without them run code
 // that carries none of the combining step)
-template <typename T, int EPI, bool SPLIT>
+// SUP: the plan has super tiles (likewise a separate instance)
+template <typename T, int EPI, bool SPLIT, bool SUP>
 __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const T* __restrict__ in,
                                                             T* __restrict__ out, EpiArgs ep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1047,13 +1079,29 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         __syncthreads();
         const SubbandDev so = A.sb[w.o];
         const ThreadMap tm = thread_map(w);
-        compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc);
-        if (bi + 1 == w.batch_end) {
-            group_reduce<T>(tm, acc, red_buf);
-            if (!SPLIT || w.split < (2 << 16) || combine_parts<T>(plan, w, tm, acc))
-                epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
+        if (SUP && w.sup()) {
+            // a super tile (one batch, 4 outputs per thread, no thread groups): its 2 x 2
+            // tiles one after the other from the same staged regions
+            for (int q = 0; q < 4; ++q) {
+                const int oy = (q >> 1) << w.lgTS(), ox = (q & 1) << w.lgTS();
+                if (w.ty0 + oy >= so.rows || w.tx0 + ox >= so.cols) continue;
+                compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc, oy, ox);
+                TileItem wq = w;
+                wq.ty0 += oy;
+                wq.tx0 += ox;
+                epilogue<T, EPI>(wq, so, tm, acc, out, ep, beta, pt);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[e] = 0;
+                for (int e = 0; e < 4; ++e) acc[e] = 0;
+            }
+        } else {
+            compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc);
+            if (bi + 1 == w.batch_end) {
+                group_reduce<T>(tm, acc, red_buf);
+                if (!SPLIT || w.split < (2 << 16) || combine_parts<T>(plan, w, tm, acc))
+                    epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[e] = 0;
+            }
         }
         it = nit;
         bi = nbi;
@@ -1262,11 +1310,11 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
 
 // pdl: programmatic dependent launch, so that this grid's CTAs are scheduled while the
 // previous kernel of the stream drains (the kernel waits for that grid before its work)
-template <typename T, int EPI, bool SPLIT>
+template <typename T, int EPI, bool SPLIT, bool SUP>
 wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl) {
     static bool attr = false;
     if (!attr) {
-        WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI, SPLIT, SUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     200 * 1024));
         attr = true;
     }
@@ -1281,20 +1329,22 @@ wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs&
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        WDB_CK(cudaLaunchKernelEx(&cfg, tile_kernel<T, EPI, SPLIT>, A, in, out, ep));
+        WDB_CK(cudaLaunchKernelEx(&cfg, tile_kernel<T, EPI, SPLIT, SUP>, A, in, out, ep));
     } else {
-        tile_kernel<T, EPI, SPLIT><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
+        tile_kernel<T, EPI, SPLIT, SUP><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
     }
     count_launch();
     WDB_CK(cudaGetLastError());
     return WDB_OK;
 }
 
-// Plans with split tiles (FP32 only) run the instance with the combining step.
+// Plans with split tiles or super tiles (FP32 only) run the instances with those steps.
 template <typename T, int EPI>
 wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl = false) {
-    if (sizeof(T) == 4 && A.plan.split_ctr) return launch_tile_as<T, EPI, sizeof(T) == 4>(A, in, out, ep, st, pdl);
-    return launch_tile_as<T, EPI, false>(A, in, out, ep, st, pdl);
+    constexpr bool f32 = sizeof(T) == 4;
+    if (f32 && A.plan.split_ctr) return launch_tile_as<T, EPI, f32, false>(A, in, out, ep, st, pdl);
+    if (f32 && A.plan.n_sup > 0) return launch_tile_as<T, EPI, false, f32>(A, in, out, ep, st, pdl);
+    return launch_tile_as<T, EPI, false, false>(A, in, out, ep, st, pdl);
 }
 
 template <int EPI>
@@ -1316,8 +1366,10 @@ int tile_grid(int smem_bytes) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(tile_kernel<float, kK2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2, false>, kTileThreads, smem_bytes);
+    cudaFuncSetAttribute(tile_kernel<float, kK2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2, false, false>, kTileThreads,
+                                                  smem_bytes);
     if (sms <= 0) sms = 1;
     if (per <= 0) per = 1;
     return sms * per;

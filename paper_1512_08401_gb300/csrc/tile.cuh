@@ -46,7 +46,7 @@ struct alignas(16) TileSub {      // per output subband
     int pair_begin, pair_end;
     int batch_begin, batch_end;   // batches of pairs whose staged regions share one buffer
     int e4;           // 1: 4 outputs per thread (TS >= 8), 0: 1 output per thread
-    int pad;
+    int sup;          // 1: work items are super tiles (2 x 2 tiles of side TS staged together)
 };
 
 struct TileTune {     // autotuner's choice for one output subband (ts = 0: the planner's)
@@ -67,7 +67,8 @@ struct alignas(16) TileItem {     // one tile (or one part of it); carries what 
     int o;
     int ty0, tx0;
     int batch_begin, batch_end;   // batches of the subband this item accumulates
-    int geo;                      // the subband's tile side and thread map: lgTS | e4 << 8
+    int geo;                      // the subband's tile side and thread map:
+                                  // lgTS | e4 << 8 | sup << 9 (sup: a 2 x 2 super tile)
     int split;                    // part | nparts << 16 (nparts > 1: the tile's batches are split
                                   // over nparts items)
     int sid;                      // split tiles: index of the arrival counter and partial sums
@@ -82,7 +83,11 @@ struct alignas(16) TileItem {     // one tile (or one part of it); carries what 
 #ifdef __CUDACC__
     __host__ __device__
 #endif
-    int e4() const { return geo >> 8; }
+    int e4() const { return (geo >> 8) & 1; }
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    int sup() const { return (geo >> 9) & 1; }
 #ifdef __CUDACC__
     __host__ __device__
 #endif
@@ -121,6 +126,7 @@ struct TilePlanDev {
     const float* tap_v;
     const double* tap_v64;
     const TapOV* tap_ov;      // (tap_off, tap_v) interleaved: the FP32 kernels' tap records
+    int n_sup;                // subbands tiled in super tiles (0: none)
     unsigned int* split_ctr;  // per split tile: parts finished (zero between launches)
     const long long* split_base;   // per split tile: first element of its partial sums
     void* split_buf;          // per split tile: nparts x TS^2 partial sums (element type of the plan)
@@ -142,6 +148,7 @@ struct TilePlanHost {
     std::vector<TapOV> tap_ov;
     std::vector<double> item_cost;   // estimated cost of every item (items are sorted by it)
     int esize = 4;                   // element size (4: FP32, 8: FP64)
+    int n_sup = 0;                   // subbands tiled in super tiles
     int n_split = 0;                 // split tiles
     std::vector<long long> split_base;   // first partial-sum element of each split tile
     long long split_elems = 0;       // partial-sum elements of all split tiles
@@ -161,9 +168,11 @@ struct TileEntry {             // one tap of one pair, in gather form
 // 0: a tile of several batches whose modelled cost exceeds split_share times one CTA's share
 // is split at batch boundaries into parts that different CTAs run concurrently; the last
 // part to finish sums the parts' partial sums in part order and runs the epilogue.
+// super_tiles: subbands of 32-tiles whose pairs all fit one buffer for a 64-tile are worked
+// in items of 2 x 2 tiles staged together (no split tiles then).
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget,
                             int ctas = 456, const std::vector<TileTune>* tune = nullptr, int level_only = 0,
-                            double cap_share = 2.0, double split_share = 0.0);
+                            double cap_share = 2.0, double split_share = 0.0, bool super_tiles = false);
 
 struct TileQueue {             // device counters of one operator launch
     unsigned int next;         // next work item

@@ -35,7 +35,8 @@ class ThetaInfo(C.Structure):
                 ("wavelet_taps", C.c_int), ("rule", C.c_int), ("K_requested", C.c_longlong),
                 ("K_eff", C.c_longlong), ("n_taps", C.c_longlong), ("n_candidates", C.c_longlong),
                 ("theta_max_abs", C.c_double), ("phase_table_len", C.c_int), ("build_ms", C.c_double),
-                ("plan_tuned", C.c_int), ("plan_items", C.c_int * 2), ("plan_split_tiles", C.c_int * 2)]
+                ("plan_tuned", C.c_int), ("plan_items", C.c_int * 2), ("plan_split_tiles", C.c_int * 2),
+                ("plan_super_subbands", C.c_int * 2)]
 
 
 class SolveParams(C.Structure):
@@ -71,7 +72,7 @@ _SIGS = {
     "wdb_theta_load": (i32, [C.c_char_p, vp, C.POINTER(vp)]),
     "wdb_theta_free": (None, [vp]),
     "wdb_theta_apply": (i32, [vp, vp, vp, i32, vp]),
-    "wdb_theta_replan": (i32, [vp, i32, f64, f64, vp]),
+    "wdb_theta_replan": (i32, [vp, i32, f64, f64, i32, vp]),
     "wdb_solve": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_solve_coeffs": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_theta_objective": (i32, [vp, vp, vp, f64, pd, vp, pd]),
@@ -255,10 +256,10 @@ class Theta:
     def save(self, path):
         _check(lib().wdb_theta_save(self._h, path.encode()))
 
-    def replan(self, smem_budget=0, cap_share=0.0, split_share=0.0, stream=None):
+    def replan(self, smem_budget=0, cap_share=0.0, split_share=0.0, super_tiles=False, stream=None):
         """Planner plans for the FP32 kernels in place of the autotuned ones (wdb_theta_replan)."""
         _check(lib().wdb_theta_replan(self._h, int(smem_budget), float(cap_share), float(split_share),
-                                      _stream(stream)))
+                                      1 if super_tiles else 0, _stream(stream)))
         self.info = self._info()
 
     def apply(self, x, out, transpose=False, stream=None):

@@ -187,9 +187,11 @@ def test_planner_plans_and_split_tiles_match_oracle(wdb, name, budget, cap, spli
         g.replan(98305, 2.0, 0.0)
 
 
-def test_split_tiles_fista_trajectory_parity(wdb):
-    """Kernels 1 and 2 over plans with split tiles: the FISTA trajectory of the oracle, and
-    the same iterate from a solve without graphs."""
+@pytest.mark.parametrize("plan", ["split", "super"])
+def test_split_and_super_tiles_fista_trajectory_parity(wdb, plan):
+    """Kernels 1 and 2 over plans with split tiles, or with super tiles (2 x 2 tiles staged
+    together and computed one after the other): the FISTA trajectory of the oracle, and the
+    same iterate from a solve without graphs."""
     prob = synthetic.small_problem()
     n, J, lam, kind = 128, 4, prob.lam, "spai"
     case = build_case(prob.psf, n, n, J, 30 * n * n, prob.u0)
@@ -197,8 +199,20 @@ def test_split_tiles_fista_trajectory_parity(wdb):
     ref = fista(case, lam, P, tau, 120)
     g = gpu_from_oracle(wdb, case, n, n, J)
     g.set_precond(kind, Ptab, tau)
-    g.replan(8192, 1.0, 0.05)
-    assert min(g.info.plan_split_tiles) > 0
+    if plan == "split":
+        g.replan(8192, 1.0, 0.05)
+        assert min(g.info.plan_split_tiles) > 0
+    else:
+        g.replan(32768, 2.0, 0.0, super_tiles=True)
+        assert min(g.info.plan_super_subbands) > 0 and list(g.info.plan_split_tiles) == [0, 0]
+        y = np.random.default_rng(16).standard_normal(n * n)
+        out = torch.zeros(n * n, device="cuda")
+        g.apply(dev(y), out)
+        assert rel_max(host(out), case.th.mat @ y) < 2e-6
+        g.apply(dev(y), out, transpose=True)
+        assert rel_max(host(out), case.th.matT @ y) < 2e-6
+        with pytest.raises(wdb.WdbError):
+            g.replan(32768, 2.0, 0.5, super_tiles=True)
     x = torch.zeros(n * n, device="cuda")
     r = g.solve_coeffs(dev(case.x0), x, lam=lam, max_iters=120, tol=0.0, precond=kind)
     assert r["iters"] == 120
