@@ -344,7 +344,7 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic_record(name, "1024"),
             "bytes_per_launch": nbytes, "launch_ms": dur,
-            "note": "1024^2 working set (~24 MB) stays in L2 across iterations; HBM bound judged at 4096^2"}
+            "note": "1024^2 working set (~24 MB) stays in L2 across iterations; the HBM bound is measured at 4096^2"}
 
     out = {"metric": METRIC, "value": ms_theta, "unit": "ms", "n_gpus": d.world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_theta, "higher_is_better": False, "scaling": "weak",
