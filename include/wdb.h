@@ -46,7 +46,8 @@ typedef enum {
     WDB_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
     WDB_EDIVERGED = 6,     /* the objective grew by more than 1e6 x its first value */
     WDB_EUNSUPPORTED = 7,  /* valid but not supported (e.g. more than 64 subbands) */
-    WDB_EIO = 8            /* file could not be read or written, or has a bad format */
+    WDB_EIO = 8,           /* file could not be read or written, or has a bad format */
+    WDB_EPLAN = 9          /* a tile plan broke one of its invariants (wdb_tile_plan_check) */
 } wdb_status;
 
 #define WDB_MAX_SUBBANDS 64
@@ -166,6 +167,24 @@ wdb_status wdb_theta_set_precond(wdb_theta* th, int precond, const double* P_hos
  * 98304, or split_share > 0 together with super_tiles. Synchronises `stream`. */
 wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, int super_tiles,
                             void* stream);
+
+/* Planner self-check on the host (no GPU needed). Builds the tile plan of Theta_K
+ * (transpose = 0) or Theta_K^T (1) for a tap list in the convention of wdb_theta_from_taps,
+ * for element size esize (4: FP32, 8: FP64), a staging buffer of smem_budget bytes (<= 0:
+ * 32768), cap_share, split_share and super_tiles as in wdb_theta_replan, balanced for `ctas`
+ * CTAs (<= 0: 456), and checks its structural invariants: every output of every subband
+ * produced exactly once, every staged region and tap area inside the staging buffer, every
+ * staged read inside its pair's region, and the conditions of super tiles, split tiles and
+ * 16-byte staging. Fills *summary (may be NULL). WDB_EPLAN: an invariant is broken
+ * (wdb_last_error names the first); WDB_EINVAL: bad sizes, subband indices or esize. */
+typedef struct {
+    int items, pairs, batches, split_tiles, super_subbands, smem_bytes;
+    long long macs;             /* multiply-adds of one application (padding included) */
+} wdb_plan_summary;
+wdb_status wdb_tile_plan_check(int n_rows, int n_cols, int levels, long long n_taps, const int* a_host,
+                               const int* b_host, const int* oy_host, const int* ox_host, const double* v_host,
+                               int transpose, int esize, int smem_budget, double cap_share, double split_share,
+                               int super_tiles, int ctas, wdb_plan_summary* summary);
 
 /* Serialise / restore a handle (taps, layout, wavelet; preconditioners are recomputed). */
 wdb_status wdb_theta_save(const wdb_theta* th, const char* path);

@@ -180,6 +180,41 @@ wdb_status wdb_theta_info_get(const wdb_theta* th, wdb_theta_info* info) {
     return WDB_OK;
 }
 
+wdb_status wdb_tile_plan_check(int n_rows, int n_cols, int levels, long long n_taps, const int* a, const int* b,
+                               const int* oy, const int* ox, const double* v, int transpose, int esize,
+                               int smem_budget, double cap_share, double split_share, int super_tiles, int ctas,
+                               wdb_plan_summary* summary) {
+    if (n_taps < 0 || (n_taps > 0 && (!a || !b || !oy || !ox || !v))) return set_error(WDB_EINVAL, "bad tap arrays");
+    if (esize != 4 && esize != 8) return set_error(WDB_EINVAL, "esize %d (4 or 8)", esize);
+    if (smem_budget > 98304) return set_error(WDB_EINVAL, "smem_budget %d > 98304", smem_budget);
+    Layout L;
+    WDB_TRY(make_layout(n_rows, n_cols, levels, &L));
+    std::vector<Tap> taps((size_t)n_taps);
+    for (long long i = 0; i < n_taps; ++i) {
+        if (a[i] < 0 || a[i] >= L.S || b[i] < 0 || b[i] >= L.S)
+            return set_error(WDB_EINVAL, "tap %lld names subband (%d, %d) of %d", i, a[i], b[i], L.S);
+        taps[(size_t)i] = Tap{a[i], b[i], oy[i], ox[i], v[i]};
+    }
+    std::vector<TileEntry> te[2];
+    gather_entries(L, taps, te);
+    const TilePlanHost P =
+        make_tile_plan(L, te[transpose ? 1 : 0], esize, smem_budget > 0 ? smem_budget : 32768, ctas > 0 ? ctas : 456,
+                       nullptr, 0, cap_share > 0.0 ? cap_share : 2.0, split_share > 0.0 ? split_share : 0.0,
+                       super_tiles != 0);
+    if (summary) {
+        summary->items = (int)P.items.size();
+        summary->pairs = (int)P.pairs.size();
+        summary->batches = (int)P.batches.size();
+        summary->split_tiles = P.n_split;
+        summary->super_subbands = P.n_sup;
+        summary->smem_bytes = P.smem_bytes;
+        summary->macs = P.macs;
+    }
+    const std::string err = check_tile_plan(L, P);
+    if (!err.empty()) return set_error(WDB_EPLAN, "%s", err.c_str());
+    return WDB_OK;
+}
+
 wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, int super_tiles,
                             void* stream) {
     if (!th) return set_error(WDB_EINVAL, "NULL handle");
@@ -455,6 +490,7 @@ const char* wdb_status_str(wdb_status s) {
         case WDB_EDIVERGED: return "diverged";
         case WDB_EUNSUPPORTED: return "unsupported";
         case WDB_EIO: return "I/O error";
+        case WDB_EPLAN: return "tile plan invariant broken";
     }
     return "unknown status";
 }

@@ -215,12 +215,12 @@ struct PEntry {
     }
 };
 
-static void build_ops(wdb_theta* th) {
-    const Layout& L = th->lay;
+// Kept taps -> gather-form entries of Theta_K (te[0]) and Theta_K^T (te[1]), sorted (host).
+void gather_entries(const Layout& L, const std::vector<Tap>& taps, std::vector<TileEntry> (&te)[2]) {
     std::vector<PEntry> F, A;
-    F.reserve(th->taps.size());
-    A.reserve(th->taps.size());
-    for (const Tap& t : th->taps) {
+    F.reserve(taps.size());
+    A.reserve(taps.size());
+    for (const Tap& t : taps) {
         const SubbandDev &sa = L.sb[t.a], &sb = L.sb[t.b];
         if (sa.level <= sb.level) {  // column form: tap array in subband a
             const int lg = sb.level - sa.level;
@@ -244,6 +244,17 @@ static void build_ops(wdb_theta* th) {
     }
     std::sort(F.begin(), F.end());
     std::sort(A.begin(), A.end());
+    for (int op = 0; op < 2; ++op) {
+        const std::vector<PEntry>& src = op ? A : F;
+        te[op].resize(src.size());
+        for (size_t i = 0; i < src.size(); ++i)
+            te[op][i] = TileEntry{src[i].out, src[i].in, src[i].up, src[i].lg, src[i].phase, src[i].dy, src[i].dx, src[i].v};
+    }
+}
+
+static void build_ops(wdb_theta* th) {
+    const Layout& L = th->lay;
+    gather_entries(L, th->taps, th->tent);
     // the tiles are shared by about 3 resident CTAs per SM
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -251,13 +262,8 @@ static void build_ops(wdb_theta* th) {
     const int ctas = 3 * std::max(sms, 1);
     th->plan_ctas = ctas;
     for (int op = 0; op < 2; ++op) {
-        const std::vector<PEntry>& src = op ? A : F;
-        std::vector<TileEntry>& te = th->tent[op];
-        te.resize(src.size());
-        for (size_t i = 0; i < src.size(); ++i)
-            te[i] = TileEntry{src[i].out, src[i].in, src[i].up, src[i].lg, src[i].phase, src[i].dy, src[i].dx, src[i].v};
-        th->tplan[op][0] = make_tile_plan(L, te, 4, kTileSmemBudget, ctas);
-        th->tplan[op][1] = make_tile_plan(L, te, 8, kTileSmemBudget, ctas);
+        th->tplan[op][0] = make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, ctas);
+        th->tplan[op][1] = make_tile_plan(L, th->tent[op], 8, kTileSmemBudget, ctas);
     }
 }
 

@@ -25,6 +25,7 @@ bool setup_fp64(const wdb_theta* th);
 wdb_status theta_build_device(wdb_theta* th, const double* psf_host, int kh, int kw, long long K, int rule,
                               cudaStream_t st);
 wdb_status theta_finalize(wdb_theta* th, cudaStream_t st);
+void gather_entries(const Layout& L, const std::vector<Tap>& taps, std::vector<TileEntry> (&te)[2]);
 wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st);
 wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, bool super_tiles,
                         cudaStream_t st);

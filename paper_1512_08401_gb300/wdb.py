@@ -21,13 +21,18 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "wdb.h")
 PRECOND = {"none": 0, "jacobi": 1, "spai": 2}
 RULE = {"weighted": 0, "naive": 1}
 STATUS = {0: "ok", 1: "invalid argument", 2: "out of memory", 3: "CUDA error", 4: "NaN or Inf",
-          5: "timeout", 6: "diverged", 7: "unsupported", 8: "I/O error"}
+          5: "timeout", 6: "diverged", 7: "unsupported", 8: "I/O error", 9: "tile plan invariant broken"}
 
 
 class WdbError(RuntimeError):
     def __init__(self, status: int, detail: str):
         super().__init__(f"libwdb: {STATUS.get(status, status)}: {detail}")
         self.status = status
+
+
+class PlanSummary(C.Structure):
+    _fields_ = [("items", C.c_int), ("pairs", C.c_int), ("batches", C.c_int), ("split_tiles", C.c_int),
+                ("super_subbands", C.c_int), ("smem_bytes", C.c_int), ("macs", C.c_longlong)]
 
 
 class ThetaInfo(C.Structure):
@@ -73,6 +78,8 @@ _SIGS = {
     "wdb_theta_free": (None, [vp]),
     "wdb_theta_apply": (i32, [vp, vp, vp, i32, vp]),
     "wdb_theta_replan": (i32, [vp, i32, f64, f64, i32, vp]),
+    "wdb_tile_plan_check": (i32, [i32, i32, i32, i64, pi, pi, pi, pi, pd, i32, i32, i32, f64, f64, i32, i32,
+                                  C.POINTER(PlanSummary)]),
     "wdb_solve": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_solve_coeffs": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_theta_objective": (i32, [vp, vp, vp, f64, pd, vp, pd]),
@@ -343,6 +350,22 @@ class FFTOp:
             self.free()
         except Exception:
             pass
+
+
+def tile_plan_check(n_rows, n_cols, levels, a, b, oy, ox, v, transpose=False, esize=4, smem_budget=0,
+                    cap_share=0.0, split_share=0.0, super_tiles=False, ctas=0):
+    """Build one operator's tile plan for a tap list on the host and check its invariants
+    (wdb_tile_plan_check); returns the plan summary as a dict, raises WdbError on a fault."""
+    a, pa = _i32(a)
+    b, pb = _i32(b)
+    oy, py = _i32(oy)
+    ox, px = _i32(ox)
+    v, pv = _f64(v)
+    sm = PlanSummary()
+    _check(lib().wdb_tile_plan_check(n_rows, n_cols, levels, len(v), pa, pb, py, px, pv, 1 if transpose else 0,
+                                      esize, smem_budget, cap_share, split_share, 1 if super_tiles else 0, ctas,
+                                      C.byref(sm)))
+    return {f: getattr(sm, f) for f, _ in PlanSummary._fields_}
 
 
 def dwt(img, coef, n_rows, n_cols, wavelet="db4", levels=4, stream=None):
