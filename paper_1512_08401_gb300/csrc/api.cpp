@@ -8,6 +8,7 @@
 #include <new>
 
 #include "solve_impl.h"
+#include "plan_check.h"
 #include "theta_impl.h"
 #include "wdb_internal.h"
 

@@ -13,7 +13,6 @@
 // staged with cp.async, double buffered so that the next batch's loads are in flight while
 // the current batch computes.
 #pragma once
-#include <string>
 #include <vector>
 
 #include "layout_types.h"
@@ -174,13 +173,6 @@ struct TileEntry {             // one tap of one pair, in gather form
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget,
                             int ctas = 456, const std::vector<TileTune>* tune = nullptr, int level_only = 0,
                             double cap_share = 2.0, double split_share = 0.0, bool super_tiles = false);
-
-// Structural invariants of a plan (host only): every output of every subband is produced by
-// exactly one item (the parts of a split tile chain its batches once), every staged region
-// and tap area lies in the staging buffer, every staged read of a tap stays inside its
-// pair's region (its polyphase plane for down pairs), and super tiles, split tiles and pairs
-// staged in 16-byte chunks meet their conditions. Empty string: valid; else the first fault.
-std::string check_tile_plan(const Layout& L, const TilePlanHost& P);
 
 struct TileQueue {             // device counters of one operator launch
     unsigned int next;         // next work item
