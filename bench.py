@@ -167,7 +167,7 @@ def traffic_record(kernel: str, workload: str):
     if not entry:
         return None
     try:
-        from paper_1512_08401_gb300.ncu_summary import kernel_sources_sha256
+        from ncu_summary import kernel_sources_sha256
         if entry.get("sources_sha256") != kernel_sources_sha256(entry["sources"]):
             return None
     except (KeyError, OSError):

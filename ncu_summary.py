@@ -3,7 +3,7 @@
 Summarise a launch list (--metrics gpu__time_duration.sum --csv) per kernel: launches,
 total device time and share, split by NVTX range when ncu recorded one:
 
-    python -m paper_1512_08401_gb300.ncu_summary launches.csv
+    python -m ncu_summary launches.csv
 
 Record the DRAM bytes per launch of the two FISTA kernels from a capture that holds
 dram__bytes_read.sum and dram__bytes_write.sum (the first launch of each kernel), with the
@@ -11,7 +11,7 @@ hash of the sources they were compiled from, in profiles/traffic.json (bench.py 
 record only while the sources still hash the same):
 
     ncu -i capture.ncu-rep --page raw --csv > raw.csv      (or an ncu --csv metrics log)
-    python -m paper_1512_08401_gb300.ncu_summary traffic raw.csv 4096 profiles/tile_kernels_4096_full.md
+    python -m ncu_summary traffic raw.csv 4096 profiles/tile_kernels_4096_full.md
 """
 from __future__ import annotations
 
@@ -23,7 +23,7 @@ import re
 import sys
 from collections import defaultdict
 
-CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1512_08401_gb300", "csrc")
 TILE_SOURCES = ["tile.cu", "tile.cuh", "device_util.cuh", "layout_types.h", "wdb_internal.h"]
 # name prefixes of the two FISTA kernels (tile_kernel<float, EPI[, SPLIT]>)
 FISTA_KERNELS = {"k1_residual": "tile_kernel<float, 2", "k2_step": "tile_kernel<float, 3"}
@@ -145,7 +145,7 @@ def write_traffic(csv_path: str, workload: str, profile: str, record: str) -> di
 
 if __name__ == "__main__":
     if len(sys.argv) >= 2 and sys.argv[1] == "traffic":
-        root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+        root = os.path.dirname(os.path.abspath(__file__))
         print(json.dumps(write_traffic(sys.argv[2], sys.argv[3], sys.argv[4],
                                        os.path.join(root, "profiles", "traffic.json")), indent=1))
     else:

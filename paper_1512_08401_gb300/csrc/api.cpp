@@ -1,5 +1,5 @@
 // C ABI of libwdb (declared in include/wdb.h). Argument validation, handle lifetime,
-// serialisation; the work is done by theta.cu, stencil.cu, dwt.cu and solve.cu.
+// serialisation; the work is done by theta.cu, subband_ops.cu, dwt.cu and solve.cu.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

@@ -1,4 +1,4 @@
-// FISTA drivers: Algorithm 3 on Theta_K (kernels 1 and 2 of stencil.cu) and the exact
+// FISTA drivers: Algorithm 3 on Theta_K (kernels 1 and 2 of subband_ops.cu) and the exact
 // operator path (Algorithm 1 gradient: IDWT, R2C, spectral residual, C2R, DWT, step).
 //
 // The iteration runs on the device without host round trips: the step kernel's last CTA
@@ -13,7 +13,7 @@
 #include "device_util.cuh"
 #include "fftops.cuh"
 #include "solve_impl.h"
-#include "stencil.cuh"
+#include "subband_ops.cuh"
 #include "theta_impl.h"
 
 namespace wdb {
@@ -224,7 +224,7 @@ wdb_status theta_workspace_public(wdb_theta* th, cudaStream_t st) {
 
 wdb_status theta_objective_dev(wdb_theta* th, const float* x, const float* x0, const float* w_dev, cudaStream_t st,
                                double* E, long long* support) {
-    StencilArgs F = stencil_args(th);
+    SubbandArgs F = subband_args(th);
     double* d_out = reinterpret_cast<double*>(&th->d_state->scratch[0]);
     WDB_TRY(tile_resnorm(tile_args(th, false, false), x, x0, th->d_r, d_out, th->d_red_part, st));
     WDB_TRY(launch_l1_terms(F, th->grid, x, w_dev, th_red(th, d_out + 1), st));
@@ -424,7 +424,7 @@ wdb_status fftop_create(const double* psf_host, int kh, int kw, const Layout& L,
         if ((s = fft_alloc(op, (void**)&op->d_vb_start, sizeof(int) * op->sched.vb_start.size()))) break;
         cudaMemcpyAsync(op->d_vb_start, op->sched.vb_start.data(), sizeof(int) * op->sched.vb_start.size(),
                         cudaMemcpyHostToDevice, st);
-        op->grid = std::max(1, std::min(op->sched.nvb, stencil_grid_limit()));
+        op->grid = std::max(1, std::min(op->sched.nvb, subband_grid_limit()));
         if ((s = fft_alloc(op, (void**)&op->d_part, sizeof(double) * op->grid * 4))) break;
         if ((s = fft_alloc(op, (void**)&op->d_red_part, sizeof(double) * op->grid * 4))) break;
         if ((s = fft_alloc(op, (void**)&op->d_counter, sizeof(unsigned int) * 4))) break;
@@ -469,8 +469,8 @@ void fftop_free(wdb_fftop* op) {
     delete op;
 }
 
-static StencilArgs fft_args(const wdb_fftop* op) {
-    StencilArgs A{};
+static SubbandArgs fft_args(const wdb_fftop* op) {
+    SubbandArgs A{};
     A.sb = op->d_sb;
     A.vb_start = op->d_vb_start;
     A.S = op->lay.S;
@@ -498,7 +498,7 @@ static wdb_status fft_power(wdb_fftop* op, const std::vector<double>& Ptab, cuda
     bool hf = false, hi = false;
     wdb_status s = WDB_OK;
     double lam = 0.0;
-    StencilArgs A = fft_args(op);
+    SubbandArgs A = fft_args(op);
     do {
         if ((s = dm((void**)&v, sizeof(double) * N))) break;
         if ((s = dm((void**)&t, sizeof(double) * N))) break;
@@ -594,7 +594,7 @@ static wdb_status fft_objective(wdb_fftop* op, const float* x, cudaStream_t st, 
                                                  1.0f / (float)L.N, 0, op->d_red_part, op->d_counter, nullptr, d_out);
     count_launch();
     WDB_CK(cudaGetLastError());
-    StencilArgs A = fft_args(op);
+    SubbandArgs A = fft_args(op);
     WDB_TRY(launch_l1_terms(A, op->grid, x, op->d_w, RedTarget{op->d_counter, op->d_red_part, d_out + 1}, st));
     double h[3];
     WDB_CK(cudaMemcpyAsync(h, d_out, sizeof(double) * 3, cudaMemcpyDeviceToHost, st));
@@ -632,7 +632,7 @@ wdb_status fft_solve(wdb_fftop* op, const float* u, float* x_out, const wdb_solv
     }
     SolveState s0 = init_state(p, m);
     WDB_CK(cudaMemcpyAsync(op->d_state, &s0, sizeof s0, cudaMemcpyHostToDevice, st));
-    StencilArgs A = fft_args(op);
+    SubbandArgs A = fft_args(op);
     IterEngine& E = op->engine;
     if (E.key != p->precond) E.release();
     E.key = p->precond;

@@ -2,7 +2,7 @@
 #pragma once
 #include <cufft.h>
 
-#include "stencil.cuh"
+#include "subband_ops.cuh"
 #include "wdb_internal.h"
 
 struct wdb_fftop {

@@ -13,7 +13,7 @@
 #include <cfloat>
 
 #include "device_util.cuh"
-#include "stencil.cuh"
+#include "subband_ops.cuh"
 
 namespace wdb {
 
@@ -21,7 +21,7 @@ namespace {
 
 // elementwise out = in * scale[class]
 template <typename T>
-__global__ void __launch_bounds__(kVB) scale_kernel(StencilArgs A, const T* __restrict__ in, T* __restrict__ out,
+__global__ void __launch_bounds__(kVB) scale_kernel(SubbandArgs A, const T* __restrict__ in, T* __restrict__ out,
                                                     const double* __restrict__ scale) {
     __shared__ int s_o;
     for (int vb = blockIdx.x; vb < A.nvb; vb += gridDim.x) {
@@ -47,7 +47,7 @@ __device__ __forceinline__ float g_over_w(float g, float w) {
 // FFT path step, g given (the DWT of the image-domain gradient):
 //   z = y - (tau/P) g ; x_new = soft(z, (tau/P) w) ; y_new = x_new + beta_k (x_new - x_old)
 // in place on x and y; FP64 totals of sum w|y| and max |g|/w.
-__global__ void __launch_bounds__(kVB) fft_step(StencilArgs A, const float* __restrict__ g_in, float* __restrict__ y,
+__global__ void __launch_bounds__(kVB) fft_step(SubbandArgs A, const float* __restrict__ g_in, float* __restrict__ y,
                                                 float* __restrict__ x, const float* __restrict__ step_tab,
                                                 const float* __restrict__ w_sb, double* part, SolveState* st) {
     if (*(volatile int*)&st->stop) return;
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(kVB) fft_step(StencilArgs A, const float* __re
 }
 
 // sum w|x| and the support size of x -> red.out[0], red.out[1]
-__global__ void __launch_bounds__(kVB) l1_terms(StencilArgs A, const float* __restrict__ x,
+__global__ void __launch_bounds__(kVB) l1_terms(SubbandArgs A, const float* __restrict__ x,
                                                 const float* __restrict__ w_sb, RedTarget red) {
     __shared__ int s_o;
     float ws = 0.f, wc = 0.f;
@@ -149,14 +149,14 @@ int ew_grid(long long n) {
 // Host launchers
 // ---------------------------------------------------------------------------------------
 template <typename T>
-wdb_status launch_scale(const StencilArgs& A, int grid, const T* in, T* out, const double* scale, cudaStream_t st) {
+wdb_status launch_scale(const SubbandArgs& A, int grid, const T* in, T* out, const double* scale, cudaStream_t st) {
     scale_kernel<T><<<grid, kVB, 0, st>>>(A, in, out, scale);
     count_launch();
     WDB_CK(cudaGetLastError());
     return WDB_OK;
 }
 
-wdb_status launch_fft_step(const StencilArgs& A, int grid, const float* g, float* y, float* x,
+wdb_status launch_fft_step(const SubbandArgs& A, int grid, const float* g, float* y, float* x,
                            const float* step_tab, const float* w_sb, double* part, SolveState* s,
                            cudaStream_t st) {
     fft_step<<<grid, kVB, 0, st>>>(A, g, y, x, step_tab, w_sb, part, s);
@@ -165,7 +165,7 @@ wdb_status launch_fft_step(const StencilArgs& A, int grid, const float* g, float
     return WDB_OK;
 }
 
-wdb_status launch_l1_terms(const StencilArgs& A, int grid, const float* x, const float* w_sb, RedTarget red,
+wdb_status launch_l1_terms(const SubbandArgs& A, int grid, const float* x, const float* w_sb, RedTarget red,
                            cudaStream_t st) {
     l1_terms<<<grid, kVB, 0, st>>>(A, x, w_sb, red);
     count_launch();
@@ -206,7 +206,7 @@ template wdb_status launch_splitmix<double>(double*, long long, unsigned long lo
 template wdb_status launch_scale_const<float>(const float*, float*, long long, double, cudaStream_t);
 template wdb_status launch_scale_const<double>(const double*, double*, long long, double, cudaStream_t);
 
-int stencil_grid_limit() {
+int subband_grid_limit() {
     static int g = 0;
     if (g == 0) {
         int dev = 0, sms = 0, per = 0;
@@ -220,8 +220,8 @@ int stencil_grid_limit() {
     return g;
 }
 
-template wdb_status launch_scale<float>(const StencilArgs&, int, const float*, float*, const double*, cudaStream_t);
-template wdb_status launch_scale<double>(const StencilArgs&, int, const double*, double*, const double*,
+template wdb_status launch_scale<float>(const SubbandArgs&, int, const float*, float*, const double*, cudaStream_t);
+template wdb_status launch_scale<double>(const SubbandArgs&, int, const double*, double*, const double*,
                                          cudaStream_t);
 
 }  // namespace wdb

@@ -23,7 +23,7 @@
 
 #include "device_util.cuh"
 #include "fftops.cuh"
-#include "stencil.cuh"
+#include "subband_ops.cuh"
 #include "theta_impl.h"
 
 namespace wdb {
@@ -191,8 +191,8 @@ static wdb_status upload(wdb_theta* th, const std::vector<T>& h, T** d, cudaStre
     return WDB_OK;
 }
 
-StencilArgs stencil_args(const wdb_theta* th) {
-    StencilArgs A;
+SubbandArgs subband_args(const wdb_theta* th) {
+    SubbandArgs A;
     A.sb = th->d_sb;
     A.vb_start = th->d_vb_start;
     A.S = th->lay.S;
@@ -586,7 +586,7 @@ wdb_status theta_finalize(wdb_theta* th, cudaStream_t st) {
     WDB_TRY(upload(th, sbv, &th->d_sb, st));
     th->sched = make_schedule(L);
     WDB_TRY(upload(th, th->sched.vb_start, &th->d_vb_start, st));
-    th->grid = std::max(1, std::min(th->sched.nvb, stencil_grid_limit()));
+    th->grid = std::max(1, std::min(th->sched.nvb, subband_grid_limit()));
     th->part_len = th->grid;
     if (kAutotunePlans) WDB_TRY(autotune_plans(th, st));
     for (int op = 0; op < 2; ++op)
@@ -782,7 +782,7 @@ static wdb_status power_iteration(wdb_theta* th, const std::vector<double>& P, c
     WDB_CK(cudaMalloc(&d_sc, sizeof(double) * sc.size()));
     WDB_CK(cudaMalloc(&d_out, sizeof(double)));
     WDB_CK(cudaMemcpyAsync(d_sc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, st));
-    StencilArgs F = stencil_args(th);
+    SubbandArgs F = subband_args(th);
     const bool f64 = sizeof(T) == 8;
     TileArgs TF = tile_args(th, false, f64), TA = tile_args(th, true, f64);
     wdb_status s = WDB_OK;

@@ -1,6 +1,6 @@
 // Internal interface between theta.cu, solve.cu and api.cpp.
 #pragma once
-#include "stencil.cuh"
+#include "subband_ops.cuh"
 #include "wdb_internal.h"
 
 namespace wdb {
@@ -18,7 +18,7 @@ constexpr int kTileSmemBudget = 32 * 1024;
 template <typename T>
 wdb_status th_alloc(wdb_theta* th, T** p, size_t n);
 TileArgs tile_args(const wdb_theta* th, bool adj, bool fp64);
-StencilArgs stencil_args(const wdb_theta* th);
+SubbandArgs subband_args(const wdb_theta* th);
 RedTarget th_red(const wdb_theta* th, double* out);
 bool setup_fp64(const wdb_theta* th);
 

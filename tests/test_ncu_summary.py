@@ -5,7 +5,7 @@ import json
 
 import pytest
 
-from paper_1512_08401_gb300 import ncu_summary as ns
+import ncu_summary as ns
 
 
 def _write(path, rows):

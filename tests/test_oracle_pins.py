@@ -439,3 +439,30 @@ def test_gap_decreases_to_zero():
     gaps = [g for (_, _, g) in res.history]
     assert all(g >= 0 for g in gaps)
     assert gaps[-1] < 1e-3 * gaps[0]
+
+
+def _golden_rows(name):
+    from fractions import Fraction
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            f = line.split()
+            rows.append((int(f[0]), [float(Fraction(s)) for s in f[1:]]))
+    return rows
+
+
+def test_fista_momentum_schedule_hand_derived_trajectory():
+    """Algorithm 3's momentum beta_k = (k-1)/(k+2) pinned by a trajectory derived by hand
+    (tests/golden/fista_diag_momentum.txt): a diagonal A with a preconditioner, exact dyadic
+    values for k = 1..6. A different momentum rule (k/(k+3), (k-1)/(k+3), Beck-Teboulle's t_k
+    recursion, an index shifted by one), a dropped P, or a threshold of tau w instead of
+    tau w / P changes x^(2) or x^(3)."""
+    A = np.array([1.0, 0.5, 1.0])
+    b = np.array([4.0, -3.0, 0.25])
+    w = np.array([1.0, 0.5, 1.0])
+    P = np.array([1.0, 0.25, 2.0])
+    for k, xk in _golden_rows("fista_diag_momentum.txt"):
+        res = solver.fista(lambda v: A * v, lambda v: A * v, b, w, P, 0.5, max_iters=k)
+        assert res.iters == k
+        assert np.array_equal(res.x, np.array(xk)), (k, res.x, xk)
