@@ -93,6 +93,8 @@ typedef struct {
                                    is <= target (checked on the device every iteration) */
     int time_kernels;           /* 1: time one residual and one step launch per chunk with
                                    CUDA events (reported in the result) */
+    int kkt_check;              /* 1: after the loop, check the returned x in FP64 on the device
+                                   (wdb_theta_kkt; the kkt_* and *64 fields of the result) */
 } wdb_solve_params;
 
 typedef struct {
@@ -107,7 +109,20 @@ typedef struct {
     int timed_chunks;           /* number of chunks those means average over */
     int first_primal_below;     /* first k with primal(y^(k)) <= target_objective (0: none) */
     wdb_status status;
+    /* params.kkt_check = 1 (else NaN): FP64 check of the returned x, as wdb_theta_kkt */
+    double kkt_off, kkt_on;     /* KKT residuals of x (see wdb_kkt_result) */
+    double gap64, rel_gap64;    /* duality gap of x from FP64 r and g, and gap / E(x) */
 } wdb_solve_result;
+
+/* FP64 optimality check of an iterate (wdb_theta_kkt). */
+typedef struct {
+    double objective;           /* E(x) = 1/2 ||Theta_K x - x0||^2 + sum w|x| */
+    double gap, rel_gap;        /* E(x) - D(-s r), s = min(1, 1/max_i |g_i|/w_i); gap / E(x) */
+    double kkt_off;             /* max over x_i = 0 of (|g_i| - w_i)_+ / w_i */
+    double kkt_on;              /* max over x_i != 0 of |g_i + w_i sign(x_i)| / w_i */
+    double gmax;                /* max_i |g_i| / w_i */
+    long long support;          /* nonzero coefficients of x */
+} wdb_kkt_result;
 
 /* ---- Theta_K construction (Algorithm 2 + Sec. 3.7), FP64 on the device ----
  * For every subband b (3J+1 of them) the wavelet at position 0 is blurred with H and H^T
@@ -226,6 +241,16 @@ wdb_status wdb_solve_batch(int B, wdb_theta* const* th, const float* const* u_de
 wdb_status wdb_theta_objective(const wdb_theta* th, const float* x_dev, const float* x0_dev,
                                double lambda, const double* w_subband_host, void* stream,
                                double* E_host);
+
+/* FP64 check of the first-order optimality conditions of the l1 problem at a device iterate x
+ * (the conditions whose identification Sec. 4 discusses: |g_i| <= w_i everywhere and
+ * g_i = -w_i sign(x_i) on the support, g = Theta_K^T (Theta_K x - x0)): r and g are computed
+ * with FP64 taps and FP64 accumulation on the device from the FP32 x and x0 (N floats each),
+ * the residuals, objective and duality gap reduced in FP64. Residuals are relative to w_i
+ * (absolute where w_i = 0). Allocates 16 N bytes of FP64 workspace in the handle on first use.
+ * WDB_EINVAL for NULL arguments. Synchronises `stream`. */
+wdb_status wdb_theta_kkt(wdb_theta* th, const float* x_dev, const float* x0_dev, double lambda,
+                         const double* w_subband_host, void* stream, wdb_kkt_result* out);
 
 /* Exact operator A = H Psi for the FFT path (Algorithm 1 gradient, Sec. 5.2): cuFFT FP32
  * R2C/C2R for the solve, FP64 for the preconditioner diagonals (constant per subband, the

@@ -2,12 +2,19 @@
 FP64 oracle only, written to oracle/data/<name>.json.
 
     python -m oracle.workloads headline [--workers 8] [--iters 6000]
+    python -m oracle.workloads operators [--workers 8]
 
 Workload "headline": 1024 x 1024 synthetic image (Gaussian sigma = 3 on 31 x 31, noise 0.01),
 db4, J = 5, lambda = 1e-3, Theta_K with K = 30 N (weighted rule, Sec. 3.7), SPAI
 preconditioner (Sec. 4.3), FISTA (Algorithm 3) from x = 0.
 
-Recorded: E* bracket [best dual value, best primal value] of the run, the first iteration
+Workload "operators": the Theta_K operators of the 1024 x 1024 problems (Gaussian sigma = 3 on
+31 x 31 and the seeded 21 px motion line; db4, J = 5, K = 30 N, weighted rule) as the oracle
+builds them, with the SPAI table (Sec. 4.3), L and tau, written to
+oracle/data/theta_1024_<blur>_k30.npz; the full-size parity tests read them so that they do not
+rebuild the operator in every run.
+
+Recorded (headline): E* bracket [best dual value, best primal value] of the run, the first iteration
 whose primal value at y^(k) is within 1e-4 (relative) of E*, the same for the paper's
 criterion E - E* <= 1e-3 E(x^(0)) (Sec. 5.4), and the oracle's own time per iteration.
 
@@ -79,10 +86,38 @@ def headline(workers: int = 8, iters: int = 6000, kn: int = 30, kind: str = "spa
     return out
 
 
+def operator_record(blur: str, workers: int = 8, kn: int = 30, kind: str = "spai") -> dict:
+    """Theta_K of the 1024^2 `blur` problem with its SPAI table, L and tau (oracle only)."""
+    prob = synthetic.headline_problem(blur)
+    n, J = 1024, 5
+    ctx = mp.get_context("spawn")
+    with ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as pool:
+        th = theta.build_theta(prob.psf, n, n, "db4", J, kn * n * n, "weighted", pool=pool)
+    per = precond.theta_periods(th.lay, J)
+    Md, M2d = precond.diagonal_tables(th.mat, th.matT, th.lay, per)
+    Ptab = precond.preconditioner(Md, M2d, kind)
+    P = precond.expand(Ptab, th.lay, per)
+    A, At = solver.theta_ops(th)
+    L, pit = precond.power_iteration(lambda v: At(A(v)), P)
+    t = th.taps
+    return {"a": t.a.astype(np.int32), "b": t.b.astype(np.int32), "oy": t.oy.astype(np.int32),
+            "ox": t.ox.astype(np.int32), "v": t.v, "n": n, "levels": J, "K_requested": kn * n * n,
+            "K_eff": th.K_eff, "Md": Md, "M2d": M2d, "P_spai": Ptab, "L_spai": L, "tau_spai": precond.step_size(L),
+            "power_iters": pit}
+
+
 def main():
     name = sys.argv[1] if len(sys.argv) > 1 else "headline"
     workers = int(sys.argv[sys.argv.index("--workers") + 1]) if "--workers" in sys.argv else 8
     iters = int(sys.argv[sys.argv.index("--iters") + 1]) if "--iters" in sys.argv else 6000
+    if name == "operators":
+        os.makedirs(DATA, exist_ok=True)
+        for blur in ("gaussian", "motion"):
+            rec = operator_record(blur, workers)
+            path = os.path.join(DATA, f"theta_1024_{blur}_k30.npz")
+            np.savez_compressed(path, **rec)
+            print(path, len(rec["v"]), rec["K_eff"], rec["L_spai"], rec["tau_spai"])
+        return
     if name != "headline":
         raise SystemExit(f"unknown workload {name}")
     out = headline(workers, iters)

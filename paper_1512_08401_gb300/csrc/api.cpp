@@ -375,6 +375,28 @@ wdb_status wdb_theta_objective(const wdb_theta* thc, const float* x_dev, const f
     return theta_objective_dev(th, x_dev, x0_dev, th->d_w, st, E_host, nullptr);
 }
 
+wdb_status wdb_theta_kkt(wdb_theta* th, const float* x_dev, const float* x0_dev, double lambda,
+                         const double* w_subband_host, void* stream, wdb_kkt_result* out) {
+    if (!th || !x_dev || !x0_dev || !out) return set_error(WDB_EINVAL, "NULL argument");
+    if (!w_subband_host && !(lambda >= 0.0 && std::isfinite(lambda)))
+        return set_error(WDB_EINVAL, "lambda must be finite and >= 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WDB_TRY(theta_workspace_public(th, st));
+    std::vector<float> w(th->lay.S);
+    for (int b = 0; b < th->lay.S; ++b) w[b] = (float)(w_subband_host ? w_subband_host[b] : lambda);
+    WDB_CK(cudaMemcpyAsync(th->d_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, st));
+    Kkt64 k{};
+    WDB_TRY(theta_kkt64(th, x_dev, x0_dev, th->d_w, st, &k));
+    out->objective = k.objective;
+    out->gap = k.gap;
+    out->rel_gap = k.rel_gap;
+    out->kkt_off = k.kkt_off;
+    out->kkt_on = k.kkt_on;
+    out->gmax = k.gmax;
+    out->support = k.support;
+    return WDB_OK;
+}
+
 wdb_status wdb_fftop_create(const double* psf_host, int kh, int kw, int n_rows, int n_cols, const char* wavelet,
                             int levels, void* stream, wdb_fftop** out) {
     if (!out) return set_error(WDB_EINVAL, "out is NULL");

@@ -74,6 +74,25 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
     }
     WDB_TRY(work_enter(&th[0]->work, &th[0]->ev_in, &th[0]->ev_out, caller));
     cudaStream_t st = th[0]->work;
+    // Every return from here on makes the caller's stream wait for the work queued so far
+    // (so that a caller reusing its buffers after an error does not race with it) and
+    // releases the pinned flag; the successful path rejoins explicitly and checks for errors.
+    struct Rejoin {
+        cudaStream_t work, caller;
+        cudaEvent_t ev;
+        int* pinned = nullptr;
+        bool done = false;
+        ~Rejoin() {
+            if (!done) {
+                cudaEventRecord(ev, work);
+                cudaStreamWaitEvent(caller, ev, 0);
+            }
+            if (pinned) {
+                cudaStreamSynchronize(work);
+                cudaFreeHost(pinned);
+            }
+        }
+    } rejoin{st, caller, th[0]->ev_out};
     // per-problem set-up: preconditioner, workspace, x0 = Psi* u, weights, start, state
     std::vector<BatchProblem> hp(B);
     int buf_elems = 16;
@@ -139,6 +158,7 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
     WDB_CK(cudaMemcpyAsync(d_adj, ai.data(), sizeof(BatchItem) * ai.size(), cudaMemcpyHostToDevice, st));
     int* h_running = nullptr;
     WDB_CK(cudaMallocHost(&h_running, sizeof(int)));
+    rejoin.pinned = h_running;
     *h_running = B;
     BatchArgs F{}, A{};
     F.probs = A.probs = d_probs;
@@ -200,8 +220,10 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
         if (ce != cudaSuccess) s = cuda_error(ce, "batch results", __FILE__, __LINE__);
     }
-    cudaFreeHost(h_running);
-    if (s == WDB_OK) s = work_exit(st, th[0]->ev_out, caller);
+    if (s == WDB_OK) {
+        s = work_exit(st, th[0]->ev_out, caller);
+        rejoin.done = s == WDB_OK;
+    }
     const double ms = now_ms() - t0;
     for (int b = 0; b < B; ++b) {
         wdb_solve_result& r = res[b];
@@ -219,7 +241,9 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
         r.L_hat = th[b]->pc[params[b].precond].L_hat;
         r.solve_ms = ms;
         r.first_primal_below = q.hit_k;
+        r.kkt_off = r.kkt_on = r.gap64 = r.rel_gap64 = NAN;
         if (q.nan_flag || !std::isfinite(r.objective)) r.status = set_error(WDB_ENAN, "problem %d: NaN/Inf", b);
+        else if (q.diverged) r.status = set_error(WDB_EDIVERGED, "problem %d: objective diverged", b);
     }
     return s;
 }

@@ -546,13 +546,13 @@ wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int ou
     if constexpr (std::is_same<TIN, bf16>::value) {
         if (!flipped && CI >= 2 && CO >= 2 && CI <= kCMax && CO <= kCMax) {   // BF16 feature maps: tensor cores
             const bf16* wl = n->wlay + (size_t)layer * kMmaW;
-            static bool attr = false;
-            if (!attr) {
+            static unsigned long long attr = 0ull;
+            if (!done_on_device(&attr)) {
                 WDB_CK(cudaFuncSetAttribute(conv3x3_mma_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)kMmaSmem));
                 WDB_CK(cudaFuncSetAttribute(conv3x3_mma_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)kMmaSmem));
-                attr = true;
+                mark_on_device(&attr);
             }
             if (CI <= 16)
                 conv3x3_mma_kernel<16><<<grid, 256, kMmaSmem, st>>>(in, CI, CO, H, W, wl, bias, out_mode, out, relu,
@@ -569,13 +569,13 @@ wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int ou
         conv3x3_kernel<1, TIN><<<grid, 256, conv_smem(CI, 1), st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
                                                                      mask, residual);
     } else {
-        static bool attr = false;
-        if (!attr) {
+        static unsigned long long attr = 0ull;
+        if (!done_on_device(&attr)) {
             WDB_CK(cudaFuncSetAttribute(conv3x3_kernel<32, bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)conv_smem(32, 32)));
             WDB_CK(cudaFuncSetAttribute(conv3x3_kernel<32, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)conv_smem(32, 32)));
-            attr = true;
+            mark_on_device(&attr);
         }
         conv3x3_kernel<32, TIN><<<grid, 256, conv_smem(CI, 32), st>>>(in, CI, CO, H, W, w, bias, out_mode, out, relu,
                                                                        mask, residual);
@@ -588,12 +588,12 @@ wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int ou
 template <typename TIN>
 wdb_status wgrad(const wdb_cnn* n, int layer, const TIN* in, const float* dout, int B, int l, cudaStream_t st) {
     const ConvLayer& cl = n->convs[layer];
-    static bool attr = false;
+    static unsigned long long attr = 0ull;
     const size_t smem = sizeof(float) * (size_t)(kCMax * kHalo * kHalo + kCMax * kT * kT);
-    if (!attr) {
+    if (!done_on_device(&attr)) {
         WDB_CK(cudaFuncSetAttribute(wgrad_kernel<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         WDB_CK(cudaFuncSetAttribute(wgrad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
+        mark_on_device(&attr);
     }
     const int H = lvl_h(n, l), W = lvl_w(n, l);
     const int tiles = B * ((H + kT - 1) / kT) * ((W + kT - 1) / kT);

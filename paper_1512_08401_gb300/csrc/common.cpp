@@ -29,6 +29,22 @@ wdb_status cuda_error(cudaError_t e, const char* what, const char* file, int lin
 
 void count_launch(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+static int current_device_bit() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return -1;
+    return dev;
+}
+
+bool done_on_device(const unsigned long long* mask) {
+    const int d = current_device_bit();
+    return d >= 0 && ((__atomic_load_n(mask, __ATOMIC_ACQUIRE) >> d) & 1ull);
+}
+
+void mark_on_device(unsigned long long* mask) {
+    const int d = current_device_bit();
+    if (d >= 0) __atomic_fetch_or(mask, 1ull << d, __ATOMIC_ACQ_REL);
+}
+
 long long launches(int reset) {
     long long v = reset ? g_launches.exchange(0) : g_launches.load();
     return v;

@@ -91,6 +91,7 @@ __device__ __forceinline__ int phase_class(const SubbandDev& so, int py, int px)
 // ---------------------------------------------------------------------------------------
 // Gap bookkeeping shared by the Theta_K and FFT paths (runs in one thread of the last CTA).
 //   primal = 1/2 rr + wy; s = min(1, 1/max_i |g_i|/w_i); dual = -s x0r - s^2/2 rr
+// A NaN / Inf primal or gap, or a primal above 1e6 times the first one, stops the loop.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void finish_iteration(SolveState* st, double wy, double gmax) {
     const int k = st->k;
@@ -104,6 +105,10 @@ __device__ __forceinline__ void finish_iteration(SolveState* st, double wy, doub
     if (k == 1) st->first_primal = primal;
     if (!isfinite(primal) || !isfinite(gap)) {
         st->nan_flag = 1;
+        st->stop = 1;
+    } else if (k > 1 && primal > 1e6 * st->first_primal) {
+        // a step too long for the operator makes the objective grow geometrically
+        st->diverged = 1;
         st->stop = 1;
     }
     const bool check = (k % st->check_every) == 0 || k >= st->max_iters;

@@ -182,13 +182,13 @@ size_t idwt_smem(int L) {
 
 template <typename T>
 wdb_status ensure_smem_attr() {
-    static bool done = false;
-    if (!done) {
+    static unsigned long long done = 0ull;
+    if (!done_on_device(&done)) {
         WDB_CK(cudaFuncSetAttribute(dwt_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)dwt_smem<T>(kMaxL)));
         WDB_CK(cudaFuncSetAttribute(idwt_level_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)idwt_smem<T>(kMaxL)));
-        done = true;
+        mark_on_device(&done);
     }
     return WDB_OK;
 }

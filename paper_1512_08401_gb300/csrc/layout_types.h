@@ -33,6 +33,12 @@ wdb_status cuda_error(cudaError_t e, const char* what, const char* file, int lin
 // Count of kernels launched by the library (graph replays add their node counts).
 void count_launch(long long n = 1);
 
+// Per-device one-time set-up flags (cudaFuncSetAttribute acts on the current device only):
+// bit d of *mask is set once the set-up has been done on device d (devices >= 64 always redo
+// it, which is harmless).
+bool done_on_device(const unsigned long long* mask);
+void mark_on_device(unsigned long long* mask);
+
 // ---------------------------------------------------------------------------------------
 // Subband layout (Sec. 2): subband-planar, A_J first, then (0,1),(1,0),(1,1) for s=J..1
 // ---------------------------------------------------------------------------------------
@@ -69,7 +75,7 @@ struct SolveState {
     int gap_k;              // iteration of the last check
     int iters_done;         // k of the last computed x
     int nan_flag;
-    int pad;
+    int diverged;           // primal(y^(k)) > 1e6 primal(y^(1)): the iteration is not converging
     double first_primal;
     double target;          // > 0: stop once primal(y^(k)) <= target
     int hit_k;              // first k with primal <= target

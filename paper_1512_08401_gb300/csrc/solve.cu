@@ -288,6 +288,8 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     double Eobj = 0.0;
     long long sup = 0;
     WDB_TRY(theta_objective_dev(th, th->d_xs, th->d_x0, th->d_w, st, &Eobj, &sup));
+    Kkt64 kk{NAN, NAN, NAN, NAN, NAN, NAN, 0};
+    if (p->kkt_check) WDB_TRY(theta_kkt64(th, th->d_xs, th->d_x0, th->d_w, st, &kk));
     WDB_CK(cudaMemcpyAsync(x_out, th->d_xs, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
     WDB_TRY(work_exit(st, th->ev_out, caller));
     WDB_CK(cudaStreamSynchronize(st));
@@ -303,8 +305,15 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     res->ms_k2 = E.n_timed ? E.sum_k2 / E.n_timed : 0.0;
     res->timed_chunks = E.n_timed;
     res->first_primal_below = hs.hit_k;
+    res->kkt_off = kk.kkt_off;
+    res->kkt_on = kk.kkt_on;
+    res->gap64 = kk.gap;
+    res->rel_gap64 = kk.rel_gap;
     res->status = WDB_OK;
     if (hs.nan_flag || !std::isfinite(Eobj)) res->status = set_error(WDB_ENAN, "NaN/Inf in the objective");
+    else if (hs.diverged)
+        res->status = set_error(WDB_EDIVERGED, "objective %g at iteration %d, above 1e6 x its first value %g",
+                                hs.primal, hs.iters_done, hs.first_primal);
     res->solve_ms = now_ms() - t0;
     return res->status;
 }
@@ -690,8 +699,12 @@ wdb_status fft_solve(wdb_fftop* op, const float* u, float* x_out, const wdb_solv
     res->ms_k2 = E.n_timed ? E.sum_k2 / E.n_timed : 0.0;
     res->timed_chunks = E.n_timed;
     res->first_primal_below = hs.hit_k;
+    res->kkt_off = res->kkt_on = res->gap64 = res->rel_gap64 = NAN;
     res->status = WDB_OK;
     if (hs.nan_flag || !std::isfinite(Eobj)) res->status = set_error(WDB_ENAN, "NaN/Inf in the objective");
+    else if (hs.diverged)
+        res->status = set_error(WDB_EDIVERGED, "objective %g at iteration %d, above 1e6 x its first value %g",
+                                hs.primal, hs.iters_done, hs.first_primal);
     res->solve_ms = now_ms() - t0;
     return res->status;
 }

@@ -38,6 +38,13 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
 wdb_status theta_objective_dev(wdb_theta* th, const float* x, const float* x0, const float* w_dev, cudaStream_t st,
                                double* E, long long* support);
 wdb_status theta_workspace_public(wdb_theta* th, cudaStream_t st);
+struct Kkt64 {
+    double objective, gap, rel_gap, kkt_off, kkt_on, gmax;
+    long long support;
+};
+// FP64 r = Theta_K x - x0, g = Theta_K^T r, KKT residuals, objective and gap of x (kkt.cu)
+wdb_status theta_kkt64(wdb_theta* th, const float* x, const float* x0, const float* w_dev, cudaStream_t st,
+                       Kkt64* out);
 wdb_status fftop_create(const double* psf_host, int kh, int kw, const Layout& L, const Filters& f,
                         const char* wavelet, cudaStream_t st, wdb_fftop** out);
 void fftop_free(wdb_fftop* op);

@@ -1312,11 +1312,11 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
 // previous kernel of the stream drains (the kernel waits for that grid before its work)
 template <typename T, int EPI, bool SPLIT, bool SUP>
 wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl) {
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0ull;
+    if (!done_on_device(&attr)) {
         WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI, SPLIT, SUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     200 * 1024));
-        attr = true;
+        mark_on_device(&attr);
     }
     if (pdl) {
         cudaLaunchConfig_t cfg = {};
@@ -1349,10 +1349,10 @@ wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep
 
 template <int EPI>
 wdb_status launch_batch(const BatchArgs& B, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr = 0ull;
+    if (!done_on_device(&attr)) {
         WDB_CK(cudaFuncSetAttribute(tile_batch_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        attr = true;
+        mark_on_device(&attr);
     }
     tile_batch_kernel<EPI><<<B.grid, kTileThreads, B.smem_bytes, st>>>(B);
     count_launch();

@@ -152,4 +152,6 @@ struct wdb_theta {
     wdb::SolveState* d_state = nullptr;
     wdb::SolveState* h_state = nullptr;    // pinned
     long long ws_N = 0;
+    double *d_x64 = nullptr, *d_r64 = nullptr;   // FP64 check workspace (wdb_theta_kkt)
+    double* d_kkt_out = nullptr;
 };

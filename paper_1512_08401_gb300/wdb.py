@@ -48,14 +48,23 @@ class SolveParams(C.Structure):
     _fields_ = [("lam", C.c_double), ("w_subband_host", C.POINTER(C.c_double)), ("max_iters", C.c_int),
                 ("tol", C.c_double), ("precond", C.c_int), ("jacobi_eps", C.c_double),
                 ("check_every", C.c_int), ("x_init_dev", C.c_void_p), ("no_graph", C.c_int),
-                ("target_objective", C.c_double), ("time_kernels", C.c_int)]
+                ("target_objective", C.c_double), ("time_kernels", C.c_int), ("kkt_check", C.c_int)]
 
 
 class SolveResult(C.Structure):
     _fields_ = [("iters", C.c_int), ("objective", C.c_double), ("primal", C.c_double), ("gap", C.c_double),
                 ("rel_gap", C.c_double), ("support", C.c_longlong), ("tau", C.c_double),
                 ("L_hat", C.c_double), ("solve_ms", C.c_double), ("ms_k1", C.c_double), ("ms_k2", C.c_double),
-                ("timed_chunks", C.c_int), ("first_primal_below", C.c_int), ("status", C.c_int)]
+                ("timed_chunks", C.c_int), ("first_primal_below", C.c_int), ("status", C.c_int),
+                ("kkt_off", C.c_double), ("kkt_on", C.c_double), ("gap64", C.c_double), ("rel_gap64", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class KktResult(C.Structure):
+    _fields_ = [("objective", C.c_double), ("gap", C.c_double), ("rel_gap", C.c_double), ("kkt_off", C.c_double),
+                ("kkt_on", C.c_double), ("gmax", C.c_double), ("support", C.c_longlong)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -83,6 +92,7 @@ _SIGS = {
     "wdb_solve": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_solve_coeffs": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
     "wdb_theta_objective": (i32, [vp, vp, vp, f64, pd, vp, pd]),
+    "wdb_theta_kkt": (i32, [vp, vp, vp, f64, pd, vp, C.POINTER(KktResult)]),
     "wdb_solve_batch": (i32, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(SolveParams), vp,
                               C.POINTER(SolveResult)]),
     "wdb_fftop_create": (i32, [pd, i32, i32, i32, i32, C.c_char_p, i32, vp, C.POINTER(vp)]),
@@ -176,7 +186,7 @@ def wavelet_filters(name: str = "db4"):
 
 
 def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0, check_every=10, x_init=None,
-                w_subband=None, no_graph=False, target_objective=0.0, time_kernels=False):
+                w_subband=None, no_graph=False, target_objective=0.0, time_kernels=False, kkt_check=False):
     p = SolveParams()
     p.lam = float(lam)
     keep = None
@@ -192,6 +202,7 @@ def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0
     p.no_graph = 1 if no_graph else 0
     p.target_objective = float(target_objective)
     p.time_kernels = 1 if time_kernels else 0
+    p.kkt_check = 1 if kkt_check else 0
     return p, keep
 
 
@@ -296,6 +307,16 @@ class Theta:
         _check(lib().wdb_theta_objective(self._h, _dev(x, self.N), _dev(x0, self.N), float(lam), pw,
                                          _stream(stream), C.byref(E)))
         return E.value
+
+    def kkt(self, x, x0, lam=1e-3, w_subband=None, stream=None):
+        """FP64 optimality check of x (wdb_theta_kkt): objective, gap, KKT residuals."""
+        out = KktResult()
+        pw = None
+        if w_subband is not None:
+            w, pw = _f64(w_subband)
+        _check(lib().wdb_theta_kkt(self._h, _dev(x, self.N), _dev(x0, self.N), float(lam), pw, _stream(stream),
+                                   C.byref(out)))
+        return out.as_dict()
 
     def free(self):
         if self._h:
