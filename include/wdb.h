@@ -19,7 +19,9 @@
  *     the detail subbands with orientation (e_y, e_x) = (0,1), (1,0), (1,1), each
  *     n_rows/2^s x n_cols/2^s row-major. Subband index 0 is A_J; 3J+1 subbands in all.
  *   - wavelet names "db1" ... "db10": orthogonal Daubechies filters with p vanishing
- *     moments (2p taps), minimum phase, periodic separable 2-D transform (Sec. 2).
+ *     moments (2p taps), minimum phase; "sym1" ... "sym10": the same filter magnitudes with
+ *     the zeros chosen for the phase closest to linear (Symmlets; the paper's experiments use
+ *     Symmlet 6, Sec. 5). Periodic separable 2-D transform (Sec. 2).
  *   - PSF: host FP64 array of kh x kw (odd sizes), row-major; element (kh/2, kw/2) is the
  *     origin; (H u)[i,j] = sum_{a,b} psf[a+kh/2][b+kw/2] u[i-a][j-b] (indices mod n).
  *   - Pointers named *_dev are device pointers owned by the caller; they must stay valid
@@ -95,6 +97,8 @@ typedef struct {
                                    CUDA events (reported in the result) */
     int kkt_check;              /* 1: after the loop, check the returned x in FP64 on the device
                                    (wdb_theta_kkt; the kkt_* and *64 fields of the result) */
+    int ista;                   /* 1: drop the momentum step, y^(k+1) = x^(k) (ISTA, the baseline
+                                   of the paper's Sec. 5.3 comparison); 0: Algorithm 3 */
 } wdb_solve_params;
 
 typedef struct {
@@ -118,7 +122,7 @@ typedef struct {
 typedef struct {
     double objective;           /* E(x) = 1/2 ||Theta_K x - x0||^2 + sum w|x| */
     double gap, rel_gap;        /* E(x) - D(-s r), s = min(1, 1/max_i |g_i|/w_i); gap / E(x) */
-    double kkt_off;             /* max over x_i = 0 of (|g_i| - w_i)_+ / w_i */
+    double kkt_off;             /* max over all i of (|g_i| - w_i)_+ / w_i */
     double kkt_on;              /* max over x_i != 0 of |g_i + w_i sign(x_i)| / w_i */
     double gmax;                /* max_i |g_i| / w_i */
     long long support;          /* nonzero coefficients of x */

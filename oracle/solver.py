@@ -66,8 +66,9 @@ class FistaResult:
 
 
 def fista(apply_A, apply_At, b, w, P, tau, max_iters, tol=0.0, check_every=10,
-          x_init=None, record_every=0) -> FistaResult:
-    """Algorithm 3 (preconditioned accelerated proximal gradient).
+          x_init=None, record_every=0, momentum=True) -> FistaResult:
+    """Algorithm 3 (preconditioned accelerated proximal gradient); momentum=False drops the
+    extrapolation step (y^(k+1) = x^(k)): ISTA, the baseline curve of Sec. 5.3 / Fig. 8.
 
     apply_A / apply_At: the operator and its adjoint; b: data (x0 or u0); w, P: N-vectors of
     weights and preconditioner; tau: step. tol > 0 enables the gap check every
@@ -94,7 +95,7 @@ def fista(apply_A, apply_At, b, w, P, tau, max_iters, tol=0.0, check_every=10,
         x = soft(z, tau * w / P)
         if check and rel <= tol:
             break
-        beta = (k - 1) / (k + 2)
+        beta = (k - 1) / (k + 2) if momentum else 0.0
         y = x + beta * (x - x_prev)
         x_prev = x
     E = objective(apply_A(x) - b, x, w)

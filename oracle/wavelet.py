@@ -60,6 +60,78 @@ def daubechies_lowpass(p: int) -> np.ndarray:
     return h
 
 
+def _factor_roots(p: int):
+    """Roots of P(y) = sum_{k<p} C(p-1+k, k) y^k, grouped so that a choice keeps the filter
+    real: one entry per real root, one per complex-conjugate pair (the root with Im > 0)."""
+    pc = [comb(p - 1 + k, k) for k in range(p)]
+    yroots = np.roots(pc[::-1]) if p > 1 else np.array([])
+    groups = []
+    for y in yroots:
+        if abs(y.imag) <= 1e-10 * max(1.0, abs(y)):
+            groups.append((complex(y.real, 0.0), False))
+        elif y.imag > 0:
+            groups.append((complex(y), True))
+    return groups
+
+
+def _filter_from_zeros(p: int, zeros: list) -> np.ndarray:
+    """Real filter h with H(Z) Z^{L-1} = (Z+1)^p prod (Z - z), normalised to sum h = sqrt(2)."""
+    poly = np.array([1.0 + 0j])
+    for _ in range(p):
+        poly = np.convolve(poly, np.array([1.0, 1.0]))
+    for zr in zeros:
+        poly = np.convolve(poly, np.array([1.0, -zr]))
+    h = np.real(poly)
+    return h * (sqrt(2.0) / h.sum())
+
+
+def phase_nonlinearity(zeros: list, m: int = 2048) -> float:
+    """Squared deviation of the phase of H(e^{iw}) = c e^{-i(L-1)w} prod_j (e^{iw} - z_j) from
+    its least-squares line, on w_k = pi (k + 1/2) / m, k < m. The phase is summed factor by
+    factor (each factor's phase is continuous: no z_j lies on the unit circle except the
+    zeros at -1, whose factor has phase w/2 on [0, pi)); the linear term of e^{-i(L-1)w} does
+    not change the deviation."""
+    w = np.pi * (np.arange(m) + 0.5) / m
+    ph = np.zeros(m)
+    e = np.exp(1j * w)
+    for z in zeros:
+        ph += np.unwrap(np.angle(e - z))
+    A = np.stack([w, np.ones_like(w)], axis=1)
+    coef, *_ = np.linalg.lstsq(A, ph, rcond=None)
+    return float(np.sum((ph - A @ coef) ** 2))
+
+
+def symlet_lowpass(p: int) -> np.ndarray:
+    """Symlet with p vanishing moments (length 2p): the same |m0(w)|^2 as db<p> (Ten Lectures,
+    cited in Sec. 2, the 'least asymmetric' choice), factorised with, for every root group of
+    P, the zero inside or outside the unit circle, choosing the combination whose phase is
+    closest to linear (phase_nonlinearity). A filter and its time reverse tie (values within
+    1e-6 of each other count as a tie); the one whose energy centroid sum_k k h[k]^2 is
+    smaller is taken. Reading: the paper names Symmlet 6
+    (Sec. 5) without giving its coefficients or its selection rule."""
+    if p < 1:
+        raise ValueError("p must be >= 1")
+    groups = _factor_roots(p)
+    best = None
+    for mask in range(1 << len(groups)):
+        zeros = []
+        for gi, (y, cplx) in enumerate(groups):
+            b = 2.0 - 4.0 * y
+            disc = np.sqrt(b * b - 4.0 + 0j)
+            z1, z2 = (b + disc) / 2.0, (b - disc) / 2.0
+            zin, zout = (z1, z2) if abs(z1) < 1.0 else (z2, z1)
+            z = zout if (mask >> gi) & 1 else zin
+            zeros.append(z)
+            if cplx:
+                zeros.append(np.conj(z))
+        h = _filter_from_zeros(p, zeros)
+        nl = phase_nonlinearity([-1.0] * p + zeros)
+        cen = float(np.sum(np.arange(len(h)) * h * h))
+        if best is None or nl < best[0] * (1 - 1e-6) or (abs(nl - best[0]) <= 1e-6 * best[0] and cen < best[1]):
+            best = (nl, cen, h)
+    return best[2]
+
+
 def highpass_from_lowpass(h: np.ndarray) -> np.ndarray:
     """Quadrature mirror high-pass g[k] = (-1)^k h[L-1-k]."""
     L = len(h)
@@ -67,11 +139,14 @@ def highpass_from_lowpass(h: np.ndarray) -> np.ndarray:
 
 
 def wavelet_filters(name: str) -> tuple[np.ndarray, np.ndarray]:
-    """Filters for a wavelet name of the form 'db<p>' (p vanishing moments, 2p taps)."""
-    if not name.startswith("db"):
+    """Filters for 'db<p>' (minimum phase) or 'sym<p>' (least asymmetric), p vanishing
+    moments, 2p taps."""
+    if name.startswith("db"):
+        h = daubechies_lowpass(int(name[2:]))
+    elif name.startswith("sym"):
+        h = symlet_lowpass(int(name[3:]))
+    else:
         raise ValueError(f"unknown wavelet {name!r}")
-    p = int(name[2:])
-    h = daubechies_lowpass(p)
     return h, highpass_from_lowpass(h)
 
 

@@ -121,6 +121,7 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
         s0.tol = p.tol;
         s0.primal = s0.dual = s0.gap = s0.rel_gap = NAN;
         s0.target = p.target_objective > 0.0 ? p.target_objective : 0.0;
+        s0.ista = p.ista ? 1 : 0;
         WDB_CK(cudaMemcpyAsync(t->d_state, &s0, sizeof s0, cudaMemcpyHostToDevice, st));
         BatchProblem& q = hp[b];
         WDB_TRY(theta_batch_plans(t, st));

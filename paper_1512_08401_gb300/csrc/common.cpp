@@ -199,13 +199,125 @@ static wdb_status daubechies(int p, Filters* f) {
     return WDB_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Symlets: the same |m0(w)|^2 as db<p>, but for every real root of P, and every complex-
+// conjugate pair of roots, the zero of H(Z) may sit inside or outside the unit circle; the
+// combination whose phase arg H(e^{iw}) is closest to a straight line (least squares over
+// w_k = pi (k + 1/2) / 2048) is the least asymmetric filter. A filter and its time reverse
+// tie (deviations within 1e-6 of each other); the one with the smaller energy centroid
+// sum_k k h[k]^2 is kept.
+// ---------------------------------------------------------------------------------------
+// phase of prod_j (e^{iw} - z_j) summed factor by factor (each factor's phase is continuous
+// in w: no zero lies on the unit circle but the zeros at -1, whose factor's phase is w/2 on
+// [0, pi)), and its squared deviation from the least-squares line
+static double phase_deviation(const std::vector<cld>& zeros) {
+    constexpr int M = 2048;
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<long double> ph(M, 0.0L), w(M);
+    for (int k = 0; k < M; ++k) w[k] = pi * (k + 0.5L) / M;
+    for (const cld& z : zeros) {
+        long double prev = 0;
+        for (int k = 0; k < M; ++k) {
+            long double a = std::arg(std::polar(1.0L, w[k]) - z);
+            if (k > 0) {
+                while (a - prev > pi) a -= 2 * pi;
+                while (a - prev < -pi) a += 2 * pi;
+            }
+            ph[k] += a;
+            prev = a;
+        }
+    }
+    long double sw = 0, sp = 0, sww = 0, swp = 0;
+    for (int k = 0; k < M; ++k) {
+        sw += w[k];
+        sp += ph[k];
+        sww += w[k] * w[k];
+        swp += w[k] * ph[k];
+    }
+    const long double slope = (M * swp - sw * sp) / (M * sww - sw * sw);
+    const long double icpt = (sp - slope * sw) / M;
+    long double dev = 0;
+    for (int k = 0; k < M; ++k) {
+        const long double e = ph[k] - slope * w[k] - icpt;
+        dev += e * e;
+    }
+    return (double)dev;
+}
+
+static wdb_status symlet(int p, Filters* f) {
+    if (p < 1 || 2 * p > kMaxL) return set_error(WDB_EINVAL, "sym%d not supported (sym1..sym10)", p);
+    std::vector<long double> P_hi(p);
+    for (int k = 0; k < p; ++k) P_hi[p - 1 - k] = binom(p - 1 + k, k);
+    std::vector<cld> yr = poly_roots(P_hi);
+    struct Group {
+        cld zin, zout;
+        bool pair;
+    };
+    std::vector<Group> groups;
+    for (cld y : yr) {
+        const bool real = std::fabs(y.imag()) <= 1e-10L * std::max(1.0L, std::abs(y));
+        if (!real && y.imag() < 0) continue;   // the conjugate's group holds it
+        if (real) y = cld(y.real(), 0);
+        cld b = 2.0L - 4.0L * y;
+        cld disc = std::sqrt(b * b - 4.0L);
+        cld z1 = (b + disc) / 2.0L, z2 = (b - disc) / 2.0L;
+        if (std::abs(z1) < 1.0L) groups.push_back({z1, z2, !real});
+        else groups.push_back({z2, z1, !real});
+    }
+    double best_dev = 0, best_cen = 0;
+    std::vector<long double> best;
+    for (unsigned mask = 0; mask < (1u << groups.size()); ++mask) {
+        std::vector<cld> poly{cld(1)};
+        auto mul = [&](cld a1) {   // multiply by (Z + a1)
+            std::vector<cld> out(poly.size() + 1, cld(0));
+            for (size_t i = 0; i < poly.size(); ++i) {
+                out[i] += poly[i];
+                out[i + 1] += poly[i] * a1;
+            }
+            poly.swap(out);
+        };
+        std::vector<cld> zeros(p, cld(-1));
+        for (int i = 0; i < p; ++i) mul(1);
+        for (size_t gi = 0; gi < groups.size(); ++gi) {
+            const cld z = ((mask >> gi) & 1u) ? groups[gi].zout : groups[gi].zin;
+            mul(-z);
+            zeros.push_back(z);
+            if (groups[gi].pair) {
+                mul(-std::conj(z));
+                zeros.push_back(std::conj(z));
+            }
+        }
+        long double sum = 0;
+        for (auto& c : poly) sum += c.real();
+        std::vector<long double> h(poly.size());
+        for (size_t k = 0; k < poly.size(); ++k) h[k] = poly[k].real() * std::sqrt(2.0L) / sum;
+        const double dev = phase_deviation(zeros);
+        long double cen = 0;
+        for (size_t k = 0; k < h.size(); ++k) cen += (long double)k * h[k] * h[k];
+        const bool better = best.empty() || dev < best_dev * (1 - 1e-6) ||
+                            (std::fabs(dev - best_dev) <= 1e-6 * best_dev && (double)cen < best_cen);
+        if (better) {
+            best = h;
+            best_dev = dev;
+            best_cen = (double)cen;
+        }
+    }
+    f->L = 2 * p;
+    for (int k = 0; k < kMaxL; ++k) f->h[k] = f->g[k] = 0.0;
+    for (int k = 0; k < f->L; ++k) f->h[k] = (double)best[k];
+    for (int k = 0; k < f->L; ++k) f->g[k] = ((k & 1) ? -1.0 : 1.0) * f->h[f->L - 1 - k];
+    return WDB_OK;
+}
+
 wdb_status wavelet_filters(const char* name, Filters* out) {
     if (!name) return set_error(WDB_EINVAL, "wavelet name is NULL");
-    if (std::strncmp(name, "db", 2) != 0) return set_error(WDB_EINVAL, "unknown wavelet '%s'", name);
+    const bool db = std::strncmp(name, "db", 2) == 0, sym = std::strncmp(name, "sym", 3) == 0;
+    if (!db && !sym) return set_error(WDB_EINVAL, "unknown wavelet '%s'", name);
+    const char* num = name + (db ? 2 : 3);
     char* end = nullptr;
-    long p = std::strtol(name + 2, &end, 10);
-    if (end == name + 2 || *end != '\0') return set_error(WDB_EINVAL, "unknown wavelet '%s'", name);
-    return daubechies((int)p, out);
+    long p = std::strtol(num, &end, 10);
+    if (end == num || *end != '\0') return set_error(WDB_EINVAL, "unknown wavelet '%s'", name);
+    return db ? daubechies((int)p, out) : symlet((int)p, out);
 }
 
 }  // namespace wdb

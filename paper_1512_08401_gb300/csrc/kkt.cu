@@ -2,9 +2,9 @@
 // (Eq. l1problemThetaApprox): r = Theta_K x - x0 and g = Theta_K^T r with FP64 taps and FP64
 // accumulation (the tile engine's FP64 instances), then, reduced in FP64,
 //   * the first-order (KKT) conditions of the l1 problem, whose violation the support
-//     identification discussion of Sec. 4 measures: off the support |g_i| <= w_i, on the
+//     identification discussion of Sec. 4 measures: |g_i| <= w_i everywhere, and on the
 //     support g_i = -w_i sign(x_i). Reported as
-//       kkt_off = max_{x_i = 0}  (|g_i| - w_i)_+ / w_i,
+//       kkt_off = max_i          (|g_i| - w_i)_+ / w_i,
 //       kkt_on  = max_{x_i != 0} |g_i + w_i sign(x_i)| / w_i
 //     (absolute values where w_i = 0);
 //   * the objective E(x) = 1/2||r||^2 + sum w|x| and the duality gap of x with the scaled
@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(kVB) kkt64_kernel(SubbandArgs A, const float* 
             const float xv = x[i];
             const double ag = fabs(gv);
             const double sc = wv > 0.0 ? 1.0 / wv : 1.0;
-            if (xv == 0.f) off = fmax(off, fmax(ag - wv, 0.0) * sc);
-            else on = fmax(on, fabs(gv + (xv > 0.f ? wv : -wv)) * sc);
+            off = fmax(off, fmax(ag - wv, 0.0) * sc);
+            if (xv != 0.f) on = fmax(on, fabs(gv + (xv > 0.f ? wv : -wv)) * sc);
             gm = fmax(gm, wv > 0.0 ? ag / wv : (ag > 0.0 ? DBL_MAX : 0.0));
         }
         __syncthreads();

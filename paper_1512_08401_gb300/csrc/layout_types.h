@@ -79,7 +79,7 @@ struct SolveState {
     double first_primal;
     double target;          // > 0: stop once primal(y^(k)) <= target
     int hit_k;              // first k with primal <= target
-    int pad2;
+    int ista;               // 1: no momentum step (y^(k+1) = x^(k)): ISTA
     double scratch[8];      // free slots for one-off reductions
 };
 

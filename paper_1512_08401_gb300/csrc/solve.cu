@@ -61,6 +61,7 @@ SolveState init_state(const wdb_solve_params* p, int m) {
     s.tol = p->tol;
     s.primal = s.dual = s.gap = s.rel_gap = NAN;
     s.target = p->target_objective > 0.0 ? p->target_objective : 0.0;
+    s.ista = p->ista ? 1 : 0;
     return s;
 }
 

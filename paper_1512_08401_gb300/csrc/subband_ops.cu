@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kVB) fft_step(SubbandArgs A, const float* __re
     if (*(volatile int*)&st->stop) return;
     __shared__ int s_o;
     const int k = st->k;
-    const float beta = (float)(k - 1) / (float)(k + 2);
+    const float beta = st->ista ? 0.f : (float)(k - 1) / (float)(k + 2);
     float ws = 0.f, wc = 0.f, gm = 0.f;
     for (int vb = blockIdx.x; vb < A.nvb; vb += gridDim.x) {
         if (threadIdx.x == 0) s_o = find_subband(A.vb_start, A.S, vb);

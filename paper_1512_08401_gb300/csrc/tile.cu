@@ -1043,7 +1043,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
     float beta = 0.f;
     if (EPI == kK2) {
         const int k = ep.st->k;
-        beta = (float)(k - 1) / (float)(k + 2);
+        beta = ep.st->ista ? 0.f : (float)(k - 1) / (float)(k + 2);
     }
     // work items come from a queue, heaviest first
     __shared__ int s_next;
@@ -1253,7 +1253,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
             float beta = 0.f;
             if (EPI == kK2) {
                 const int k = P.st->k;
-                beta = (float)(k - 1) / (float)(k + 2);
+                beta = P.st->ista ? 0.f : (float)(k - 1) / (float)(k + 2);
             }
             epilogue<float, EPI>(w, so, tm, acc, (EPI == kK1) ? P.r : nullptr, ep, beta, pt);
             flush_partials<EPI>(pt, P.sums, red_d);

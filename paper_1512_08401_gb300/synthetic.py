@@ -21,6 +21,8 @@ PSFs:
   * gaussian(sigma, k): exp(-(a^2+b^2)/(2 sigma^2)) on a k x k support, sum 1
   * motion_line(length, angle): points t (cos a, sin a), t in [-(L-1)/2, (L-1)/2] in steps
     of 1/8 px, bilinearly splatted into an L x L grid, sum 1
+  * the five families of the paper's Sec. 5 / Table 3 (paper_blur): Gaussian, skewed
+    Gaussian, spline motion blur, Airy pattern, defocus disk
 """
 from __future__ import annotations
 
@@ -62,6 +64,120 @@ def motion_line_psf(length: int, angle: float) -> np.ndarray:
                 if 0 <= yy < length and 0 <= xx < length and wy * wx > 0:
                     h[yy, xx] += wy * wx
     return h / h.sum()
+
+
+def skewed_gaussian_psf(sigma: float, k: int | None = None) -> np.ndarray:
+    """The paper's anisotropic ('skewed') Gaussian (Sec. 5): exp(-t1^2/(2 s^2) - t2^2/(2 s^2))
+    for t1 >= 0 and exp(-4 t1^2/(2 s^2) - t2^2/(2 s^2)) otherwise. Readings: t1 is the row
+    offset and t2 the column offset, in pixels; support k = 2 ceil(3 s) + 1; sum 1."""
+    k = 2 * int(np.ceil(3 * sigma)) + 1 if k is None else k
+    c = k // 2
+    t = np.arange(-c, c + 1, dtype=np.float64)
+    t1, t2 = t[:, None], t[None, :]
+    h = np.where(t1 >= 0, np.exp(-t1 ** 2 / (2 * sigma ** 2)), np.exp(-4 * t1 ** 2 / (2 * sigma ** 2)))
+    h = h * np.exp(-t2 ** 2 / (2 * sigma ** 2))
+    return h / h.sum()
+
+
+def spline_motion_psf(rng: np.random.Generator, points: int = 5, sigma1: float = 8.0,
+                      sigma2: float = 1.0) -> np.ndarray:
+    """The paper's motion blur (Sec. 5): `points` points drawn from N(0, sigma1^2 I), joined by
+    a cubic spline, the curve blurred by a Gaussian of standard deviation sigma2. Readings:
+    the spline is the natural cubic spline through the points in drawing order, parametrised
+    by the point index; the curve is sampled at 1/256 of a parameter step, each sample
+    splatted bilinearly with a weight equal to its arc length; the curve is centred on its
+    arc-length centroid; the support is the odd square holding the curve plus 3 sigma2."""
+    pts = rng.normal(0.0, sigma1, size=(points, 2))
+    t = np.arange(points, dtype=np.float64)
+    # natural cubic spline, second derivatives from the tridiagonal system
+    n = points - 1
+    M = np.zeros((points, 2))
+    if n >= 2:
+        A = np.zeros((n - 1, n - 1))
+        rhs = np.zeros((n - 1, 2))
+        for i in range(1, n):
+            A[i - 1, i - 1] = 4.0
+            if i > 1:
+                A[i - 1, i - 2] = 1.0
+            if i < n - 1:
+                A[i - 1, i] = 1.0
+            rhs[i - 1] = 6.0 * (pts[i + 1] - 2 * pts[i] + pts[i - 1])
+        M[1:n] = np.linalg.solve(A, rhs)
+    ts = np.arange(0, n * 256 + 1) / 256.0
+    seg = np.minimum(ts.astype(int), n - 1)
+    u = ts - seg
+    P0, P1, M0, M1 = pts[seg], pts[seg + 1], M[seg], M[seg + 1]
+    u2 = u[:, None]
+    curve = ((1 - u2) * P0 + u2 * P1 + ((1 - u2) ** 3 - (1 - u2)) * M0 / 6.0 + (u2 ** 3 - u2) * M1 / 6.0)
+    d = np.linalg.norm(np.diff(curve, axis=0), axis=1)
+    wts = np.concatenate([[d[0] / 2], (d[:-1] + d[1:]) / 2, [d[-1] / 2]])
+    curve = curve - (wts[:, None] * curve).sum(0) / wts.sum()
+    ext = int(np.ceil(np.abs(curve).max() + 3 * sigma2)) + 1
+    k = 2 * ext + 1
+    img = np.zeros((k, k))
+    for (y, x), wv in zip(curve + ext, wts):
+        y0, x0 = int(np.floor(y)), int(np.floor(x))
+        fy, fx = y - y0, x - x0
+        img[y0, x0] += wv * (1 - fy) * (1 - fx)
+        img[y0 + 1, x0] += wv * fy * (1 - fx)
+        img[y0, x0 + 1] += wv * (1 - fy) * fx
+        img[y0 + 1, x0 + 1] += wv * fy * fx
+    g = gaussian_psf(sigma2, 2 * int(np.ceil(3 * sigma2)) + 1)
+    gc = g.shape[0] // 2
+    out = np.zeros_like(img)
+    for a in range(g.shape[0]):
+        for b in range(g.shape[1]):
+            sh = np.roll(np.roll(img, a - gc, axis=0), b - gc, axis=1)
+            out += g[a, b] * sh
+    return out / out.sum()
+
+
+def airy_psf(sigma: float) -> np.ndarray:
+    """Airy pattern (2 J1(x)/x)^2 (Sec. 5, Table 3), x = r / a. Reading: the width parameter
+    sigma is the standard deviation of the Gaussian that best matches the central lobe
+    (a = 0.7555 sigma, first dark ring at r = 2.895 sigma); support 2 ceil(3 * 2.895 sigma) + 1
+    (three rings); each pixel averages 4 x 4 sub-samples; sum 1."""
+    from scipy.special import j1
+    a = 0.7555 * sigma
+    c = int(np.ceil(3 * 2.895 * sigma))
+    sub = (np.arange(4) + 0.5) / 4 - 0.5
+    t = np.arange(-c, c + 1, dtype=np.float64)
+    yy = (t[:, None, None, None] + sub[None, None, :, None])
+    xx = (t[None, :, None, None] + sub[None, None, None, :])
+    x = np.sqrt(yy ** 2 + xx ** 2) / a
+    with np.errstate(invalid="ignore", divide="ignore"):
+        v = np.where(x > 1e-12, (2 * j1(x) / np.where(x > 1e-12, x, 1.0)) ** 2, 1.0)
+    h = v.mean(axis=(2, 3))
+    return h / h.sum()
+
+
+def defocus_psf(sigma: float) -> np.ndarray:
+    """Defocus blur (Sec. 5, Table 3): the uniform disk of radius sigma (reading), each pixel
+    weighted by the fraction of its 8 x 8 sub-samples inside the disk; sum 1."""
+    c = int(np.ceil(sigma)) + 1
+    sub = (np.arange(8) + 0.5) / 8 - 0.5
+    t = np.arange(-c, c + 1, dtype=np.float64)
+    yy = t[:, None, None, None] + sub[None, None, :, None]
+    xx = t[None, :, None, None] + sub[None, None, None, :]
+    h = (yy ** 2 + xx ** 2 <= sigma ** 2).mean(axis=(2, 3))
+    return h / h.sum()
+
+
+def paper_blur(family: str, width: float, seed: int = 0) -> np.ndarray:
+    """One of the five blur families of the paper's Table 3 at width 2.5 or 5 (sigma)."""
+    if family == "gaussian":
+        return gaussian_psf(width, 2 * int(np.ceil(3 * width)) + 1)
+    if family == "skewed":
+        return skewed_gaussian_psf(width)
+    if family == "motion":
+        # the paper's motion blur has sigma1 = 8 at its one stated size; the two widths of
+        # Table 3 scale it by width / 5 (reading)
+        return spline_motion_psf(rng_for(5, seed), sigma1=8.0 * width / 5.0)
+    if family == "airy":
+        return airy_psf(width)
+    if family == "defocus":
+        return defocus_psf(width)
+    raise ValueError(family)
 
 
 def clean_image(n_rows: int, n_cols: int, rng: np.random.Generator) -> np.ndarray:

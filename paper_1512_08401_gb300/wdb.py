@@ -48,7 +48,8 @@ class SolveParams(C.Structure):
     _fields_ = [("lam", C.c_double), ("w_subband_host", C.POINTER(C.c_double)), ("max_iters", C.c_int),
                 ("tol", C.c_double), ("precond", C.c_int), ("jacobi_eps", C.c_double),
                 ("check_every", C.c_int), ("x_init_dev", C.c_void_p), ("no_graph", C.c_int),
-                ("target_objective", C.c_double), ("time_kernels", C.c_int), ("kkt_check", C.c_int)]
+                ("target_objective", C.c_double), ("time_kernels", C.c_int), ("kkt_check", C.c_int),
+                ("ista", C.c_int)]
 
 
 class SolveResult(C.Structure):
@@ -186,7 +187,8 @@ def wavelet_filters(name: str = "db4"):
 
 
 def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0, check_every=10, x_init=None,
-                w_subband=None, no_graph=False, target_objective=0.0, time_kernels=False, kkt_check=False):
+                w_subband=None, no_graph=False, target_objective=0.0, time_kernels=False, kkt_check=False,
+                ista=False):
     p = SolveParams()
     p.lam = float(lam)
     keep = None
@@ -203,6 +205,7 @@ def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0
     p.target_objective = float(target_objective)
     p.time_kernels = 1 if time_kernels else 0
     p.kkt_check = 1 if kkt_check else 0
+    p.ista = 1 if ista else 0
     return p, keep
 
 

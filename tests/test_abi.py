@@ -35,12 +35,22 @@ def test_filters_derived_independently_match_oracle(wdb):
         assert np.abs(g - highpass_from_lowpass(ref)).max() < 1e-14
 
 
+def test_symlets_derived_independently_match_oracle(wdb):
+    from oracle.wavelet import symlet_lowpass
+    for p in range(1, 11):
+        h, g = wdb.wavelet_filters(f"sym{p}")
+        ref = symlet_lowpass(p)
+        assert np.abs(h - ref).max() < 1e-13, p
+        assert np.abs(g - highpass_from_lowpass(ref)).max() < 1e-13, p
+
+
 @pytest.mark.parametrize("kwargs,msg", [
     (dict(psf=np.ones((4, 5)) / 20), "odd"),
     (dict(psf=np.ones((65, 3)) / 195), "larger"),
     (dict(n=100), "divisible"),
     (dict(K=-1), "K"),
-    (dict(wavelet="sym6"), "wavelet"),
+    (dict(wavelet="coif3"), "wavelet"),
+    (dict(wavelet="sym11"), "sym"),
     (dict(wavelet="db11"), "db"),
     (dict(levels=0), "levels"),
 ])

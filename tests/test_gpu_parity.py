@@ -49,17 +49,19 @@ def rel_max(a, b):
 # wavelet transforms
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("n_rows,n_cols,J", [(64, 64, 3), (48, 80, 3), (128, 128, 4), (16, 16, 4), (32, 64, 5)])
-def test_dwt_idwt_parity(wdb, n_rows, n_cols, J):
+@pytest.mark.parametrize("n_rows,n_cols,J,wname", [(64, 64, 3, "db4"), (48, 80, 3, "db4"), (128, 128, 4, "db4"),
+                                                    (16, 16, 4, "db4"), (32, 64, 5, "db4"), (256, 256, 6, "sym6"),
+                                                    (64, 128, 4, "sym6")])
+def test_dwt_idwt_parity(wdb, n_rows, n_cols, J, wname):
     rng = np.random.default_rng(11)
     u = rng.standard_normal((n_rows, n_cols))
     c = torch.zeros(n_rows * n_cols, device="cuda")
-    wdb.dwt(dev(u), c, n_rows, n_cols, "db4", J)
-    ref = wavelet.dwt2(u, "db4", J)
+    wdb.dwt(dev(u), c, n_rows, n_cols, wname, J)
+    ref = wavelet.dwt2(u, wname, J)
     assert rel_max(host(c), ref) < 2e-6
     img = torch.zeros_like(c)
-    wdb.idwt(dev(ref), img, n_rows, n_cols, "db4", J)
-    assert rel_max(host(img), wavelet.idwt2(ref, n_rows, n_cols, "db4", J).ravel()) < 2e-6
+    wdb.idwt(dev(ref), img, n_rows, n_cols, wname, J)
+    assert rel_max(host(img), wavelet.idwt2(ref, n_rows, n_cols, wname, J).ravel()) < 2e-6
 
 
 # ---------------------------------------------------------------------------------------
@@ -373,6 +375,49 @@ def test_fft_path_trajectory_parity(wdb, kind):
     op.set_precond(kind, Psb, tau)
     x = torch.zeros(nr * nc, device="cuda")
     r = op.solve(dev(u0), x, lam=lam, max_iters=100, precond=kind)
+    xg = host(x)
+    assert np.linalg.norm(xg - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    assert abs(r["objective"] - ref.objective) <= 1e-5 * ref.objective
+
+
+@pytest.mark.parametrize("kind", ["none", "spai"])
+def test_ista_trajectory_parity_128(wdb, kind):
+    """ISTA (ista = 1: no momentum step), the baseline of the paper's Sec. 5.3 comparison,
+    against the oracle's iteration with momentum off."""
+    prob = synthetic.small_problem()
+    n, J, lam = 128, 4, prob.lam
+    case = build_case(prob.psf, n, n, J, 30 * n * n, prob.u0)
+    Ptab, P, tau, _ = precond_and_step(case, kind)
+    A, At = solver.theta_ops(case.th)
+    ref = solver.fista(A, At, case.x0, np.full(n * n, lam), P, tau, 150, momentum=False)
+    g = gpu_from_oracle(wdb, case, n, n, J)
+    g.set_precond(kind, Ptab, tau)
+    x = torch.zeros(n * n, device="cuda")
+    r = g.solve_coeffs(dev(case.x0), x, lam=lam, max_iters=150, tol=0.0, precond=kind, ista=True)
+    xg = host(x)
+    assert r["iters"] == 150
+    assert np.linalg.norm(xg - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
+    assert abs(r["objective"] - ref.objective) <= 1e-5 * ref.objective
+    # and it is not FISTA: the accelerated iterate differs
+    fis = solver.fista(A, At, case.x0, np.full(n * n, lam), P, tau, 150)
+    assert np.linalg.norm(fis.x - ref.x) > 1e-3 * np.linalg.norm(ref.x)
+
+
+def test_fft_path_ista_parity(wdb):
+    psf, nr, nc, J = CASES["gauss64"]
+    rng = np.random.default_rng(16)
+    u0 = synthetic.blur_fft(synthetic.clean_image(nr, nc, rng), psf) + 0.01 * rng.standard_normal((nr, nc))
+    lam = 1e-3
+    lay = wavelet.layout(nr, nc, J)
+    A, At = solver.exact_ops(psf, nr, nc, "db4", J)
+    P = np.ones(nr * nc)
+    L, _ = precond.power_iteration(lambda v: At(A(v)), P)
+    tau = precond.step_size(L)
+    ref = solver.fista(A, At, u0.ravel(), np.full(nr * nc, lam), P, tau, 80, momentum=False)
+    op = wdb.FFTOp(psf, nr, nc, "db4", J)
+    op.set_precond("none", np.ones(len(lay)), tau)
+    x = torch.zeros(nr * nc, device="cuda")
+    r = op.solve(dev(u0), x, lam=lam, max_iters=80, precond="none", ista=True)
     xg = host(x)
     assert np.linalg.norm(xg - ref.x) <= 1e-5 * np.linalg.norm(ref.x)
     assert abs(r["objective"] - ref.objective) <= 1e-5 * ref.objective

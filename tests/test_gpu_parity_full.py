@@ -69,29 +69,30 @@ def check_apply(wdb, g, mat, matT, N, seed):
 # ---------------------------------------------------------------------------------------
 
 DEEP = {
-    "gauss256_j5": (lambda: synthetic.gaussian_psf(2.0, 15), 256, 5),
-    "motion256_j5": (lambda: synthetic.motion_line_psf(11, 0.6), 256, 5),
-    "gauss512_j6": (lambda: synthetic.gaussian_psf(2.0, 13), 512, 6),
-    "motion512_j6": (lambda: synthetic.motion_line_psf(9, 1.1), 512, 6),
+    "gauss256_j5": (lambda: synthetic.gaussian_psf(2.0, 15), 256, 5, "db4"),
+    "motion256_j5": (lambda: synthetic.motion_line_psf(11, 0.6), 256, 5, "db4"),
+    "gauss512_j6": (lambda: synthetic.gaussian_psf(2.0, 13), 512, 6, "db4"),
+    "motion512_j6": (lambda: synthetic.motion_line_psf(9, 1.1), 512, 6, "db4"),
+    "skewed256_sym6_j6": (lambda: synthetic.skewed_gaussian_psf(2.5), 256, 6, "sym6"),
 }
 _deep_cache = {}
 
 
 def deep_case(name):
     if name not in _deep_cache:
-        mk, n, J = DEEP[name]
+        mk, n, J, wname = DEEP[name]
         psf = mk()
         rng = np.random.default_rng(21)
         u0 = synthetic.blur_fft(synthetic.clean_image(n, n, rng), psf) + 0.01 * rng.standard_normal((n, n))
-        _deep_cache[name] = (build_case(psf, n, n, J, 30 * n * n, u0), n, J)
+        _deep_cache[name] = (build_case(psf, n, n, J, 30 * n * n, u0, wavelet_name=wname), n, J, wname)
     return _deep_cache[name]
 
 
 @pytest.mark.parametrize("name", list(DEEP))
 def test_apply_parity_deep_levels_all_plans(wdb, name):
-    case, n, J = deep_case(name)
+    case, n, J, wname = deep_case(name)
     a, b, oy, ox, v = taps_arrays(case.th)
-    g = wdb.Theta.from_taps(n, n, "db4", J, a, b, oy, ox, v)
+    g = wdb.Theta.from_taps(n, n, wname, J, a, b, oy, ox, v)
     assert g.info.K_eff == case.th.K_eff
     assert g.info.plan_tuned == 1
     check_apply(wdb, g, case.th.mat, case.th.matT, n * n, 1)           # autotuned plan
@@ -103,14 +104,14 @@ def test_apply_parity_deep_levels_all_plans(wdb, name):
     g.free()
 
 
-@pytest.mark.parametrize("name", ["gauss512_j6", "motion256_j5"])
+@pytest.mark.parametrize("name", ["gauss512_j6", "motion256_j5", "skewed256_sym6_j6"])
 def test_fista_trajectory_parity_deep_levels(wdb, name):
-    case, n, J = deep_case(name)
+    case, n, J, wname = deep_case(name)
     Ptab, P, tau, _ = precond_and_step(case, "spai")
     lam = 1e-3
     ref = fista(case, lam, P, tau, 40)
     a, b, oy, ox, v = taps_arrays(case.th)
-    g = wdb.Theta.from_taps(n, n, "db4", J, a, b, oy, ox, v)
+    g = wdb.Theta.from_taps(n, n, wname, J, a, b, oy, ox, v)
     g.set_precond("spai", Ptab, tau)
     x = torch.zeros(n * n, device="cuda")
     r = g.solve_coeffs(dev(case.x0), x, lam=lam, max_iters=40, tol=0.0, precond="spai")

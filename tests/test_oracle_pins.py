@@ -57,6 +57,62 @@ def test_db4_minimum_phase():
     assert np.sum(h[:4] ** 2) > 0.9
 
 
+@pytest.mark.parametrize("p", [2, 3, 4, 5, 6, 8, 10])
+def test_symlet_orthonormal_same_magnitude_as_db_and_more_linear_phase(p):
+    """Symmlets (the paper's Symmlet 6, Sec. 5): an orthonormal filter with p vanishing
+    moments whose magnitude response equals db<p>'s (the same |m0|^2 factorised with other
+    zeros), whose zeros are those of db<p> or their inverses, and whose phase is at least as
+    close to linear as db<p>'s (strictly closer from p = 4 on). A wrong zero selection, a lost
+    conjugate or a broken normalisation fails one of these."""
+    h = wavelet.symlet_lowpass(p)
+    d = wavelet.daubechies_lowpass(p)
+    g = wavelet.highpass_from_lowpass(h)
+    L = len(h)
+    assert L == 2 * p
+    for m in range(p):
+        s = sum(h[k] * h[k + 2 * m] for k in range(L - 2 * m))
+        assert abs(s - (1.0 if m == 0 else 0.0)) < 1e-13
+    assert abs(h.sum() - np.sqrt(2.0)) < 1e-14
+    k = np.arange(L, dtype=np.float64)
+    for m in range(p):
+        assert abs(np.sum(g * k ** m)) < 1e-12 * np.sum(np.abs(g) * k ** m)
+    w = np.linspace(0, np.pi, 257)
+    E = np.exp(-1j * np.outer(w, np.arange(L)))
+    assert np.abs(np.abs(E @ h) - np.abs(E @ d)).max() < 1e-12
+    def nontrivial_zeros(f):
+        # divide the p-fold zero at -1 out of H(Z) Z^{L-1} (synthetic division), then the rest
+        q = np.array(f, dtype=np.float64)
+        for _ in range(p):
+            q, r = np.polydiv(q, [1.0, 1.0])
+            assert abs(r[-1]) < 1e-10
+        return np.roots(q)
+    nz = nontrivial_zeros(h)
+    nd = nontrivial_zeros(d)
+    assert len(nz) == len(nd) == p - 1
+    for z in nz:
+        assert min(np.abs(nd - z).min(), np.abs(nd - 1 / z).min()) < 1e-4 * max(1.0, abs(z))
+    nl = lambda zeros: wavelet.phase_nonlinearity([-1.0] * p + list(zeros))
+    assert nl(nz) <= nl(nd) * (1 + 1e-9)
+    if p >= 4:
+        assert nl(nz) < 0.5 * nl(nd)
+
+
+def test_symlet_small_orders_are_daubechies():
+    """For p <= 3 P(y) has at most one root, so the only alternative factorisation is the
+    time reverse of db<p>: the Symmlet is db<p> (its reverse has the larger energy centroid)."""
+    for p in (1, 2, 3):
+        assert np.abs(wavelet.symlet_lowpass(p) - wavelet.daubechies_lowpass(p)).max() < 1e-14
+
+
+@pytest.mark.parametrize("J", [1, 3, 5])
+def test_symlet_dwt_perfect_reconstruction(J):
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((64, 96))
+    c = wavelet.dwt2(u, "sym6", J)
+    assert abs(np.linalg.norm(c) - np.linalg.norm(u)) < 1e-12 * np.linalg.norm(u)
+    assert np.abs(wavelet.idwt2(c, 64, 96, "sym6", J) - u).max() < 1e-12
+
+
 # ---------------------------------------------------------------------------------------
 # DWT (Sec. 2)
 # ---------------------------------------------------------------------------------------
@@ -465,4 +521,17 @@ def test_fista_momentum_schedule_hand_derived_trajectory():
     for k, xk in _golden_rows("fista_diag_momentum.txt"):
         res = solver.fista(lambda v: A * v, lambda v: A * v, b, w, P, 0.5, max_iters=k)
         assert res.iters == k
+        assert np.array_equal(res.x, np.array(xk)), (k, res.x, xk)
+
+
+def test_ista_hand_derived_trajectory():
+    """ISTA (momentum off) on the same diagonal problem: the hand-derived contraction
+    (tests/golden/ista_diag.txt). Any extrapolation left in, or a step applied to y instead
+    of x, changes x^(3)."""
+    A = np.array([1.0, 0.5, 1.0])
+    b = np.array([4.0, -3.0, 0.25])
+    w = np.array([1.0, 0.5, 1.0])
+    P = np.array([1.0, 0.25, 2.0])
+    for k, xk in _golden_rows("ista_diag.txt"):
+        res = solver.fista(lambda v: A * v, lambda v: A * v, b, w, P, 0.5, max_iters=k, momentum=False)
         assert np.array_equal(res.x, np.array(xk)), (k, res.x, xk)
