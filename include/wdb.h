@@ -283,12 +283,18 @@ wdb_status wdb_idwt(const float* coef_dev, float* img_dev, int n_rows, int n_col
  * locked-down memory pool, real-time paths where cudaMalloc and the synchronisation it may
  * imply are not allowed, or callers holding a capture or lock that an allocation would
  * break). Same result as wdb_dwt, but the intermediate approximations live in a file-scope
- * device array of 4 Mi floats (16 MiB) that every GPU loading the library keeps until the
- * process exits; images above 8 Mi - 2 pixels are rejected with WDB_EINVAL. The first call
- * on each device looks the array's device address up (make that first call before any
- * stream capture). All calls share the array: calls that overlap on the GPU (other streams,
- * other threads) race and must be serialised by the caller. No cudaMalloc, cudaFree or
- * allocating library routine is called. */
+ * device array of 4 Mi floats (16 MiB) that a GPU keeps until the process exits once the
+ * library's code has been loaded on it; images above 8 Mi - 2 pixels are rejected with
+ * WDB_EINVAL. The first call on each device looks the array's device address up, with that
+ * device current; under lazy module loading (CUDA_MODULE_LOADING=LAZY, PyTorch's default)
+ * that lookup is also what loads the module holding the array, which reserves its 16 MiB
+ * and may synchronise the device, so make the first call on every device during set-up,
+ * before any stream capture and outside any section that must not allocate. Later calls on
+ * that device allocate nothing. The looked-up address is kept for the life of the process:
+ * after a cudaDeviceReset of that device the function must not be called on it again. All
+ * calls share the array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller. No cudaMalloc, cudaFree or allocating library
+ * routine is called. */
 wdb_status wdb_dwt_noalloc(const float* img_dev, float* coef_dev, int n_rows, int n_cols,
                            const char* wavelet, int levels, void* stream);
 

@@ -382,11 +382,10 @@ wdb_status wdb_theta_kkt(wdb_theta* th, const float* x_dev, const float* x0_dev,
         return set_error(WDB_EINVAL, "lambda must be finite and >= 0");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     WDB_TRY(theta_workspace_public(th, st));
-    std::vector<float> w(th->lay.S);
-    for (int b = 0; b < th->lay.S; ++b) w[b] = (float)(w_subband_host ? w_subband_host[b] : lambda);
-    WDB_CK(cudaMemcpyAsync(th->d_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, st));
+    std::vector<double> w(th->lay.S);
+    for (int b = 0; b < th->lay.S; ++b) w[b] = w_subband_host ? w_subband_host[b] : lambda;
     Kkt64 k{};
-    WDB_TRY(theta_kkt64(th, x_dev, x0_dev, th->d_w, st, &k));
+    WDB_TRY(theta_kkt64(th, x_dev, x0_dev, w.data(), st, &k));
     out->objective = k.objective;
     out->gap = k.gap;
     out->rel_gap = k.rel_gap;

@@ -168,6 +168,183 @@ __global__ void __launch_bounds__(256) idwt_level_kernel(const T* __restrict__ c
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// FP32 levels for the filter lengths of the workloads (L = 8: db4, L = 12: sym6, and every
+// other even length up to 20), the filter taps compile-time constants of the unrolled loops:
+// 32 x 32 outputs per subband and CTA (input halo 1.2x instead of 1.4x), input rows read
+// as 8-byte column pairs split by column parity in shared memory, so that every pass reads
+// consecutive words across the lanes; each thread forms two outputs from one set of loads.
+// ---------------------------------------------------------------------------------------
+constexpr int kFT = 32;   // outputs per tile side (per subband)
+
+template <int L>
+__global__ void __launch_bounds__(256) dwt_level_fast(const float* __restrict__ in, int R, int C,
+                                                      float* __restrict__ outA, float* __restrict__ d01,
+                                                      float* __restrict__ d10, float* __restrict__ d11,
+                                                      FiltT<float> f) {
+    constexpr int IY = 2 * kFT + L - 2;       // input rows of the tile (with halo)
+    constexpr int PX = kFT + L / 2 - 1;       // column pairs of the tile (with halo)
+    __shared__ float s_ev[IY][PX + 1], s_od[IY][PX + 1];   // even / odd input columns
+    __shared__ float s_lo[IY][kFT], s_hi[IY][kFT];
+    const int oy0 = blockIdx.y * kFT, ox0 = blockIdx.x * kFT;
+    const int R2 = R >> 1, C2 = C >> 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // load: one warp per input row, one column pair per lane (C even: a pair never wraps)
+    for (int iy = warp; iy < IY; iy += 8) {
+        int gy = 2 * oy0 + iy;
+        while (gy >= R) gy -= R;
+        const float* __restrict__ row = in + (size_t)gy * C;
+        for (int c = lane; c < PX; c += 32) {
+            int gx = 2 * (ox0 + c);
+            while (gx >= C) gx -= C;
+            const float2 v = *reinterpret_cast<const float2*>(row + gx);
+            s_ev[iy][c] = v.x;
+            s_od[iy][c] = v.y;
+        }
+    }
+    __syncthreads();
+    // along x: lo/hi[iy][j] = sum_k h/g[k] in[iy][2j + k]
+    for (int t = threadIdx.x; t < IY * kFT; t += 256) {
+        const int iy = t >> 5, j = t & 31;
+        float lo = 0.f, hi = 0.f;
+#pragma unroll
+        for (int m = 0; m < L / 2; ++m) {
+            const float e = s_ev[iy][j + m], o = s_od[iy][j + m];
+            lo = fmaf(f.h[2 * m], e, lo);
+            lo = fmaf(f.h[2 * m + 1], o, lo);
+            hi = fmaf(f.g[2 * m], e, hi);
+            hi = fmaf(f.g[2 * m + 1], o, hi);
+        }
+        s_lo[iy][j] = lo;
+        s_hi[iy][j] = hi;
+    }
+    __syncthreads();
+    // along y: output row i from rows 2i .. 2i + L - 1
+    for (int t = threadIdx.x; t < kFT * kFT; t += 256) {
+        const int i = t >> 5, j = t & 31;
+        const int oy = oy0 + i, ox = ox0 + j;
+        float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const float lo = s_lo[2 * i + k][j], hi = s_hi[2 * i + k][j];
+            ll = fmaf(f.h[k], lo, ll);
+            hl = fmaf(f.g[k], lo, hl);
+            lh = fmaf(f.h[k], hi, lh);
+            hh = fmaf(f.g[k], hi, hh);
+        }
+        if (oy < R2 && ox < C2) {
+            const size_t o = (size_t)oy * C2 + ox;
+            outA[o] = ll;
+            d01[o] = lh;
+            d10[o] = hl;
+            d11[o] = hh;
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) idwt_level_fast(const float* __restrict__ cA, const float* __restrict__ c01,
+                                                       const float* __restrict__ c10, const float* __restrict__ c11,
+                                                       int R2, int C2, float* __restrict__ out, FiltT<float> f) {
+    constexpr int H2 = L / 2;
+    constexpr int CY = kFT + H2 - 1, CX = kFT + H2 - 1;   // coefficient rows / cols with halo
+    __shared__ float sLL[CY][CX], sLH[CY][CX], sHL[CY][CX], sHH[CY][CX];
+    __shared__ float sLx[2 * kFT][CX], sHx[2 * kFT][CX];
+    const int cy0 = blockIdx.y * kFT, cx0 = blockIdx.x * kFT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int iy = warp; iy < CY; iy += 8) {
+        int gy = cy0 - H2 + 1 + iy;
+        while (gy < 0) gy += R2;
+        while (gy >= R2) gy -= R2;
+        const size_t r = (size_t)gy * C2;
+        for (int ix = lane; ix < CX; ix += 32) {
+            int gx = cx0 - H2 + 1 + ix;
+            while (gx < 0) gx += C2;
+            while (gx >= C2) gx -= C2;
+            sLL[iy][ix] = cA[r + gx];
+            sLH[iy][ix] = c01[r + gx];
+            sHL[iy][ix] = c10[r + gx];
+            sHH[iy][ix] = c11[r + gx];
+        }
+    }
+    __syncthreads();
+    // along y: rows 2i and 2i + 1 from coefficient rows i - m, m < L/2:
+    //   Lx[2i + p] = sum_m h[2m + p] LL[i - m] + g[2m + p] HL[i - m]   (Hx from LH, HH)
+    for (int t = threadIdx.x; t < kFT * CX; t += 256) {
+        const int i = t / CX, cx = t - i * CX;
+        float l0 = 0.f, l1 = 0.f, h0 = 0.f, h1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < H2; ++m) {
+            const int ci = i - m + H2 - 1;
+            const float ll = sLL[ci][cx], hl = sHL[ci][cx], lh = sLH[ci][cx], hh = sHH[ci][cx];
+            l0 = fmaf(f.h[2 * m], ll, fmaf(f.g[2 * m], hl, l0));
+            l1 = fmaf(f.h[2 * m + 1], ll, fmaf(f.g[2 * m + 1], hl, l1));
+            h0 = fmaf(f.h[2 * m], lh, fmaf(f.g[2 * m], hh, h0));
+            h1 = fmaf(f.h[2 * m + 1], lh, fmaf(f.g[2 * m + 1], hh, h1));
+        }
+        sLx[2 * i][cx] = l0;
+        sLx[2 * i + 1][cx] = l1;
+        sHx[2 * i][cx] = h0;
+        sHx[2 * i + 1][cx] = h1;
+    }
+    __syncthreads();
+    // along x: columns 2c and 2c + 1 from the same coefficient columns, one 8-byte store
+    const int R = 2 * R2, C = 2 * C2;
+    for (int t = threadIdx.x; t < 2 * kFT * kFT; t += 256) {
+        const int yl = t >> 5, c = t & 31;
+        const int y = 2 * cy0 + yl, xc = cx0 + c;
+        float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < H2; ++m) {
+            const float lx = sLx[yl][c - m + H2 - 1], hx = sHx[yl][c - m + H2 - 1];
+            o0 = fmaf(f.h[2 * m], lx, fmaf(f.g[2 * m], hx, o0));
+            o1 = fmaf(f.h[2 * m + 1], lx, fmaf(f.g[2 * m + 1], hx, o1));
+        }
+        if (y < R && xc < C2) *reinterpret_cast<float2*>(out + (size_t)y * C + 2 * xc) = make_float2(o0, o1);
+    }
+}
+
+template <int L>
+void dwt_fast_launch(const float* src, int R, int C, float* a, float* d01, float* d10, float* d11,
+                     const FiltT<float>& f, cudaStream_t st) {
+    dim3 grid((C / 2 + kFT - 1) / kFT, (R / 2 + kFT - 1) / kFT);
+    dwt_level_fast<L><<<grid, 256, 0, st>>>(src, R, C, a, d01, d10, d11, f);
+}
+
+template <int L>
+void idwt_fast_launch(const float* a, const float* d01, const float* d10, const float* d11, int R2, int C2,
+                      float* out, const FiltT<float>& f, cudaStream_t st) {
+    dim3 grid((C2 + kFT - 1) / kFT, (R2 + kFT - 1) / kFT);
+    idwt_level_fast<L><<<grid, 256, 0, st>>>(a, d01, d10, d11, R2, C2, out, f);
+}
+
+// FP32 level through the fast kernels (true) or not available for this filter length (false)
+bool dwt_level_f32(const float* src, int R, int C, float* a, float* d01, float* d10, float* d11,
+                   const FiltT<float>& f, cudaStream_t st) {
+    switch (f.L) {
+        case 2: dwt_fast_launch<2>(src, R, C, a, d01, d10, d11, f, st); return true;
+        case 4: dwt_fast_launch<4>(src, R, C, a, d01, d10, d11, f, st); return true;
+        case 6: dwt_fast_launch<6>(src, R, C, a, d01, d10, d11, f, st); return true;
+        case 8: dwt_fast_launch<8>(src, R, C, a, d01, d10, d11, f, st); return true;
+        case 10: dwt_fast_launch<10>(src, R, C, a, d01, d10, d11, f, st); return true;
+        case 12: dwt_fast_launch<12>(src, R, C, a, d01, d10, d11, f, st); return true;
+        default: return false;
+    }
+}
+
+bool idwt_level_f32(const float* a, const float* d01, const float* d10, const float* d11, int R2, int C2,
+                    float* out, const FiltT<float>& f, cudaStream_t st) {
+    switch (f.L) {
+        case 2: idwt_fast_launch<2>(a, d01, d10, d11, R2, C2, out, f, st); return true;
+        case 4: idwt_fast_launch<4>(a, d01, d10, d11, R2, C2, out, f, st); return true;
+        case 6: idwt_fast_launch<6>(a, d01, d10, d11, R2, C2, out, f, st); return true;
+        case 8: idwt_fast_launch<8>(a, d01, d10, d11, R2, C2, out, f, st); return true;
+        case 10: idwt_fast_launch<10>(a, d01, d10, d11, R2, C2, out, f, st); return true;
+        case 12: idwt_fast_launch<12>(a, d01, d10, d11, R2, C2, out, f, st); return true;
+        default: return false;
+    }
+}
+
 template <typename T>
 size_t dwt_smem(int L) {
     int IY = 2 * kTile + L - 2;
@@ -211,9 +388,15 @@ wdb_status dwt2(const T* img, T* coef, const Layout& Ly, const Filters& f, T* sc
         int base = 1 + 3 * (Ly.J - s);   // subband index of (0,1) at level s
         T* dst = (s == Ly.J) ? coef + Ly.sb[0].off : ((s & 1) ? bufA : bufB);
         int R2 = R / 2, C2 = C / 2;
-        dim3 grid((C2 + kTile - 1) / kTile, (R2 + kTile - 1) / kTile);
-        dwt_level_kernel<T><<<grid, 256, dwt_smem<T>(f.L), st>>>(
-            src, R, C, dst, coef + Ly.sb[base].off, coef + Ly.sb[base + 1].off, coef + Ly.sb[base + 2].off, ft);
+        bool fast = false;
+        if constexpr (sizeof(T) == 4)
+            fast = dwt_level_f32(src, R, C, dst, coef + Ly.sb[base].off, coef + Ly.sb[base + 1].off,
+                                 coef + Ly.sb[base + 2].off, ft, st);
+        if (!fast) {
+            dim3 grid((C2 + kTile - 1) / kTile, (R2 + kTile - 1) / kTile);
+            dwt_level_kernel<T><<<grid, 256, dwt_smem<T>(f.L), st>>>(
+                src, R, C, dst, coef + Ly.sb[base].off, coef + Ly.sb[base + 1].off, coef + Ly.sb[base + 2].off, ft);
+        }
         count_launch();
         WDB_CK(cudaGetLastError());
         src = dst;
@@ -235,9 +418,15 @@ wdb_status idwt2(const T* coef, T* img, const Layout& Ly, const Filters& f, T* s
         int base = 1 + 3 * (Ly.J - s);
         int R2 = Ly.n_rows >> s, C2 = Ly.n_cols >> s;
         T* dst = (s == 1) ? img : ((s & 1) ? bufA : bufB);
-        dim3 grid((C2 + kTile - 1) / kTile, (R2 + kTile - 1) / kTile);
-        idwt_level_kernel<T><<<grid, 256, idwt_smem<T>(f.L), st>>>(
-            src, coef + Ly.sb[base].off, coef + Ly.sb[base + 1].off, coef + Ly.sb[base + 2].off, R2, C2, dst, ft);
+        bool fast = false;
+        if constexpr (sizeof(T) == 4)
+            fast = idwt_level_f32(src, coef + Ly.sb[base].off, coef + Ly.sb[base + 1].off, coef + Ly.sb[base + 2].off,
+                                  R2, C2, dst, ft, st);
+        if (!fast) {
+            dim3 grid((C2 + kTile - 1) / kTile, (R2 + kTile - 1) / kTile);
+            idwt_level_kernel<T><<<grid, 256, idwt_smem<T>(f.L), st>>>(
+                src, coef + Ly.sb[base].off, coef + Ly.sb[base + 1].off, coef + Ly.sb[base + 2].off, R2, C2, dst, ft);
+        }
         count_launch();
         WDB_CK(cudaGetLastError());
         src = dst;

@@ -42,12 +42,13 @@ __global__ void __launch_bounds__(256) resid64_kernel(double* __restrict__ r, co
     }
 }
 
-// KKT residuals and max |g|/w over the coefficients, subband by subband
+// KKT residuals, max |g|/w, sum w|x| and the support size over the coefficients, subband by
+// subband, with the FP64 weights of the problem
 __global__ void __launch_bounds__(kVB) kkt64_kernel(SubbandArgs A, const float* __restrict__ x,
-                                                    const double* __restrict__ g, const float* __restrict__ w_sb,
+                                                    const double* __restrict__ g, const double* __restrict__ w_sb,
                                                     RedTarget red) {
     __shared__ int s_o;
-    double off = 0.0, on = 0.0, gm = 0.0;
+    double off = 0.0, on = 0.0, gm = 0.0, wx = 0.0, cnt = 0.0;
     for (int vb = blockIdx.x; vb < A.nvb; vb += gridDim.x) {
         if (threadIdx.x == 0) s_o = find_subband(A.vb_start, A.S, vb);
         __syncthreads();
@@ -56,22 +57,21 @@ __global__ void __launch_bounds__(kVB) kkt64_kernel(SubbandArgs A, const float* 
         const int local = (vb - A.vb_start[o]) * kVB + threadIdx.x;
         if (local < so.rows * so.cols) {
             const size_t i = so.off + local;
-            const double gv = g[i], wv = (double)w_sb[o];
+            const double gv = g[i], wv = w_sb[o];
             const float xv = x[i];
             const double ag = fabs(gv);
             const double sc = wv > 0.0 ? 1.0 / wv : 1.0;
             off = fmax(off, fmax(ag - wv, 0.0) * sc);
             if (xv != 0.f) on = fmax(on, fabs(gv + (xv > 0.f ? wv : -wv)) * sc);
             gm = fmax(gm, wv > 0.0 ? ag / wv : (ag > 0.0 ? DBL_MAX : 0.0));
+            wx += wv * fabs((double)xv);
+            cnt += xv != 0.f ? 1.0 : 0.0;
         }
         __syncthreads();
     }
-    double v[3] = {off, on, gm}, tot[3];
-    if (grid_reduce<3>(v, 7u, red.part, red.counter, tot) && threadIdx.x == 0) {
-        red.out[0] = tot[0];
-        red.out[1] = tot[1];
-        red.out[2] = tot[2];
-    }
+    double v[5] = {off, on, gm, wx, cnt}, tot[5];
+    if (grid_reduce<5>(v, 7u, red.part, red.counter, tot) && threadIdx.x == 0)
+        for (int q = 0; q < 5; ++q) red.out[q] = tot[q];
 }
 
 int grid_for(long long n, int cap) {
@@ -82,12 +82,15 @@ int grid_for(long long n, int cap) {
 
 }  // namespace
 
-wdb_status theta_kkt64(wdb_theta* th, const float* x, const float* x0, const float* w_dev, cudaStream_t st,
+wdb_status theta_kkt64(wdb_theta* th, const float* x, const float* x0, const double* w_host, cudaStream_t st,
                        Kkt64* out) {
     const long long N = th->lay.N;
+    const int S = th->lay.S;
     if (!th->d_x64) WDB_TRY(th_alloc(th, &th->d_x64, (size_t)N));
     if (!th->d_r64) WDB_TRY(th_alloc(th, &th->d_r64, (size_t)N));
-    if (!th->d_kkt_out) WDB_TRY(th_alloc(th, &th->d_kkt_out, 8));
+    if (!th->d_kkt_out) WDB_TRY(th_alloc(th, &th->d_kkt_out, 8 + (size_t)S));
+    double* d_w64 = th->d_kkt_out + 8;
+    WDB_CK(cudaMemcpyAsync(d_w64, w_host, sizeof(double) * S, cudaMemcpyHostToDevice, st));
     const TileArgs F = tile_args(th, false, true), At = tile_args(th, true, true);
     double* d_out = th->d_kkt_out;
     const int grid = grid_for(N, th->grid);
@@ -102,10 +105,11 @@ wdb_status theta_kkt64(wdb_theta* th, const float* x, const float* x0, const flo
     double* g = th->d_x64;
     WDB_TRY(tile_apply<double>(At, th->d_r64, g, nullptr, nullptr, th->d_red_part, st));
     const SubbandArgs A = subband_args(th);
-    kkt64_kernel<<<th->grid, kVB, 0, st>>>(A, x, g, w_dev, th_red(th, d_out + 2));
+    // (the per-CTA partial buffer holds 4 values for each of part_len CTAs)
+    const int kgrid = std::max(1, std::min(th->grid, th->part_len * 4 / 5));
+    kkt64_kernel<<<kgrid, kVB, 0, st>>>(A, x, g, d_w64, th_red(th, d_out + 2));
     count_launch();
     WDB_CK(cudaGetLastError());
-    WDB_TRY(launch_l1_terms(A, th->grid, x, w_dev, th_red(th, d_out + 5), st));
     double h[7];
     WDB_CK(cudaMemcpyAsync(h, d_out, sizeof h, cudaMemcpyDeviceToHost, st));
     WDB_CK(cudaStreamSynchronize(st));

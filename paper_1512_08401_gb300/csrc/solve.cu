@@ -290,7 +290,11 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     long long sup = 0;
     WDB_TRY(theta_objective_dev(th, th->d_xs, th->d_x0, th->d_w, st, &Eobj, &sup));
     Kkt64 kk{NAN, NAN, NAN, NAN, NAN, NAN, 0};
-    if (p->kkt_check) WDB_TRY(theta_kkt64(th, th->d_xs, th->d_x0, th->d_w, st, &kk));
+    if (p->kkt_check) {
+        std::vector<double> w64(L.S);
+        for (int b = 0; b < L.S; ++b) w64[b] = p->w_subband_host ? p->w_subband_host[b] : p->lambda;
+        WDB_TRY(theta_kkt64(th, th->d_xs, th->d_x0, w64.data(), st, &kk));
+    }
     WDB_CK(cudaMemcpyAsync(x_out, th->d_xs, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
     WDB_TRY(work_exit(st, th->ev_out, caller));
     WDB_CK(cudaStreamSynchronize(st));

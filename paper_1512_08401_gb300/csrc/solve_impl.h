@@ -43,7 +43,8 @@ struct Kkt64 {
     long long support;
 };
 // FP64 r = Theta_K x - x0, g = Theta_K^T r, KKT residuals, objective and gap of x (kkt.cu)
-wdb_status theta_kkt64(wdb_theta* th, const float* x, const float* x0, const float* w_dev, cudaStream_t st,
+// (w_host: the problem's FP64 weights per subband)
+wdb_status theta_kkt64(wdb_theta* th, const float* x, const float* x0, const double* w_host, cudaStream_t st,
                        Kkt64* out);
 wdb_status fftop_create(const double* psf_host, int kh, int kw, const Layout& L, const Filters& f,
                         const char* wavelet, cudaStream_t st, wdb_fftop** out);

@@ -42,6 +42,28 @@ def test_noalloc_matches_dwt_twice(wdb, n_rows, n_cols, J):
         assert np.abs(a - b).max() <= 2e-6 * np.abs(b).max(), f"call {call}"
 
 
+def test_noalloc_second_call_leaves_device_memory_alone(wdb):
+    """After the first call on this device (which may load the module holding the array),
+    another call changes the device's free memory by nothing (cudaMemGetInfo), and its result
+    agrees with the FP64 oracle's transform within the transform tests' tolerance."""
+    from oracle import wavelet
+    n_rows, n_cols, J = 256, 384, 4
+    N = n_rows * n_cols
+    rng = np.random.default_rng(22)
+    img = rng.standard_normal((n_rows, n_cols))
+    u = torch.from_numpy(img.astype(np.float32).ravel()).cuda()
+    got = torch.zeros(N, device="cuda")
+    wdb.dwt_noalloc(u, got, n_rows, n_cols, "db4", J)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    wdb.dwt_noalloc(u, got, n_rows, n_cols, "db4", J)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    ref = wavelet.dwt2(img.astype(np.float32).astype(np.float64), "db4", J)
+    a = got.cpu().numpy().astype(np.float64)
+    assert np.abs(a - ref).max() <= 2e-6 * np.abs(ref).max()
+
+
 def test_noalloc_rejects_oversize(wdb):
     u = torch.zeros(4, device="cuda")
     st = wdb.lib().wdb_dwt_noalloc(C.c_void_p(u.data_ptr()), C.c_void_p(u.data_ptr()), 4096, 4096, b"db4", 6, None)
