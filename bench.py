@@ -281,6 +281,13 @@ def run_ours(args):
     f_star = fop.solve(u_dev, x_dev, lam=LAM, max_iters=3000, precond=PRECOND)
     E_theta, E_fft = r_star["objective"], f_star["objective"]
     tgt_theta, tgt_fft = E_theta * (1 + REL_GAP), E_fft * (1 + REL_GAP)
+    # the paper's protocol (Sec. 5.4): the number of iterations N_it that reaches the target
+    # (untimed run with the on-device objective target), then N_it iterations timed as one
+    # graph chunk without checks, for each path
+    n_theta = th.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND,
+                       target_objective=tgt_theta)["first_primal_below"]
+    n_fft = fop.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND,
+                      target_objective=tgt_fft)["first_primal_below"]
 
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -308,10 +315,10 @@ def run_ours(args):
             torch.cuda.nvtx.range_pop()
         return ms, res
 
-    theta_solve = lambda: th.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND,  # noqa: E731
-                                   target_objective=tgt_theta, time_kernels=True)
-    fft_solve = lambda: fop.solve(u_dev, x_dev, lam=LAM, max_iters=20000, precond=PRECOND,  # noqa: E731
-                                  target_objective=tgt_fft, time_kernels=True)
+    theta_solve = lambda: th.solve(u_dev, x_dev, lam=LAM, max_iters=n_theta, check_every=n_theta,  # noqa: E731
+                                   precond=PRECOND, time_kernels=True)
+    fft_solve = lambda: fop.solve(u_dev, x_dev, lam=LAM, max_iters=n_fft, check_every=n_fft,  # noqa: E731
+                                  precond=PRECOND, time_kernels=True)
     timed(theta_solve, args.warmup)
     timed(fft_solve, args.warmup)
     clocks = Clocks()
@@ -324,6 +331,10 @@ def run_ours(args):
     clk = clocks.stop()
     e_ms, _ = timed(theta_solve, args.steps, e2e=True)
 
+    # the Theta_K path's result measured on the exact problem (each path stops at 1e-4 of its
+    # own optimum; this is where Theta_K's lands on the exact one)
+    theta_solve()
+    E_exact_of_theta = fop.objective(u_dev, x_dev, lam=LAM)
     ms_theta = d.max(torch, statistics.mean(t_ms))
     ms_fft = d.max(torch, statistics.mean(f_ms))
     ms_e2e = d.max(torch, statistics.mean(e_ms))
@@ -331,6 +342,9 @@ def run_ours(args):
     solves_per_s = d.sum(torch, float(len(t_ms))) / (d.max(torch, sum(t_ms)) * 1e-3)
     it_theta = statistics.mean(r["iters"] for r in t_res)
     it_fft = statistics.mean(r["iters"] for r in f_res)
+    # the timed runs end at y^(N_it), whose primal value met the target in the untimed run
+    reached_theta = (t_res[-1]["primal"] - E_theta) / E_theta
+    reached_fft = (f_res[-1]["primal"] - E_fft) / E_fft
     k1 = statistics.mean(r["ms_k1"] for r in t_res)
     k2 = statistics.mean(r["ms_k2"] for r in t_res)
 
@@ -354,11 +368,18 @@ def run_ours(args):
                       "l2": "flushed between steps (256 MiB write)", "K_eff": th.info.K_eff,
                       "n_taps": th.info.n_taps, "tau": pc["tau"], "L_hat": pc["L_hat"]},
            "iters_to_gap": it_theta, "fista_iters_per_s": it_theta / (ms_theta * 1e-3),
+           "protocol": ("paper Sec. 5.4: N_it from an untimed run with the objective target E*(1 + 1e-4), then "
+                        "N_it iterations timed as one CUDA-graph chunk (no checks), each path with its own E*"),
+           "rel_gap_reached": {"theta": reached_theta, "fft": reached_fft},
            "solves_per_s_all_ranks": solves_per_s,
            "fft_path": {"ms": ms_fft, "iters": it_fft, "iters_per_s": it_fft / (ms_fft * 1e-3),
                         "ms_gradient": statistics.mean(r["ms_k1"] for r in f_res),
                         "ms_step": statistics.mean(r["ms_k2"] for r in f_res), "tau": fpc["tau"]},
            "speedup_theta_vs_fft": ms_fft / ms_theta,
+           "model_error": {"E_exact_star_minus_E_theta_star_rel": (E_fft - E_theta) / E_fft,
+                           "E_exact_of_theta_result_rel_gap": (E_exact_of_theta - E_fft) / E_fft,
+                           "note": ("each path is timed to 1e-4 of its own optimum; the Theta_K path solves the "
+                                    "K-sparse model, and its result has this relative gap on the exact problem")},
            "E_star": {"theta_gpu": E_theta, "fft_gpu": E_fft},
            "kernel_ms": {"k1_residual": k1, "k2_step": k2},
            "roofline": roof,
@@ -567,10 +588,12 @@ TABLE3_KN = {("gaussian", 2.5): 2, ("gaussian", 5.0): 1, ("skewed", 2.5): 5, ("s
 def run_blurs(args):
     """Analogue of the paper's Table 3 (Sec. 5.5) on the synthetic 1024^2 image: the five blur
     families at widths 2.5 and 5, noise 5e-3, Symmlet 6 with J = 6, w = 1e-4 j(i), K / N from
-    the table's operations per pixel, stopping rule E(x_k) - E* <= 1e-3 E(x_0) (Sec. 5.4):
-    ms and iterations of the Theta_K path (SPAI) against the FFT path (plain FISTA, the paper's
-    Fourier method, and FISTA-SPAI), E* of each path from a long run, and the pSNR of each
-    result against the clean image."""
+    the table's operations per pixel. Each path (Theta_K with SPAI; the FFT path as plain FISTA,
+    the paper's Fourier method, and with SPAI) is timed with the paper's protocol (Sec. 5.4):
+    the iteration count N_it that reaches a 1e-4 relative gap to the path's own E* (long run),
+    then N_it iterations as one graph chunk. The iterations to the paper's rule
+    E(x_k) - E* <= 1e-3 E(x_0) are reported too (with x_0 = 0 that rule is loose on these
+    images), with the pSNR of each result against the clean image."""
     import torch
     from paper_1512_08401_gb300 import build, synthetic, wdb
     build.build()
@@ -609,10 +632,12 @@ def run_blurs(args):
                    "build_ms": th.info.build_ms}
             for tag, op, pre in (("theta_spai", th, "spai"), ("fft_plain", fop, "none"), ("fft_spai", fop, "spai")):
                 Es = op.solve(u, x, w_subband=wsb, max_iters=3000, precond=pre)["objective"]
-                tgt = Es + 1e-3 * E0
-                ms, r = timed(lambda: op.solve(u, x, w_subband=wsb, max_iters=20000, precond=pre,
-                                               target_objective=tgt))
-                row[tag] = {"ms": ms, "iters": r["first_primal_below"] or r["iters"], "E_star": Es,
+                n4 = op.solve(u, x, w_subband=wsb, max_iters=20000, precond=pre,
+                              target_objective=Es * (1 + REL_GAP))["first_primal_below"]
+                n3 = op.solve(u, x, w_subband=wsb, max_iters=20000, precond=pre,
+                              target_objective=Es + 1e-3 * E0)["first_primal_below"]
+                ms, r = timed(lambda: op.solve(u, x, w_subband=wsb, max_iters=n4, check_every=n4, precond=pre))
+                row[tag] = {"ms": ms, "iters": n4, "iters_paper_rule": n3, "E_star": Es,
                             "psnr_db": psnr(wdb, torch, x, prob.u_clean, n, wname, J)}
             row["speedup_vs_fft_plain"] = row["fft_plain"]["ms"] / row["theta_spai"]["ms"]
             row["speedup_vs_fft_spai"] = row["fft_spai"]["ms"] / row["theta_spai"]["ms"]
@@ -621,7 +646,7 @@ def run_blurs(args):
             print(json.dumps(row), file=sys.stderr, flush=True)
             th.free()
             fop.free()
-    print(json.dumps({"metric": "ms to E - E* <= 1e-3 E(x0), five blur families x two widths, 1024^2 (Table 3 analogue)",
+    print(json.dumps({"metric": "ms to 1e-4 rel. objective gap, five blur families x two widths, 1024^2 (Table 3 analogue)",
                       "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
                       "data": "synthetic", "dtype": "f32", "l2": "flushed before each timed solve",
                       "config": {"workload": "1024x1024 synthetic, noise 5e-3, sym6 J=6, w = 1e-4 j(i), K/N from "

@@ -266,6 +266,12 @@ wdb_status wdb_fftop_precond(wdb_fftop* op, int precond, double jacobi_eps, void
                              double* P_host /* 3J+1 */, double* tau_host, double* L_hat_host);
 wdb_status wdb_fftop_set_precond(wdb_fftop* op, int precond, const double* P_host, double tau);
 
+/* Exact objective 1/2||H Psi x - u0||^2 + sum w|x| of a device iterate x (N floats) for the
+ * device image u0 (the FP32 spectral path of wdb_solve_fft, FP64 reductions), e.g. to measure
+ * a Theta_K solution on the exact problem. Synchronises `stream`. */
+wdb_status wdb_fftop_objective(wdb_fftop* op, const float* u_dev, const float* x_dev, double lambda,
+                               const double* w_subband_host, void* stream, double* E_host);
+
 /* FISTA with the exact gradient: per iteration IDWT(y), R2C, r^ = h^ z^ - u0^ with
  * Parseval reductions, g^ = conj(h^) r^, C2R, DWT, then the same fused step as wdb_solve.
  * result->objective is the exact objective 1/2||H Psi x - u0||^2 + sum w|x|. */

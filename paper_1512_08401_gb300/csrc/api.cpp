@@ -411,6 +411,16 @@ wdb_status wdb_fftop_create(const double* psf_host, int kh, int kw, int n_rows, 
 
 void wdb_fftop_free(wdb_fftop* op) { fftop_free(op); }
 
+wdb_status wdb_fftop_objective(wdb_fftop* op, const float* u_dev, const float* x_dev, double lambda,
+                               const double* w_subband_host, void* stream, double* E_host) {
+    if (!op || !u_dev || !x_dev || !E_host) return set_error(WDB_EINVAL, "NULL argument");
+    if (!w_subband_host && !(lambda >= 0.0 && std::isfinite(lambda)))
+        return set_error(WDB_EINVAL, "lambda must be finite and >= 0");
+    std::vector<double> w(op->lay.S);
+    for (int b = 0; b < op->lay.S; ++b) w[b] = w_subband_host ? w_subband_host[b] : lambda;
+    return fft_objective_public(op, u_dev, x_dev, w.data(), static_cast<cudaStream_t>(stream), E_host);
+}
+
 wdb_status wdb_fftop_precond(wdb_fftop* op, int precond, double jacobi_eps, void* stream, double* P_host,
                              double* tau_host, double* L_hat_host) {
     if (!op) return set_error(WDB_EINVAL, "NULL handle");

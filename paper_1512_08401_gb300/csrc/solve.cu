@@ -618,6 +618,23 @@ static wdb_status fft_objective(wdb_fftop* op, const float* x, cudaStream_t st, 
     return WDB_OK;
 }
 
+wdb_status fft_objective_public(wdb_fftop* op, const float* u, const float* x, const double* w_host,
+                                cudaStream_t caller, double* E) {
+    const Layout& L = op->lay;
+    WDB_TRY(work_enter(&op->work, &op->ev_in, &op->ev_out, caller));
+    cudaStream_t st = op->work;
+    std::vector<float> w(L.S);
+    for (int b = 0; b < L.S; ++b) w[b] = (float)w_host[b];
+    WDB_CK(cudaMemcpyAsync(op->d_w, w.data(), sizeof(float) * L.S, cudaMemcpyHostToDevice, st));
+    WDB_CK(cudaMemcpyAsync(op->d_z, u, sizeof(float) * L.N, cudaMemcpyDeviceToDevice, st));
+    cufftSetStream(op->r2c, st);
+    WDB_CKF(cufftExecR2C(op->r2c, op->d_z, op->d_uhat));
+    WDB_TRY(fft_objective(op, x, st, E, nullptr));
+    WDB_TRY(work_exit(st, op->ev_out, caller));
+    WDB_CK(cudaStreamSynchronize(st));
+    return WDB_OK;
+}
+
 wdb_status fft_solve(wdb_fftop* op, const float* u, float* x_out, const wdb_solve_params* p, cudaStream_t caller,
                      wdb_solve_result* res) {
     const double t0 = now_ms();

@@ -52,6 +52,8 @@ void fftop_free(wdb_fftop* op);
 wdb_status fftop_precond(wdb_fftop* op, int kind, double eps, cudaStream_t st);
 wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, float* const* x,
                        const wdb_solve_params* params, cudaStream_t caller, wdb_solve_result* res);
+wdb_status fft_objective_public(wdb_fftop* op, const float* u, const float* x, const double* w_host,
+                                cudaStream_t st, double* E);
 wdb_status fft_solve(wdb_fftop* op, const float* u, float* x_out, const wdb_solve_params* p, cudaStream_t st,
                      wdb_solve_result* res);
 

@@ -401,6 +401,7 @@ static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
                 if (L.sb[o].level == lev) best[o] = pick;
         }
         if (s != WDB_OK) break;
+        th->tune_levels[op] = best;
         std::vector<TilePlanHost> whole;
         whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, &best, 0));
         for (int budget : {kTileSmemBudget * 3 / 4, kTileSmemBudget, kTileSmemBudget * 3 / 2})
@@ -474,12 +475,15 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
 
 TileArgs tile_args(const wdb_theta* th, bool adj, bool fp64) { return th->targs[adj ? 1 : 0][fp64 ? 1 : 0]; }
 
-// Plans for batched solves: the planner's choice with a loose per-tile cap (16 per-CTA
-// shares), since the tiles of many problems share the CTAs; built on first use.
+// Plans for batched solves: the autotuner's tile side and thread map per output level (the
+// planner's where the operator was not tuned) with a loose per-tile cap (16 per-CTA shares),
+// since the tiles of many problems share the CTAs; built on first use.
 wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st) {
     if (th->bplan_ok) return WDB_OK;
     for (int op = 0; op < 2; ++op) {
-        th->bplan[op] = make_tile_plan(th->lay, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, 16.0);
+        const std::vector<TileTune>* tune =
+            (int)th->tune_levels[op].size() == th->lay.S ? &th->tune_levels[op] : nullptr;
+        th->bplan[op] = make_tile_plan(th->lay, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, tune, 0, 16.0);
         WDB_TRY(upload_plan(th, th->bplan[op], th->bargs[op], st));
     }
     th->bplan_ok = true;

@@ -127,6 +127,7 @@ struct wdb_theta {
     std::vector<wdb::TileEntry> tent[2];   // gather-form taps of Theta_K and Theta_K^T (plan input)
     int plan_ctas = 0;                     // CTAs the plans are balanced for
     int tuned = 0;                         // 1: the FP32 plans were autotuned on this GPU
+    std::vector<wdb::TileTune> tune_levels[2];   // the autotuner's tile side per output subband
     wdb::TilePlanHost bplan[2];            // FP32 plans for batched solves (large tiles: the
     wdb::TileArgs bargs[2];                // batch's many problems balance the CTAs)
     bool bplan_ok = false;

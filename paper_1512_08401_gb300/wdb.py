@@ -98,6 +98,7 @@ _SIGS = {
                               C.POINTER(SolveResult)]),
     "wdb_fftop_create": (i32, [pd, i32, i32, i32, i32, C.c_char_p, i32, vp, C.POINTER(vp)]),
     "wdb_fftop_free": (None, [vp]),
+    "wdb_fftop_objective": (i32, [vp, vp, vp, f64, pd, vp, pd]),
     "wdb_fftop_precond": (i32, [vp, i32, f64, vp, pd, pd, pd]),
     "wdb_fftop_set_precond": (i32, [vp, i32, pd, f64]),
     "wdb_solve_fft": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
@@ -356,6 +357,16 @@ class FFTOp:
     def set_precond(self, kind, P, tau):
         P, pp = _f64(P)
         _check(lib().wdb_fftop_set_precond(self._h, PRECOND[kind], pp, float(tau)))
+
+    def objective(self, u, x, lam=1e-3, w_subband=None, stream=None):
+        """Exact objective of the iterate x for the image u (wdb_fftop_objective)."""
+        E = C.c_double()
+        pw = None
+        if w_subband is not None:
+            w, pw = _f64(w_subband)
+        _check(lib().wdb_fftop_objective(self._h, _dev(u, self.N), _dev(x, self.N), float(lam), pw, _stream(stream),
+                                         C.byref(E)))
+        return E.value
 
     def solve(self, u, x, stream=None, **kw):
         p, _keep = make_params(**kw)
