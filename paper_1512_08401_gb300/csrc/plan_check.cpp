@@ -13,10 +13,6 @@
 
 namespace wdb {
 
-namespace {
-constexpr int kUpStagedLgPlan = 3;   // the planner stages the phase tables of up pairs with r <= 8
-}  // namespace
-
 std::string check_tile_plan(const Layout& L, const TilePlanHost& P) {
     char msg[256];
     auto fail = [&](const char* fmt, int a, int b) {
@@ -35,7 +31,7 @@ std::string check_tile_plan(const Layout& L, const TilePlanHost& P) {
         const bool same = e.p.in_sb == q.in_sb && e.p.soff == q.soff && e.p.mode == q.mode && e.p.lg == q.lg &&
                           e.p.RR == q.RR && e.p.RC == q.RC && e.p.PR == q.PR && e.p.PC == q.PC && e.p.PS == q.PS &&
                           e.p.y0 == q.y0 && e.p.x0 == q.x0 && e.p.tap_begin == q.tap_begin && e.p.ntap == q.ntap &&
-                          e.p.vec == q.vec;
+                          e.p.vec == q.vec && e.p.tst == q.tst;
         if (!same || e.in_off != si.off || e.in_rows != si.rows || e.in_cols != si.cols)
             return fail("pair table entry %d differs from pair %d", (int)k, (int)k);
     }
@@ -69,7 +65,9 @@ std::string check_tile_plan(const Layout& L, const TilePlanHost& P) {
                     return fail("pair %d staged in 16-byte chunks without 4-aligned rows (batch %d)", pi, bi);
                 // every staged read: tap offset plus the farthest output of the staged tile
                 const int ntab = tp.mode == kDown ? tp.ntap : tp.ntap * r * r;
-                if (tp.mode == kDown || tp.lg <= kUpStagedLgPlan)
+                if (tp.mode == kUp && tp.tst && (long long)tp.ntap * r * r * (4 + esize) > buf_bytes / 4 && tp.lg > 3)
+                    return fail("pair %d stages a phase table above a quarter of the buffer (batch %d)", pi, bi);
+                if (tp.mode == kDown || tp.tst)
                     if (tp.tap_begin < bt.tap_begin || tp.tap_begin + ntab > bt.tap_end)
                         return fail("pair %d taps outside batch %d", pi, bi);
                 const int far = tp.mode == kDown ? TSs - 1 : (TSs - 1) >> tp.lg;

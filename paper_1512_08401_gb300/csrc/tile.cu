@@ -32,7 +32,14 @@ constexpr double kCostTapStage = 6.0;    // per staged tap (offset + value)
 constexpr double kCostMacGlobal = 60.0;  // per multiply-add gathered from global memory (latency bound)
 constexpr double kCostItem = 20000.0;    // per tile (scheduling, descriptors, barriers, epilogue)
 constexpr double kCostBatch = 6000.0;    // per batch (staging round trip, barriers)
-constexpr int kUpStagedLg = 3;           // up pairs with r <= 8 stage their phase tables
+constexpr int kUpStagedLg = 3;           // up pairs with r <= 8 always stage their phase tables
+
+// Up pairs stage their phase tables (r^2 phases x the fullest phase's taps) with the batch when
+// r <= 8, or when the table takes at most a quarter of the staging buffer; larger tables are
+// read from global memory.
+bool tables_staged(int lg, int maxph, int esize, int budget) {
+    return lg <= kUpStagedLg || ((long long)maxph << (2 * lg)) * (4 + esize) <= budget / 4;
+}
 
 int next_pow2(int v) {
     int p = 1;
@@ -105,7 +112,8 @@ double subband_cost(const SubbandDev& so, const std::vector<PairBuild*>& prs, in
         double cs = 1e300;
         if (g.bytes <= budget)
             cs = (double)g.RR * g.RC * kCostStage + macs * mac_smem +
-                 kCostTapStage * (double)(!pb.up ? (int)pb.taps.size() : (pb.lg <= kUpStagedLg ? pb.maxph << (2 * pb.lg) : 0));
+                 kCostTapStage * (double)(!pb.up ? (int)pb.taps.size()
+                                                 : (tables_staged(pb.lg, pb.maxph, esize, budget) ? pb.maxph << (2 * pb.lg) : 0));
         const double cg = macs * kCostMacGlobal;
         glob[k] = cg < cs;
         c += std::min(cs, cg);
@@ -219,7 +227,8 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 if (global[k]) ok = false;
                 const Geometry g = geometry(pb, 64, esize, e4, vecf[k], 32);
                 regs += (g.bytes + 15) / 16 * 16 / esize;
-                ntaps += !pb.up ? (long long)pb.taps.size() : (pb.lg <= kUpStagedLg ? (long long)pb.maxph << (2 * pb.lg) : 0);
+                ntaps += !pb.up ? (long long)pb.taps.size()
+                                : (tables_staged(pb.lg, pb.maxph, esize, budget) ? (long long)pb.maxph << (2 * pb.lg) : 0);
             }
             const long long tapel = (ntaps * (4 + esize) + 15) / 16 * 16 / esize;
             if (ok && regs + tapel <= budget / esize) {
@@ -232,10 +241,11 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         std::vector<int> order;
         for (int k = 0; k < np; ++k)
             if (!global[k] && !by_out[o][k]->up) order.push_back(k);
+        auto tst = [&](int k) { return tables_staged(by_out[o][k]->lg, by_out[o][k]->maxph, esize, budget); };
         for (int k = 0; k < np; ++k)
-            if (!global[k] && by_out[o][k]->up && by_out[o][k]->lg <= kUpStagedLg) order.push_back(k);
+            if (!global[k] && by_out[o][k]->up && tst(k)) order.push_back(k);
         for (int k = 0; k < np; ++k)
-            if (!global[k] && by_out[o][k]->up && by_out[o][k]->lg > kUpStagedLg) order.push_back(k);
+            if (!global[k] && by_out[o][k]->up && !tst(k)) order.push_back(k);
         for (int k = 0; k < np; ++k)
             if (global[k]) order.push_back(k);
         TileSub& sub = plan.subs[o];
@@ -266,7 +276,8 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             const int need = (int)((g.bytes + 15) / 16 * 16 / esize);
             // staged taps: down pairs and up pairs with r <= 8 (larger phase tables are read
             // from global memory)
-            const int nt = !pb.up ? (int)pb.taps.size() : (pb.lg <= kUpStagedLg ? pb.maxph << (2 * pb.lg) : 0);
+            const int nt = !pb.up ? (int)pb.taps.size()
+                                  : (tables_staged(pb.lg, pb.maxph, esize, budget) ? pb.maxph << (2 * pb.lg) : 0);
             // taps: one int offset + one value each, rounded to 16 bytes
             auto tap_elems = [&](int ntaps) { return (int)(((long long)ntaps * (4 + esize) + 15) / 16 * 16 / esize); };
             const bool nonempty = batch_regions.back() > 0;
@@ -294,7 +305,8 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 double c = macs * kCostMacGlobal;
                 if (!global[order[q]]) {
                     const Geometry g = geometry(pb, ST, esize, e4, vecf[order[q]], TS);
-                    const int nt = !pb.up ? (int)pb.taps.size() : (pb.lg <= kUpStagedLg ? pb.maxph << (2 * pb.lg) : 0);
+                    const int nt = !pb.up ? (int)pb.taps.size()
+                                          : (tables_staged(pb.lg, pb.maxph, esize, budget) ? pb.maxph << (2 * pb.lg) : 0);
                     c = (double)g.RR * g.RC * kCostStage + macs * mac_smem + kCostTapStage * nt;
                 }
                 bc[batch_of[q]] += c;
@@ -328,6 +340,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             tp.y0 = pb.dy0;
             tp.x0 = pb.dx0;
             tp.vec = vecf[k] ? 1 : 0;
+            tp.tst = (pb.up && !global[k] && tables_staged(pb.lg, pb.maxph, esize, budget)) ? 1 : 0;
             if (global[k]) {   // bounding box of the taps (input units) for the interior test
                 tp.RR = pb.dy1 - pb.dy0 + 1;
                 tp.RC = pb.dx1 - pb.dx0 + 1;
@@ -380,7 +393,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
             taps_per_out += tp.ntap;
             plan.pairs.push_back(tp);
             bt.pair_end = (int)plan.pairs.size();
-            if (!global[k] && (!pb.up || pb.lg <= kUpStagedLg)) bt.tap_end = (int)plan.tap_off.size();
+            if (!global[k] && (!pb.up || tp.tst)) bt.tap_end = (int)plan.tap_off.size();
         }
         // tap copies follow the regions of each batch in the buffer
         for (int bi = sub.batch_begin; bi < (int)plan.batches.size(); ++bi) {
@@ -493,7 +506,6 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
 namespace {
 
 enum Epi { kApply = 0, kApplyNorm = 1, kK1 = 2, kK2 = 3, kResNorm = 4, kObj = 5 };
-constexpr int kUpStagedLgDev = 3;   // must equal the planner's kUpStagedLg
 
 struct EpiArgs {
     const float* x0;          // kK1, kResNorm, kObj
@@ -829,7 +841,7 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
             const int rr = r * r;
             const int py = w.ty0 + oy + tm.ly, px = w.tx0 + ox + tm.lx;
             const int rowb = ((py >> lg) - (w.ty0 >> lg)) * P.PC + sh;
-            const bool st = lg <= kUpStagedLgDev;   // phase tables staged with the batch
+            const bool st = P.tst != 0;   // phase tables staged with the batch
             const TapSrc<T> gts = (st ? stap : global_taps<T>(plan)) + P.tap_begin;
             if (E == 4 && st && lg <= tm.lgsx) {
                 const int ph = ((py & m) << lg) + (px & m);
@@ -876,6 +888,36 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
             // too little reuse to pay for staging)
             const T* __restrict__ src = in + tab[i].in_off;
             const int R = tab[i].in_rows, C = tab[i].in_cols;
+            if (P.mode == kDownGlobal && E == 4) {
+                // the four outputs of the thread share the pair's taps: when all four gather
+                // inside the subband (no wrap), each tap's offset and value are loaded once and
+                // its four inputs are independent loads
+                const int py = w.ty0 + oy + tm.ly, px0 = w.tx0 + ox + tm.lx;
+                const int by = py << lg, bx0 = px0 << lg, bstep = tm.sx << lg;
+                const bool rows_ok = py < so.rows && by + P.y0 >= 0 && by + P.y0 + P.RR <= R;
+                const bool cols_ok = px0 + 3 * tm.sx < so.cols && bx0 + P.x0 >= 0 && bx0 + 3 * bstep + P.x0 + P.RC <= C;
+                if (rows_ok && cols_ok) {
+                    const T* __restrict__ bp = src + (size_t)by * C + bx0;
+                    const int* __restrict__ tl = plan.tap_lin + P.tap_begin;
+                    const T* __restrict__ tv = gvals + P.tap_begin;
+                    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 2
+                    for (int j = g; j < P.ntap; j += G) {
+                        const int l = __ldg(tl + j);
+                        const T v = __ldg(tv + j);
+                        const T* __restrict__ q = bp + l;
+                        a0 = fma(v, __ldg(q), a0);
+                        a1 = fma(v, __ldg(q + bstep), a1);
+                        a2 = fma(v, __ldg(q + 2 * bstep), a2);
+                        a3 = fma(v, __ldg(q + 3 * bstep), a3);
+                    }
+                    acc[0] += a0;
+                    acc[1] += a1;
+                    acc[2] += a2;
+                    acc[3] += a3;
+                    continue;
+                }
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
                 if (e >= E) continue;
@@ -897,10 +939,24 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                 // interior: every tap of the pair lands inside the input subband, no wrap
                 const bool inside = by + P.y0 >= 0 && by + P.y0 + P.RR <= R && bx + P.x0 >= 0 && bx + P.x0 + P.RC <= C;
                 if (inside) {
+                    // four independent chains (offset, then input) in flight
                     const T* __restrict__ bp = src + (size_t)by * C + bx;
                     const int* __restrict__ tl = plan.tap_lin + tb;
                     const T* __restrict__ tv = gvals + tb;
-                    for (int j = g; j < P.ntap; j += G) a += __ldg(tv + j * step) * __ldg(bp + __ldg(tl + j * step));
+                    T a1 = 0, a2 = 0, a3 = 0;
+                    int j = g;
+                    for (; j + 3 * G < P.ntap; j += 4 * G) {
+                        const int l0 = __ldg(tl + j * step), l1 = __ldg(tl + (j + G) * step);
+                        const int l2 = __ldg(tl + (j + 2 * G) * step), l3 = __ldg(tl + (j + 3 * G) * step);
+                        const T v0 = __ldg(tv + j * step), v1 = __ldg(tv + (j + G) * step);
+                        const T v2 = __ldg(tv + (j + 2 * G) * step), v3 = __ldg(tv + (j + 3 * G) * step);
+                        a = fma(v0, __ldg(bp + l0), a);
+                        a1 = fma(v1, __ldg(bp + l1), a1);
+                        a2 = fma(v2, __ldg(bp + l2), a2);
+                        a3 = fma(v3, __ldg(bp + l3), a3);
+                    }
+                    for (; j < P.ntap; j += G) a = fma(__ldg(tv + j * step), __ldg(bp + __ldg(tl + j * step)), a);
+                    a += (a1 + a2) + a3;
                 } else {
                     for (int j = g; j < P.ntap; j += G) {
                         const int pk = __ldg(plan.tap_off + tb + j * step);

@@ -36,6 +36,8 @@ struct alignas(16) TilePair {
     int tap_begin;    // first tap (up: phase-interleaved, index tap_begin + j r^2 + phase)
     int ntap;         // down: taps; up: padded taps per phase
     int vec;          // 1: rows staged in 16-byte chunks from a 4-aligned column (up or r = 1 pairs)
+    int tst;          // up pairs: 1 when the phase tables are staged with the batch (else read from
+                      // global memory)
 };
 
 constexpr int kMaxBatchPairs = 16;   // pairs per batch (their descriptors sit in shared memory)
