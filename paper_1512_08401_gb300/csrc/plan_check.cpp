@@ -65,8 +65,8 @@ std::string check_tile_plan(const Layout& L, const TilePlanHost& P) {
                     return fail("pair %d staged in 16-byte chunks without 4-aligned rows (batch %d)", pi, bi);
                 // every staged read: tap offset plus the farthest output of the staged tile
                 const int ntab = tp.mode == kDown ? tp.ntap : tp.ntap * r * r;
-                if (tp.mode == kUp && tp.tst && (long long)tp.ntap * r * r * (4 + esize) > buf_bytes / 4 && tp.lg > 3)
-                    return fail("pair %d stages a phase table above a quarter of the buffer (batch %d)", pi, bi);
+                if (tp.mode == kUp && tp.tst && (long long)tp.ntap * r * r * (4 + esize) > buf_bytes / 2 && tp.lg > 3)
+                    return fail("pair %d stages a phase table above half of the buffer (batch %d)", pi, bi);
                 if (tp.mode == kDown || tp.tst)
                     if (tp.tap_begin < bt.tap_begin || tp.tap_begin + ntab > bt.tap_end)
                         return fail("pair %d taps outside batch %d", pi, bi);

@@ -35,10 +35,10 @@ constexpr double kCostBatch = 6000.0;    // per batch (staging round trip, barri
 constexpr int kUpStagedLg = 3;           // up pairs with r <= 8 always stage their phase tables
 
 // Up pairs stage their phase tables (r^2 phases x the fullest phase's taps) with the batch when
-// r <= 8, or when the table takes at most a quarter of the staging buffer; larger tables are
-// read from global memory.
+// r <= 8, or when the table takes at most half of the staging buffer; larger tables are read
+// from global memory.
 bool tables_staged(int lg, int maxph, int esize, int budget) {
-    return lg <= kUpStagedLg || ((long long)maxph << (2 * lg)) * (4 + esize) <= budget / 4;
+    return lg <= kUpStagedLg || ((long long)maxph << (2 * lg)) * (4 + esize) <= budget / 2;
 }
 
 int next_pow2(int v) {
