@@ -78,6 +78,7 @@ typedef struct {
     int plan_items[2];          /* work items of the FP32 plans of Theta_K and Theta_K^T */
     int plan_split_tiles[2];    /* tiles of those plans split over several CTAs */
     int plan_super_subbands[2]; /* subbands of those plans worked in 2 x 2 super tiles */
+    int plan_groups[2];         /* groups of subbands worked together by those plans' items */
 } wdb_theta_info;
 
 /* Parameters of one solve. Zero-initialise and set what you need. */
@@ -179,11 +180,14 @@ wdb_status wdb_theta_set_precond(wdb_theta* th, int precond, const double* P_hos
  * smem_budget bytes (<= 0: 32768; at most 98304), tiles whose modelled cost stays under
  * cap_share CTA shares (<= 0: 2), and either tiles above split_share CTA shares split at
  * batch boundaries over several CTAs (<= 0: none), whose partial sums the last part to
- * finish adds in part order, or (super_tiles != 0) work items of 2 x 2 tiles of side 32
- * staged together wherever all their regions fit one buffer. Results change only by the
+ * finish adds in part order, or (super_tiles = 1) work items of 2 x 2 tiles of side 32
+ * staged together wherever all their regions fit one buffer, or (super_tiles = 2) grouped
+ * items: one item computes the tile of every subband of a level (A_J with the level-J
+ * details), staging each input region once for all of them. Results change only by the
  * FP32 summation order. Captured solve graphs of the handle are dropped; the replaced plans'
  * device memory is released with the handle. WDB_EINVAL for a NULL handle, smem_budget >
- * 98304, or split_share > 0 together with super_tiles. Synchronises `stream`. */
+ * 98304, super_tiles outside 0..2, or split_share > 0 together with super_tiles.
+ * Synchronises `stream`. */
 wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, double split_share, int super_tiles,
                             void* stream);
 
@@ -199,6 +203,7 @@ wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, do
 typedef struct {
     int items, pairs, batches, split_tiles, super_subbands, smem_bytes;
     long long macs;             /* multiply-adds of one application (padding included) */
+    int groups;                 /* groups of subbands worked together (super_tiles = 2) */
 } wdb_plan_summary;
 wdb_status wdb_tile_plan_check(int n_rows, int n_cols, int levels, long long n_taps, const int* a_host,
                                const int* b_host, const int* oy_host, const int* ox_host, const double* v_host,

@@ -177,6 +177,7 @@ wdb_status wdb_theta_info_get(const wdb_theta* th, wdb_theta_info* info) {
         info->plan_items[op] = (int)th->tplan[op][0].items.size();
         info->plan_split_tiles[op] = th->tplan[op][0].n_split;
         info->plan_super_subbands[op] = th->tplan[op][0].n_sup;
+        info->plan_groups[op] = th->tplan[op][0].n_grp;
     }
     return WDB_OK;
 }
@@ -201,13 +202,14 @@ wdb_status wdb_tile_plan_check(int n_rows, int n_cols, int levels, long long n_t
     const TilePlanHost P =
         make_tile_plan(L, te[transpose ? 1 : 0], esize, smem_budget > 0 ? smem_budget : 32768, ctas > 0 ? ctas : 456,
                        nullptr, 0, cap_share > 0.0 ? cap_share : 2.0, split_share > 0.0 ? split_share : 0.0,
-                       super_tiles != 0);
+                       super_tiles == 1, super_tiles == 2);
     if (summary) {
         summary->items = (int)P.items.size();
         summary->pairs = (int)P.pairs.size();
         summary->batches = (int)P.batches.size();
         summary->split_tiles = P.n_split;
         summary->super_subbands = P.n_sup;
+        summary->groups = P.n_grp;
         summary->smem_bytes = P.smem_bytes;
         summary->macs = P.macs;
     }
@@ -220,9 +222,10 @@ wdb_status wdb_theta_replan(wdb_theta* th, int smem_budget, double cap_share, do
                             void* stream) {
     if (!th) return set_error(WDB_EINVAL, "NULL handle");
     if (smem_budget > 98304) return set_error(WDB_EINVAL, "smem_budget %d > 98304", smem_budget);
-    if (super_tiles && split_share > 0.0) return set_error(WDB_EINVAL, "split tiles and super tiles together");
+    if (super_tiles < 0 || super_tiles > 2) return set_error(WDB_EINVAL, "tiling mode %d (0, 1 or 2)", super_tiles);
+    if (super_tiles && split_share > 0.0) return set_error(WDB_EINVAL, "split tiles with super tiles or groups");
     return theta_replan(th, smem_budget > 0 ? smem_budget : 32768, cap_share > 0.0 ? cap_share : 2.0,
-                        split_share > 0.0 ? split_share : 0.0, super_tiles != 0, static_cast<cudaStream_t>(stream));
+                        split_share > 0.0 ? split_share : 0.0, super_tiles, static_cast<cudaStream_t>(stream));
 }
 
 wdb_status wdb_theta_export_taps(const wdb_theta* th, long long cap, int* a, int* b, int* oy, int* ox, double* v) {

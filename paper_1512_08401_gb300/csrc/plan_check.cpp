@@ -28,10 +28,11 @@ std::string check_tile_plan(const Layout& L, const TilePlanHost& P) {
         const PairSm& e = P.pair_sm[k];
         const SubbandDev& si = L.sb[P.pairs[k].in_sb];
         const TilePair& q = P.pairs[k];
-        const bool same = e.p.in_sb == q.in_sb && e.p.soff == q.soff && e.p.mode == q.mode && e.p.lg == q.lg &&
+        bool same = e.p.in_sb == q.in_sb && e.p.soff == q.soff && e.p.mode == q.mode && e.p.lg == q.lg &&
                           e.p.RR == q.RR && e.p.RC == q.RC && e.p.PR == q.PR && e.p.PC == q.PC && e.p.PS == q.PS &&
                           e.p.y0 == q.y0 && e.p.x0 == q.x0 && e.p.tap_begin == q.tap_begin && e.p.ntap == q.ntap &&
-                          e.p.vec == q.vec && e.p.tst == q.tst;
+                          e.p.vec == q.vec && e.p.tst == q.tst && e.p.nm == q.nm;
+        for (int k = 0; k < 4 && same; ++k) same = e.p.mtb[k] == q.mtb[k] && e.p.mnt[k] == q.mnt[k];
         if (!same || e.in_off != si.off || e.in_rows != si.rows || e.in_cols != si.cols)
             return fail("pair table entry %d differs from pair %d", (int)k, (int)k);
     }
@@ -63,21 +64,29 @@ std::string check_tile_plan(const Layout& L, const TilePlanHost& P) {
                 if (tp.vec && (esize != 4 || si.cols % 4 || si.off % 4 || tp.PC % 4 || tp.soff % 4 ||
                                (tp.mode == kDown && tp.lg != 0)))
                     return fail("pair %d staged in 16-byte chunks without 4-aligned rows (batch %d)", pi, bi);
-                // every staged read: tap offset plus the farthest output of the staged tile
-                const int ntab = tp.mode == kDown ? tp.ntap : tp.ntap * r * r;
-                if (tp.mode == kUp && tp.tst && (long long)tp.ntap * r * r * (4 + esize) > buf_bytes / 2 && tp.lg > 3)
+                // every staged read of every member's taps: tap offset plus the farthest output of
+                // the staged tile
+                const int nmem = sub.grp > 0 ? sub.grp : 1;
+                if (tp.nm != nmem) return fail("pair %d has %d members, its group another count", pi, tp.nm);
+                if (tp.mtb[0] != tp.tap_begin || tp.mnt[0] != tp.ntap) return fail("pair %d member 0 is not its taps", pi, 0);
+                long long table = 0;
+                for (int mk = 0; mk < nmem; ++mk) table += (long long)tp.mnt[mk] * r * r;
+                if (tp.mode == kUp && tp.tst && table * (4 + esize) > buf_bytes / 2 && tp.lg > 3)
                     return fail("pair %d stages a phase table above half of the buffer (batch %d)", pi, bi);
-                if (tp.mode == kDown || tp.tst)
-                    if (tp.tap_begin < bt.tap_begin || tp.tap_begin + ntab > bt.tap_end)
-                        return fail("pair %d taps outside batch %d", pi, bi);
-                const int far = tp.mode == kDown ? TSs - 1 : (TSs - 1) >> tp.lg;
-                for (int j = 0; j < ntab; ++j) {
-                    const long long off = P.tap_off[tp.tap_begin + j] - tp.soff;
-                    if (off < 0 || off >= size) return fail("pair %d tap %d outside its region", pi, j);
-                    const long long in_plane = tp.mode == kDown ? off % tp.PS : off;
-                    const long long row = in_plane / tp.PC, col = in_plane % tp.PC;
-                    if (row + far >= tp.PR || col + far + (tp.vec ? 3 : 0) >= tp.PC)
-                        return fail("pair %d tap %d reads past its region's rows or columns", pi, j);
+                for (int mk = 0; mk < nmem; ++mk) {
+                    const int tb = tp.mtb[mk];
+                    const int ntab = tp.mode == kDown ? tp.mnt[mk] : tp.mnt[mk] * r * r;
+                    if (tp.mode == kDown || tp.tst)
+                        if (tb < bt.tap_begin || tb + ntab > bt.tap_end) return fail("pair %d taps outside batch %d", pi, bi);
+                    const int far = tp.mode == kDown ? TSs - 1 : (TSs - 1) >> tp.lg;
+                    for (int j = 0; j < ntab; ++j) {
+                        const long long off = P.tap_off[tb + j] - tp.soff;
+                        if (off < 0 || off >= size) return fail("pair %d tap %d outside its region", pi, j);
+                        const long long in_plane = tp.mode == kDown ? off % tp.PS : off;
+                        const long long row = in_plane / tp.PC, col = in_plane % tp.PC;
+                        if (row + far >= tp.PR || col + far + (tp.vec ? 3 : 0) >= tp.PC)
+                            return fail("pair %d tap %d reads past its region's rows or columns", pi, j);
+                    }
                 }
             }
         }
@@ -115,8 +124,17 @@ std::string check_tile_plan(const Layout& L, const TilePlanHost& P) {
         } else if (w.batch_begin != sub.batch_begin || w.batch_end != sub.batch_end) {
             return fail("item %d does not cover the batches of subband %d", (int)k, w.o);
         }
-        for (int y = w.ty0; y < std::min(w.ty0 + side, so.rows); ++y)
-            for (int x = w.tx0; x < std::min(w.tx0 + side, so.cols); ++x) hit[w.o][(size_t)y * so.cols + x]++;
+        // a grouped item covers the tile of every subband of its group (same size)
+        const int nm = w.nm() > 0 ? w.nm() : 1;
+        if (nm != (sub.grp > 0 ? sub.grp : 1) || w.o + nm > L.S) return fail("item %d has %d members", (int)k, nm);
+        for (int mk = 0; mk < nm; ++mk) {
+            const SubbandDev& sm = L.sb[w.o + mk];
+            const TileSub& subm = P.subs[w.o + mk];
+            if (sm.rows != so.rows || sm.cols != so.cols || subm.TS != sub.TS || subm.batch_begin != sub.batch_begin)
+                return fail("item %d member %d differs from the group's first subband", (int)k, mk);
+            for (int y = w.ty0; y < std::min(w.ty0 + side, so.rows); ++y)
+                for (int x = w.tx0; x < std::min(w.tx0 + side, so.cols); ++x) hit[w.o + mk][(size_t)y * so.cols + x]++;
+        }
     }
     for (int o = 0; o < L.S; ++o)
         for (size_t i = 0; i < hit[o].size(); ++i)

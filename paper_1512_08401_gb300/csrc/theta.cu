@@ -314,6 +314,7 @@ wdb_status temp_plan(const wdb_theta* th, const TilePlanHost& h, TempPlan& d, cu
     }
     p.n_items = (int)h.items.size();
     p.n_sup = h.n_sup;
+    p.n_grp = h.n_grp;
     p.buf_elems = h.buf_elems;
     p.smem_bytes = h.smem_bytes;
     d.a.sb = th->d_sb;
@@ -418,6 +419,12 @@ static wdb_status autotune_plans(wdb_theta* th, cudaStream_t st) {
         for (double cap : {2.0, 4.0})
             whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, cap, 0.0,
                                            true));
+        // and with grouped items (each input region staged once for every subband of a level)
+        for (int budget : {kTileSmemBudget, kTileSmemBudget * 3 / 2})
+            whole.push_back(make_tile_plan(L, th->tent[op], 4, budget, th->plan_ctas, &best, 0, 2.0, 0.0, false, true));
+        for (double cap : {1.0, 2.0, 4.0})
+            whole.push_back(make_tile_plan(L, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, nullptr, 0, cap, 0.0,
+                                           false, true));
         float best_ms = 1e30f;
         for (size_t k = 0; k < whole.size() && s == WDB_OK; ++k) {
             const float ms = time_plan(whole[k]);
@@ -461,6 +468,7 @@ static wdb_status upload_plan(wdb_theta* th, const TilePlanHost& h, TileArgs& a,
     }
     a.plan.n_items = (int)h.items.size();
     a.plan.n_sup = h.n_sup;
+    a.plan.n_grp = h.n_grp;
     a.plan.buf_elems = h.buf_elems;
     a.plan.smem_bytes = h.smem_bytes;
     a.sb = th->d_sb;
@@ -492,11 +500,11 @@ wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st) {
 
 // Planner plans in place of the FP32 plans (no autotuning); captured solve graphs hold the
 // old plans' arguments and are dropped.
-wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, bool super_tiles,
+wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, int tiling,
                         cudaStream_t st) {
     for (int op = 0; op < 2; ++op) {
         th->tplan[op][0] = make_tile_plan(th->lay, th->tent[op], 4, budget, th->plan_ctas, nullptr, 0, cap_share,
-                                          split_share, super_tiles);
+                                          split_share, tiling == 1, tiling == 2);
         WDB_TRY(upload_plan(th, th->tplan[op][0], th->targs[op][0], st));
     }
     th->tuned = 0;

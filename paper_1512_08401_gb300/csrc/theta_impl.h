@@ -27,7 +27,8 @@ wdb_status theta_build_device(wdb_theta* th, const double* psf_host, int kh, int
 wdb_status theta_finalize(wdb_theta* th, cudaStream_t st);
 void gather_entries(const Layout& L, const std::vector<Tap>& taps, std::vector<TileEntry> (&te)[2]);
 wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st);
-wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, bool super_tiles,
+// tiling: 0 ordinary tiles, 1 super tiles where they fit, 2 grouped items
+wdb_status theta_replan(wdb_theta* th, int budget, double cap_share, double split_share, int tiling,
                         cudaStream_t st);
 wdb_status theta_precond(wdb_theta* th, int kind, double eps, cudaStream_t st);
 std::vector<double> precond_table(const std::vector<double>& Md, const std::vector<double>& M2d, int kind,

@@ -22,8 +22,16 @@ struct PairBuild {
     int out, in, up, lg;
     int dy0 = 1 << 30, dy1 = -(1 << 30), dx0 = 1 << 30, dx1 = -(1 << 30);
     std::vector<const TileEntry*> taps;
-    int maxph = 0;     // taps applied per output: all taps (down), the fullest phase (up)
+    int maxph = 0;     // taps applied per output: all taps (down), the fullest phase (up); grouped
+                       // pairs: summed over the members
+    int nm = 1;        // grouped pairs: members (output subbands of the group)
+    std::vector<const TileEntry*> mtaps[4];   // grouped pairs: the taps of each member
+    int mmaxph[4] = {0, 0, 0, 0};
 };
+
+// First subband of the group of subband o (grouped plans): A_J and the three details of level
+// J form one group, the three details of every finer level another.
+int group_first(const Layout& L, int o) { return o < 4 ? 0 : 1 + 3 * ((o - 1) / 3); }
 
 // Cost model of one tile, in thread instructions (used to choose the tile side and, per
 // pair, staging against gathering from global memory / L2).
@@ -125,14 +133,19 @@ double subband_cost(const SubbandDev& so, const std::vector<PairBuild*>& prs, in
 
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int budget, int ctas,
                             const std::vector<TileTune>* tune, int level_only, double cap_share, double split_share,
-                            bool super_tiles) {
+                            bool super_tiles, bool grouped) {
     if (super_tiles) split_share = 0.0;   // a plan has split tiles or super tiles, not both
+    if (grouped) {   // a plan has grouped items, or split or super tiles
+        super_tiles = false;
+        split_share = 0.0;
+    }
     TilePlanHost plan;
     plan.esize = esize;
     std::map<std::pair<int, int>, PairBuild> pairs;
     for (const TileEntry& e : entries) {
-        PairBuild& p = pairs[{e.out, e.in}];
-        p.out = e.out;
+        const int u = grouped ? group_first(L, e.out) : e.out;
+        PairBuild& p = pairs[{u, e.in}];
+        p.out = u;
         p.in = e.in;
         p.up = e.up;
         p.lg = e.lg;
@@ -141,6 +154,13 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         p.dx0 = std::min(p.dx0, e.dx);
         p.dx1 = std::max(p.dx1, e.dx);
         p.taps.push_back(&e);
+        if (grouped) p.mtaps[e.out - u].push_back(&e);
+    }
+    // units of work: every subband, or (grouped) the first subband of every group
+    std::vector<int> unit_nm(L.S, 0);
+    for (int o = 0; o < L.S; ++o) {
+        const int u = grouped ? group_first(L, o) : o;
+        unit_nm[u] = std::max(unit_nm[u], o - u + 1);
     }
     std::vector<std::vector<PairBuild*>> by_out(L.S);
     for (auto& kv : pairs) by_out[kv.first.first].push_back(&kv.second);
@@ -154,12 +174,21 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
     std::vector<std::vector<double>> sub_bcost(L.S);
     for (int o = 0; o < L.S; ++o)
         for (PairBuild* pb : by_out[o]) {
-            if (!pb->up) {
-                pb->maxph = (int)pb->taps.size();
-            } else {
+            auto maxph_of = [&](const std::vector<const TileEntry*>& tl) {
+                if (!pb->up) return (int)tl.size();
                 std::vector<int> cnt(1 << (2 * pb->lg), 0);
-                for (const TileEntry* e : pb->taps) cnt[e->phase]++;
-                pb->maxph = *std::max_element(cnt.begin(), cnt.end());
+                for (const TileEntry* e : tl) cnt[e->phase]++;
+                return *std::max_element(cnt.begin(), cnt.end());
+            };
+            if (!grouped) {
+                pb->maxph = maxph_of(pb->taps);
+            } else {
+                pb->nm = unit_nm[o];
+                pb->maxph = 0;
+                for (int k = 0; k < pb->nm; ++k) {
+                    pb->mmaxph[k] = maxph_of(pb->mtaps[k]);
+                    pb->maxph += pb->mmaxph[k];
+                }
             }
         }
     // balance: the whole operator's modelled cost (each subband at its cheapest tile side)
@@ -171,6 +200,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
         for (int o = 0; o < L.S; ++o) {
             const SubbandDev& so = L.sb[o];
             ts_max[o] = std::min(32, next_pow2(std::max(so.rows, so.cols)));
+            if (grouped && group_first(L, o) != o) continue;   // counted with the group's first
             double bc = 1e300;
             for (int ts = ts_max[o]; ts >= 1; ts >>= 1)
                 bc = std::min(bc, subband_cost(so, by_out[o], ts, ts >= 8, esize, budget, tmp));
@@ -181,6 +211,7 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
     // goes below that: small operators accept some imbalance)
     const double item_cap = std::max(cap_share * total / std::max(1, ctas), 16.0 * kCostItem);
     for (int o = 0; o < L.S; ++o) {
+        if (grouped && group_first(L, o) != o) continue;   // worked by the group's items
         const SubbandDev& so = L.sb[o];
         // tile side and per-pair mode (staged in shared memory or gathered from global
         // memory) that minimise the modelled cost per output, among the sides whose tiles
@@ -358,39 +389,50 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 }
                 return (e.dy - pb.dy0) * g.PC + (e.dx - pb.dx0) + tp.soff;
             };
-            if (!pb.up) {
-                tp.ntap = (int)pb.taps.size();
-                for (const TileEntry* e : pb.taps) {
-                    plan.tap_off.push_back(offset(*e));
-                    plan.tap_lin.push_back(global[k] ? e->dy * cin + e->dx : 0);
-                    plan.tap_v.push_back((float)e->v);
-                    plan.tap_v64.push_back(e->v);
-                }
-            } else {
-                const int nph = r * r;
-                std::vector<std::vector<const TileEntry*>> ph(nph);
-                for (const TileEntry* e : pb.taps) ph[e->phase].push_back(e);
-                int mx = 0;
-                for (auto& v : ph) mx = std::max(mx, (int)v.size());
-                tp.ntap = mx;
-                for (int j = 0; j < mx; ++j)
-                    for (int qq = 0; qq < nph; ++qq) {
-                        if (j < (int)ph[qq].size()) {
-                            plan.tap_off.push_back(offset(*ph[qq][j]));
-                            plan.tap_lin.push_back(global[k] ? ph[qq][j]->dy * cin + ph[qq][j]->dx : 0);
-                            plan.tap_v.push_back((float)ph[qq][j]->v);
-                            plan.tap_v64.push_back(ph[qq][j]->v);
-                        } else {
-                            // padding: value 0 at the region origin (staged) or the
-                            // output's own input position (global)
-                            plan.tap_off.push_back(global[k] ? 0 : tp.soff);
-                            plan.tap_lin.push_back(0);
-                            plan.tap_v.push_back(0.f);
-                            plan.tap_v64.push_back(0.0);
-                        }
+            // taps member by member (one member unless the plan is grouped): down pairs
+            // their list, up pairs their phase table padded to the member's fullest phase
+            tp.nm = pb.nm;
+            for (int mk = 0; mk < 4; ++mk) tp.mtb[mk] = tp.mnt[mk] = 0;
+            int per_out = 0;
+            for (int mk = 0; mk < pb.nm; ++mk) {
+                const std::vector<const TileEntry*>& tl = grouped ? pb.mtaps[mk] : pb.taps;
+                tp.mtb[mk] = (int)plan.tap_off.size();
+                if (!pb.up) {
+                    tp.mnt[mk] = (int)tl.size();
+                    for (const TileEntry* e : tl) {
+                        plan.tap_off.push_back(offset(*e));
+                        plan.tap_lin.push_back(global[k] ? e->dy * cin + e->dx : 0);
+                        plan.tap_v.push_back((float)e->v);
+                        plan.tap_v64.push_back(e->v);
                     }
+                } else {
+                    const int nph = r * r;
+                    std::vector<std::vector<const TileEntry*>> ph(nph);
+                    for (const TileEntry* e : tl) ph[e->phase].push_back(e);
+                    int mx = 0;
+                    for (auto& v : ph) mx = std::max(mx, (int)v.size());
+                    tp.mnt[mk] = mx;
+                    for (int j = 0; j < mx; ++j)
+                        for (int qq = 0; qq < nph; ++qq) {
+                            if (j < (int)ph[qq].size()) {
+                                plan.tap_off.push_back(offset(*ph[qq][j]));
+                                plan.tap_lin.push_back(global[k] ? ph[qq][j]->dy * cin + ph[qq][j]->dx : 0);
+                                plan.tap_v.push_back((float)ph[qq][j]->v);
+                                plan.tap_v64.push_back(ph[qq][j]->v);
+                            } else {
+                                // padding: value 0 at the region origin (staged) or the
+                                // output's own input position (global)
+                                plan.tap_off.push_back(global[k] ? 0 : tp.soff);
+                                plan.tap_lin.push_back(0);
+                                plan.tap_v.push_back(0.f);
+                                plan.tap_v64.push_back(0.0);
+                            }
+                        }
+                }
+                per_out += tp.mnt[mk];
             }
-            taps_per_out += tp.ntap;
+            tp.ntap = tp.mnt[0];
+            taps_per_out += per_out;
             plan.pairs.push_back(tp);
             bt.pair_end = (int)plan.pairs.size();
             if (!global[k] && (!pb.up || tp.tst)) bt.tap_end = (int)plan.tap_off.size();
@@ -428,10 +470,17 @@ TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entri
                 plan.macs += (long long)(outs * taps_per_out);
                 if (level_only <= 0 || so.level == level_only)
                     items.push_back({TileItem{o, a * ST, b * ST, sub.batch_begin, sub.batch_end,
-                                              sub.lgTS | (sub.e4 << 8) | (sub.sup << 9), 1 << 16, -1},
+                                              sub.lgTS | (sub.e4 << 8) | (sub.sup << 9) |
+                                                  (grouped ? unit_nm[o] << 12 : 0),
+                                              1 << 16, -1},
                                      cost});
             }
         plan.n_sup += sup ? 1 : 0;
+        if (grouped) {   // the group's other subbands share its tiles, pairs and batches
+            sub.grp = unit_nm[o];
+            for (int k = 1; k < unit_nm[o]; ++k) plan.subs[o + k] = sub;
+            plan.n_grp += 1;
+        }
     }
     if (split_share > 0.0 && !items.empty()) {
         // split the tiles that would dominate one CTA's share into parts of whole batches
@@ -794,10 +843,12 @@ __device__ __forceinline__ void up_taps4(TapSrc<T> ts, int j0, int n, int G, int
 // Accumulate the pairs of batch `bi` of tile `w` (staged in S) into acc.
 // (oy, ox): offset of the computed tile inside the staged one (a super tile's quarter; 0, 0
 // for ordinary tiles)
-template <typename T>
+// M: accumulator sets (1, or 4 for grouped items, whose pairs hold one tap list per member
+// output subband; the region and the per-thread set-up of a pair serve every member).
+template <typename T, int M>
 __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* __restrict__ in, const TileItem& w,
                                               const SubbandDev& so, int bi, const T* __restrict__ S,
-                                              const PairSm* __restrict__ tab, const ThreadMap& tm, T (&acc)[4],
+                                              const PairSm* __restrict__ tab, const ThreadMap& tm, T (&acc)[M][4],
                                               int oy = 0, int ox = 0) {
     const TileBatch bt = plan.batches[bi];
     const TapSrc<T> stap = staged_taps<T>(S, bt);
@@ -808,80 +859,95 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
         const TilePair P = tab[i].p;
         const int sh = tab[i].shift;   // staged column of the region's first column (vec pairs)
         const int lg = P.lg, r = 1 << lg, m = r - 1;
+        const int nmem = M == 1 ? 1 : P.nm;
         if (P.mode == kDown) {
-            const TapSrc<T> ts = stap + P.tap_begin;
             const T* __restrict__ Sb = S + (tm.ly + oy) * P.PC + tm.lx + ox + sh;
-            if (E == 4) {
-                if (tm.sx == 8) down_taps4<8, T>(ts, g, P.ntap, G, Sb, acc);
-                else if (tm.sx == 4) down_taps4<4, T>(ts, g, P.ntap, G, Sb, acc);
-                else down_taps4<2, T>(ts, g, P.ntap, G, Sb, acc);
-            } else {
-                T a0 = 0, a1 = 0;
-                int j = g;
-                for (; j + G < P.ntap; j += 2 * G) {
-                    int o0, o1;
-                    T v0, v1;
-                    ts.get(j, o0, v0);
-                    ts.get(j + G, o1, v1);
-                    a0 = fma(v0, Sb[o0], a0);
-                    a1 = fma(v1, Sb[o1], a1);
+            for (int mk = 0; mk < nmem; ++mk) {
+                const TapSrc<T> ts = stap + (M == 1 ? P.tap_begin : P.mtb[mk]);
+                const int ntap = M == 1 ? P.ntap : P.mnt[mk];
+                T (&ac)[4] = acc[mk];
+                if (E == 4) {
+                    if (tm.sx == 8) down_taps4<8, T>(ts, g, ntap, G, Sb, ac);
+                    else if (tm.sx == 4) down_taps4<4, T>(ts, g, ntap, G, Sb, ac);
+                    else down_taps4<2, T>(ts, g, ntap, G, Sb, ac);
+                } else {
+                    T a0 = 0, a1 = 0;
+                    int j = g;
+                    for (; j + G < ntap; j += 2 * G) {
+                        int o0, o1;
+                        T v0, v1;
+                        ts.get(j, o0, v0);
+                        ts.get(j + G, o1, v1);
+                        a0 = fma(v0, Sb[o0], a0);
+                        a1 = fma(v1, Sb[o1], a1);
+                    }
+                    if (j < ntap) {
+                        int o0;
+                        T v0;
+                        ts.get(j, o0, v0);
+                        a0 = fma(v0, Sb[o0], a0);
+                    }
+                    ac[0] += a0 + a1;
                 }
-                if (j < P.ntap) {
-                    int o0;
-                    T v0;
-                    ts.get(j, o0, v0);
-                    a0 = fma(v0, Sb[o0], a0);
-                }
-                acc[0] += a0 + a1;
             }
         } else if (P.mode == kUp) {
-            // the phase tables (r^2 interleaved phases per tap slot) stay in global memory:
-            // neighbouring outputs read neighbouring phases, and every tile of the subband
-            // reads the same table, so these loads are coalesced L1/L2 hits
+            // the phase tables (r^2 interleaved phases per tap slot) are staged with the batch
+            // (tst) or read from global memory, where neighbouring outputs read neighbouring
+            // phases and every tile of the subband reads the same table (L1/L2 hits)
             const int rr = r * r;
             const int py = w.ty0 + oy + tm.ly, px = w.tx0 + ox + tm.lx;
             const int rowb = ((py >> lg) - (w.ty0 >> lg)) * P.PC + sh;
-            const bool st = P.tst != 0;   // phase tables staged with the batch
-            const TapSrc<T> gts = (st ? stap : global_taps<T>(plan)) + P.tap_begin;
+            const bool st = P.tst != 0;
+            const TapSrc<T> gts0 = st ? stap : global_taps<T>(plan);
             if (E == 4 && st && lg <= tm.lgsx) {
                 const int ph = ((py & m) << lg) + (px & m);
                 const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
                 const int stepc = tm.lgsx - lg;   // log2 of the coarse column step
-                if (stepc == 2) up_taps4<4, T>(gts + ph, g, P.ntap, G, rr, Sb, acc);
-                else if (stepc == 1) up_taps4<2, T>(gts + ph, g, P.ntap, G, rr, Sb, acc);
-                else up_taps4<1, T>(gts + ph, g, P.ntap, G, rr, Sb, acc);
+                for (int mk = 0; mk < nmem; ++mk) {
+                    const TapSrc<T> gts = gts0 + ((M == 1 ? P.tap_begin : P.mtb[mk]) + ph);
+                    const int ntap = M == 1 ? P.ntap : P.mnt[mk];
+                    if (stepc == 2) up_taps4<4, T>(gts, g, ntap, G, rr, Sb, acc[mk]);
+                    else if (stepc == 1) up_taps4<2, T>(gts, g, ntap, G, rr, Sb, acc[mk]);
+                    else up_taps4<1, T>(gts, g, ntap, G, rr, Sb, acc[mk]);
+                }
             } else if (E == 4) {
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int pxe = px + tm.sx * e;
                     const int ph = ((py & m) << lg) + (pxe & m);
                     const T* __restrict__ Sb = S + rowb + ((pxe >> lg) - (w.tx0 >> lg));
-                    TapSrc<T> ts = gts + (ph + g * rr);
                     const int stp = G * rr;
+                    for (int mk = 0; mk < nmem; ++mk) {
+                        TapSrc<T> ts = gts0 + ((M == 1 ? P.tap_begin : P.mtb[mk]) + ph + g * rr);
+                        const int ntap = M == 1 ? P.ntap : P.mnt[mk];
+                        T a = 0;
+                        for (int j = g; j < ntap; j += G) {
+                            int o;
+                            T v;
+                            ts.get(0, o, v);
+                            a = fma(v, Sb[o], a);
+                            ts = ts + stp;
+                        }
+                        acc[mk][e] += a;
+                    }
+                }
+            } else {
+                const int ph = ((py & m) << lg) + (px & m);
+                const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
+                const int stp = G * rr;
+                for (int mk = 0; mk < nmem; ++mk) {
+                    TapSrc<T> ts = gts0 + ((M == 1 ? P.tap_begin : P.mtb[mk]) + ph + g * rr);
+                    const int ntap = M == 1 ? P.ntap : P.mnt[mk];
                     T a = 0;
-                    for (int j = g; j < P.ntap; j += G) {
+                    for (int j = g; j < ntap; j += G) {
                         int o;
                         T v;
                         ts.get(0, o, v);
                         a = fma(v, Sb[o], a);
                         ts = ts + stp;
                     }
-                    acc[e] += a;
+                    acc[mk][0] += a;
                 }
-            } else {
-                const int ph = ((py & m) << lg) + (px & m);
-                const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
-                TapSrc<T> ts = gts + (ph + g * rr);
-                const int stp = G * rr;
-                T a = 0;
-                for (int j = g; j < P.ntap; j += G) {
-                    int o;
-                    T v;
-                    ts.get(0, o, v);
-                    a = fma(v, Sb[o], a);
-                    ts = ts + stp;
-                }
-                acc[0] += a;
             }
         } else {
             // gather from global memory (regions larger than the shared-memory budget, or
@@ -898,23 +964,27 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                 const bool cols_ok = px0 + 3 * tm.sx < so.cols && bx0 + P.x0 >= 0 && bx0 + 3 * bstep + P.x0 + P.RC <= C;
                 if (rows_ok && cols_ok) {
                     const T* __restrict__ bp = src + (size_t)by * C + bx0;
-                    const int* __restrict__ tl = plan.tap_lin + P.tap_begin;
-                    const T* __restrict__ tv = gvals + P.tap_begin;
-                    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+                    for (int mk = 0; mk < nmem; ++mk) {
+                        const int tb = M == 1 ? P.tap_begin : P.mtb[mk];
+                        const int ntap = M == 1 ? P.ntap : P.mnt[mk];
+                        const int* __restrict__ tl = plan.tap_lin + tb;
+                        const T* __restrict__ tv = gvals + tb;
+                        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll 2
-                    for (int j = g; j < P.ntap; j += G) {
-                        const int l = __ldg(tl + j);
-                        const T v = __ldg(tv + j);
-                        const T* __restrict__ q = bp + l;
-                        a0 = fma(v, __ldg(q), a0);
-                        a1 = fma(v, __ldg(q + bstep), a1);
-                        a2 = fma(v, __ldg(q + 2 * bstep), a2);
-                        a3 = fma(v, __ldg(q + 3 * bstep), a3);
+                        for (int j = g; j < ntap; j += G) {
+                            const int l = __ldg(tl + j);
+                            const T v = __ldg(tv + j);
+                            const T* __restrict__ q = bp + l;
+                            a0 = fma(v, __ldg(q), a0);
+                            a1 = fma(v, __ldg(q + bstep), a1);
+                            a2 = fma(v, __ldg(q + 2 * bstep), a2);
+                            a3 = fma(v, __ldg(q + 3 * bstep), a3);
+                        }
+                        acc[mk][0] += a0;
+                        acc[mk][1] += a1;
+                        acc[mk][2] += a2;
+                        acc[mk][3] += a3;
                     }
-                    acc[0] += a0;
-                    acc[1] += a1;
-                    acc[2] += a2;
-                    acc[3] += a3;
                     continue;
                 }
             }
@@ -923,48 +993,52 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                 if (e >= E) continue;
                 const int py = w.ty0 + oy + tm.ly, px = w.tx0 + ox + tm.lx + tm.sx * e;
                 if (py >= so.rows || px >= so.cols) continue;
-                int by, bx, tb, step;
+                int by, bx, pho, step;
                 if (P.mode == kDownGlobal) {
                     by = py << lg;
                     bx = px << lg;
-                    tb = P.tap_begin;
+                    pho = 0;
                     step = 1;
                 } else {
                     by = py >> lg;
                     bx = px >> lg;
-                    tb = P.tap_begin + (((py & m) << lg) + (px & m));
+                    pho = ((py & m) << lg) + (px & m);
                     step = r * r;
                 }
-                T a = 0;
                 // interior: every tap of the pair lands inside the input subband, no wrap
                 const bool inside = by + P.y0 >= 0 && by + P.y0 + P.RR <= R && bx + P.x0 >= 0 && bx + P.x0 + P.RC <= C;
-                if (inside) {
-                    // four independent chains (offset, then input) in flight
-                    const T* __restrict__ bp = src + (size_t)by * C + bx;
-                    const int* __restrict__ tl = plan.tap_lin + tb;
-                    const T* __restrict__ tv = gvals + tb;
-                    T a1 = 0, a2 = 0, a3 = 0;
-                    int j = g;
-                    for (; j + 3 * G < P.ntap; j += 4 * G) {
-                        const int l0 = __ldg(tl + j * step), l1 = __ldg(tl + (j + G) * step);
-                        const int l2 = __ldg(tl + (j + 2 * G) * step), l3 = __ldg(tl + (j + 3 * G) * step);
-                        const T v0 = __ldg(tv + j * step), v1 = __ldg(tv + (j + G) * step);
-                        const T v2 = __ldg(tv + (j + 2 * G) * step), v3 = __ldg(tv + (j + 3 * G) * step);
-                        a = fma(v0, __ldg(bp + l0), a);
-                        a1 = fma(v1, __ldg(bp + l1), a1);
-                        a2 = fma(v2, __ldg(bp + l2), a2);
-                        a3 = fma(v3, __ldg(bp + l3), a3);
+                for (int mk = 0; mk < nmem; ++mk) {
+                    const int tb = (M == 1 ? P.tap_begin : P.mtb[mk]) + pho;
+                    const int ntap = M == 1 ? P.ntap : P.mnt[mk];
+                    T a = 0;
+                    if (inside) {
+                        // four independent chains (offset, then input) in flight
+                        const T* __restrict__ bp = src + (size_t)by * C + bx;
+                        const int* __restrict__ tl = plan.tap_lin + tb;
+                        const T* __restrict__ tv = gvals + tb;
+                        T a1 = 0, a2 = 0, a3 = 0;
+                        int j = g;
+                        for (; j + 3 * G < ntap; j += 4 * G) {
+                            const int l0 = __ldg(tl + j * step), l1 = __ldg(tl + (j + G) * step);
+                            const int l2 = __ldg(tl + (j + 2 * G) * step), l3 = __ldg(tl + (j + 3 * G) * step);
+                            const T v0 = __ldg(tv + j * step), v1 = __ldg(tv + (j + G) * step);
+                            const T v2 = __ldg(tv + (j + 2 * G) * step), v3 = __ldg(tv + (j + 3 * G) * step);
+                            a = fma(v0, __ldg(bp + l0), a);
+                            a1 = fma(v1, __ldg(bp + l1), a1);
+                            a2 = fma(v2, __ldg(bp + l2), a2);
+                            a3 = fma(v3, __ldg(bp + l3), a3);
+                        }
+                        for (; j < ntap; j += G) a = fma(__ldg(tv + j * step), __ldg(bp + __ldg(tl + j * step)), a);
+                        a += (a1 + a2) + a3;
+                    } else {
+                        for (int j = g; j < ntap; j += G) {
+                            const int pk = __ldg(plan.tap_off + tb + j * step);
+                            const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
+                            a += __ldg(gvals + tb + j * step) * src[(size_t)yy * C + xx];
+                        }
                     }
-                    for (; j < P.ntap; j += G) a = fma(__ldg(tv + j * step), __ldg(bp + __ldg(tl + j * step)), a);
-                    a += (a1 + a2) + a3;
-                } else {
-                    for (int j = g; j < P.ntap; j += G) {
-                        const int pk = __ldg(plan.tap_off + tb + j * step);
-                        const int yy = wrap1(by + (pk >> 16), R), xx = wrap1(bx + (int)(short)(pk & 0xffff), C);
-                        a += __ldg(gvals + tb + j * step) * src[(size_t)yy * C + xx];
-                    }
+                    acc[mk][e] += a;
                 }
-                acc[e] += a;
             }
         }
     }
@@ -1080,9 +1154,11 @@ __device__ __forceinline__ void epilogue(const TileItem& w, const SubbandDev& so
 // SPLIT: the plan has split tiles (a separate instance, so that plans without them run code
 // that carries none of the combining step)
 // SUP: the plan has super tiles (likewise a separate instance)
-template <typename T, int EPI, bool SPLIT, bool SUP>
+// GRP: the plan has grouped items (the tile of up to four subbands per item; likewise)
+template <typename T, int EPI, bool SPLIT, bool SUP, bool GRP>
 __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const T* __restrict__ in,
                                                             T* __restrict__ out, EpiArgs ep) {
+    constexpr int M = GRP ? 4 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* const buf0 = reinterpret_cast<T*>(smem_raw);
     T* const buf1 = buf0 + A.plan.buf_elems;
@@ -1115,7 +1191,11 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
     PairSm* tab_next = tab_buf[1];
     if (it < plan.n_items) stage_batch<T>(plan, in, w, bi, S, tab);
     cp_async_commit();
-    T acc[4] = {0, 0, 0, 0};
+    T acc[M][4];
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[k][e] = 0;
     while (it < plan.n_items) {
         int nit = it, nbi = bi + 1;
         TileItem nw = w;
@@ -1141,22 +1221,37 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
             for (int q = 0; q < 4; ++q) {
                 const int oy = (q >> 1) << w.lgTS(), ox = (q & 1) << w.lgTS();
                 if (w.ty0 + oy >= so.rows || w.tx0 + ox >= so.cols) continue;
-                compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc, oy, ox);
+                compute_batch<T, M>(plan, in, w, so, bi, S, tab, tm, acc, oy, ox);
                 TileItem wq = w;
                 wq.ty0 += oy;
                 wq.tx0 += ox;
-                epilogue<T, EPI>(wq, so, tm, acc, out, ep, beta, pt);
+                epilogue<T, EPI>(wq, so, tm, acc[0], out, ep, beta, pt);
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[e] = 0;
+                for (int e = 0; e < 4; ++e) acc[0][e] = 0;
             }
         } else {
-            compute_batch<T>(plan, in, w, so, bi, S, tab, tm, acc);
+            compute_batch<T, M>(plan, in, w, so, bi, S, tab, tm, acc);
             if (bi + 1 == w.batch_end) {
-                group_reduce<T>(tm, acc, red_buf);
-                if (!SPLIT || w.split < (2 << 16) || combine_parts<T>(plan, w, tm, acc))
-                    epilogue<T, EPI>(w, so, tm, acc, out, ep, beta, pt);
+                if (!GRP) {
+                    group_reduce<T>(tm, acc[0], red_buf);
+                    if (!SPLIT || w.split < (2 << 16) || combine_parts<T>(plan, w, tm, acc[0]))
+                        epilogue<T, EPI>(w, so, tm, acc[0], out, ep, beta, pt);
+                } else {
+                    // one epilogue per member subband of the group (same geometry)
+                    const int nm = w.nm() > 0 ? w.nm() : 1;
+                    for (int k = 0; k < M; ++k) {
+                        if (k >= nm) break;
+                        if (k > 0 && tm.G > 1) __syncthreads();   // red_buf reused
+                        group_reduce<T>(tm, acc[k], red_buf);
+                        TileItem wk = w;
+                        wk.o = w.o + k;
+                        epilogue<T, EPI>(wk, A.sb[wk.o], tm, acc[k], out, ep, beta, pt);
+                    }
+                }
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[e] = 0;
+                for (int k = 0; k < M; ++k)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[k][e] = 0;
             }
         }
         it = nit;
@@ -1271,7 +1366,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         stage_batch<float>(pl, in_of(bw.p), pl.items[bw.item], bi, S, tab);
     }
     cp_async_commit();
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[1][4] = {{0.f, 0.f, 0.f, 0.f}};
     Partials pt;
     while (it < B.n_items) {
         const BatchItem bw = B.items[it];
@@ -1297,9 +1392,9 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         __syncthreads();
         const SubbandDev so = P.sb[w.o];
         const ThreadMap tm = thread_map(w);
-        compute_batch<float>(pl, in_of(bw.p), w, so, bi, S, tab, tm, acc);
+        compute_batch<float, 1>(pl, in_of(bw.p), w, so, bi, S, tab, tm, acc);
         if (bi + 1 == w.batch_end) {
-            group_reduce<float>(tm, acc, red_buf);
+            group_reduce<float>(tm, acc[0], red_buf);
             EpiArgs ep{};
             ep.x0 = P.x0;
             ep.y = P.y;
@@ -1311,10 +1406,10 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
                 const int k = P.st->k;
                 beta = P.st->ista ? 0.f : (float)(k - 1) / (float)(k + 2);
             }
-            epilogue<float, EPI>(w, so, tm, acc, (EPI == kK1) ? P.r : nullptr, ep, beta, pt);
+            epilogue<float, EPI>(w, so, tm, acc[0], (EPI == kK1) ? P.r : nullptr, ep, beta, pt);
             flush_partials<EPI>(pt, P.sums, red_d);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[e] = 0.f;
+            for (int e = 0; e < 4; ++e) acc[0][e] = 0.f;
         }
         it = nit;
         bi = nbi;
@@ -1366,11 +1461,11 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
 
 // pdl: programmatic dependent launch, so that this grid's CTAs are scheduled while the
 // previous kernel of the stream drains (the kernel waits for that grid before its work)
-template <typename T, int EPI, bool SPLIT, bool SUP>
+template <typename T, int EPI, bool SPLIT, bool SUP, bool GRP>
 wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl) {
     static unsigned long long attr = 0ull;
     if (!done_on_device(&attr)) {
-        WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI, SPLIT, SUP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        WDB_CK(cudaFuncSetAttribute(tile_kernel<T, EPI, SPLIT, SUP, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     200 * 1024));
         mark_on_device(&attr);
     }
@@ -1385,9 +1480,9 @@ wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs&
         at[0].val.programmaticStreamSerializationAllowed = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        WDB_CK(cudaLaunchKernelEx(&cfg, tile_kernel<T, EPI, SPLIT, SUP>, A, in, out, ep));
+        WDB_CK(cudaLaunchKernelEx(&cfg, tile_kernel<T, EPI, SPLIT, SUP, GRP>, A, in, out, ep));
     } else {
-        tile_kernel<T, EPI, SPLIT, SUP><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
+        tile_kernel<T, EPI, SPLIT, SUP, GRP><<<A.grid, kTileThreads, A.plan.smem_bytes, st>>>(A, in, out, ep);
     }
     count_launch();
     WDB_CK(cudaGetLastError());
@@ -1398,9 +1493,10 @@ wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs&
 template <typename T, int EPI>
 wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl = false) {
     constexpr bool f32 = sizeof(T) == 4;
-    if (f32 && A.plan.split_ctr) return launch_tile_as<T, EPI, f32, false>(A, in, out, ep, st, pdl);
-    if (f32 && A.plan.n_sup > 0) return launch_tile_as<T, EPI, false, f32>(A, in, out, ep, st, pdl);
-    return launch_tile_as<T, EPI, false, false>(A, in, out, ep, st, pdl);
+    if (f32 && A.plan.split_ctr) return launch_tile_as<T, EPI, f32, false, false>(A, in, out, ep, st, pdl);
+    if (f32 && A.plan.n_sup > 0) return launch_tile_as<T, EPI, false, f32, false>(A, in, out, ep, st, pdl);
+    if (f32 && A.plan.n_grp > 0) return launch_tile_as<T, EPI, false, false, f32>(A, in, out, ep, st, pdl);
+    return launch_tile_as<T, EPI, false, false, false>(A, in, out, ep, st, pdl);
 }
 
 template <int EPI>
@@ -1422,9 +1518,9 @@ int tile_grid(int smem_bytes) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(tile_kernel<float, kK2, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(tile_kernel<float, kK2, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          200 * 1024);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2, false, false>, kTileThreads,
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_kernel<float, kK2, false, false, false>, kTileThreads,
                                                   smem_bytes);
     if (sms <= 0) sms = 1;
     if (per <= 0) per = 1;

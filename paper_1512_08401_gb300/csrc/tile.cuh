@@ -38,6 +38,8 @@ struct alignas(16) TilePair {
     int vec;          // 1: rows staged in 16-byte chunks from a 4-aligned column (up or r = 1 pairs)
     int tst;          // up pairs: 1 when the phase tables are staged with the batch (else read from
                       // global memory)
+    int nm;           // output subbands that read this region (grouped items: up to 4; else 1)
+    int mtb[4], mnt[4];   // per output subband of the group: first tap and taps (up: per phase)
 };
 
 constexpr int kMaxBatchPairs = 16;   // pairs per batch (their descriptors sit in shared memory)
@@ -49,6 +51,8 @@ struct alignas(16) TileSub {      // per output subband
     int batch_begin, batch_end;   // batches of pairs whose staged regions share one buffer
     int e4;           // 1: 4 outputs per thread (TS >= 8), 0: 1 output per thread
     int sup;          // 1: work items are super tiles (2 x 2 tiles of side TS staged together)
+    int grp;          // grouped items: subbands of this subband's group (the item's o is the first)
+    int pad[3];
 };
 
 struct TileTune {     // autotuner's choice for one output subband (ts = 0: the planner's)
@@ -71,6 +75,7 @@ struct alignas(16) TileItem {     // one tile (or one part of it); carries what 
     int batch_begin, batch_end;   // batches of the subband this item accumulates
     int geo;                      // the subband's tile side and thread map:
                                   // lgTS | e4 << 8 | sup << 9 (sup: a 2 x 2 super tile)
+                                  // | nm << 12 (grouped items: the tile of subbands o .. o + nm - 1)
     int split;                    // part | nparts << 16 (nparts > 1: the tile's batches are split
                                   // over nparts items)
     int sid;                      // split tiles: index of the arrival counter and partial sums
@@ -90,6 +95,10 @@ struct alignas(16) TileItem {     // one tile (or one part of it); carries what 
     __host__ __device__
 #endif
     int sup() const { return (geo >> 9) & 1; }
+#ifdef __CUDACC__
+    __host__ __device__
+#endif
+    int nm() const { return (geo >> 12) & 7; }
 #ifdef __CUDACC__
     __host__ __device__
 #endif
@@ -129,6 +138,7 @@ struct TilePlanDev {
     const double* tap_v64;
     const TapOV* tap_ov;      // (tap_off, tap_v) interleaved: the FP32 kernels' tap records
     int n_sup;                // subbands tiled in super tiles (0: none)
+    int n_grp;                // groups of subbands worked together (0: none)
     unsigned int* split_ctr;  // per split tile: parts finished (zero between launches)
     const long long* split_base;   // per split tile: first element of its partial sums
     void* split_buf;          // per split tile: nparts x TS^2 partial sums (element type of the plan)
@@ -151,6 +161,7 @@ struct TilePlanHost {
     std::vector<double> item_cost;   // estimated cost of every item (items are sorted by it)
     int esize = 4;                   // element size (4: FP32, 8: FP64)
     int n_sup = 0;                   // subbands tiled in super tiles
+    int n_grp = 0;                   // groups of subbands worked together (grouped items)
     int n_split = 0;                 // split tiles
     std::vector<long long> split_base;   // first partial-sum element of each split tile
     long long split_elems = 0;       // partial-sum elements of all split tiles
@@ -172,9 +183,14 @@ struct TileEntry {             // one tap of one pair, in gather form
 // part to finish sums the parts' partial sums in part order and runs the epilogue.
 // super_tiles: subbands of 32-tiles whose pairs all fit one buffer for a 64-tile are worked
 // in items of 2 x 2 tiles staged together (no split tiles then).
+// grouped: the subbands of one level (A_J with the level-J details) are worked together: an
+// item is one tile of every subband of the group, each input region is staged once for all
+// of them (the union of their pairs' regions) and each member keeps its own taps (no split
+// or super tiles then).
 TilePlanHost make_tile_plan(const Layout& L, const std::vector<TileEntry>& entries, int esize, int smem_budget,
                             int ctas = 456, const std::vector<TileTune>* tune = nullptr, int level_only = 0,
-                            double cap_share = 2.0, double split_share = 0.0, bool super_tiles = false);
+                            double cap_share = 2.0, double split_share = 0.0, bool super_tiles = false,
+                            bool grouped = false);
 
 struct TileQueue {             // device counters of one operator launch
     unsigned int next;         // next work item

@@ -32,7 +32,7 @@ class WdbError(RuntimeError):
 
 class PlanSummary(C.Structure):
     _fields_ = [("items", C.c_int), ("pairs", C.c_int), ("batches", C.c_int), ("split_tiles", C.c_int),
-                ("super_subbands", C.c_int), ("smem_bytes", C.c_int), ("macs", C.c_longlong)]
+                ("super_subbands", C.c_int), ("smem_bytes", C.c_int), ("macs", C.c_longlong), ("groups", C.c_int)]
 
 
 class ThetaInfo(C.Structure):
@@ -41,7 +41,7 @@ class ThetaInfo(C.Structure):
                 ("K_eff", C.c_longlong), ("n_taps", C.c_longlong), ("n_candidates", C.c_longlong),
                 ("theta_max_abs", C.c_double), ("phase_table_len", C.c_int), ("build_ms", C.c_double),
                 ("plan_tuned", C.c_int), ("plan_items", C.c_int * 2), ("plan_split_tiles", C.c_int * 2),
-                ("plan_super_subbands", C.c_int * 2)]
+                ("plan_super_subbands", C.c_int * 2), ("plan_groups", C.c_int * 2)]
 
 
 class SolveParams(C.Structure):
@@ -278,10 +278,12 @@ class Theta:
     def save(self, path):
         _check(lib().wdb_theta_save(self._h, path.encode()))
 
-    def replan(self, smem_budget=0, cap_share=0.0, split_share=0.0, super_tiles=False, stream=None):
-        """Planner plans for the FP32 kernels in place of the autotuned ones (wdb_theta_replan)."""
-        _check(lib().wdb_theta_replan(self._h, int(smem_budget), float(cap_share), float(split_share),
-                                      1 if super_tiles else 0, _stream(stream)))
+    def replan(self, smem_budget=0, cap_share=0.0, split_share=0.0, super_tiles=False, grouped=False, stream=None):
+        """Planner plans for the FP32 kernels in place of the autotuned ones (wdb_theta_replan);
+        super_tiles: 2 x 2 super tiles where they fit; grouped: items over every subband of a level."""
+        mode = 2 if grouped else (1 if super_tiles else 0)
+        _check(lib().wdb_theta_replan(self._h, int(smem_budget), float(cap_share), float(split_share), mode,
+                                      _stream(stream)))
         self.info = self._info()
 
     def apply(self, x, out, transpose=False, stream=None):
@@ -388,7 +390,7 @@ class FFTOp:
 
 
 def tile_plan_check(n_rows, n_cols, levels, a, b, oy, ox, v, transpose=False, esize=4, smem_budget=0,
-                    cap_share=0.0, split_share=0.0, super_tiles=False, ctas=0):
+                    cap_share=0.0, split_share=0.0, super_tiles=False, ctas=0, grouped=False):
     """Build one operator's tile plan for a tap list on the host and check its invariants
     (wdb_tile_plan_check); returns the plan summary as a dict, raises WdbError on a fault."""
     a, pa = _i32(a)
@@ -398,8 +400,8 @@ def tile_plan_check(n_rows, n_cols, levels, a, b, oy, ox, v, transpose=False, es
     v, pv = _f64(v)
     sm = PlanSummary()
     _check(lib().wdb_tile_plan_check(n_rows, n_cols, levels, len(v), pa, pb, py, px, pv, 1 if transpose else 0,
-                                      esize, smem_budget, cap_share, split_share, 1 if super_tiles else 0, ctas,
-                                      C.byref(sm)))
+                                      esize, smem_budget, cap_share, split_share,
+                                      2 if grouped else (1 if super_tiles else 0), ctas, C.byref(sm)))
     return {f: getattr(sm, f) for f, _ in PlanSummary._fields_}
 
 

@@ -161,7 +161,8 @@ def test_apply_parity(wdb, name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("budget,cap,split", [(32768, 2.0, 0.25), (8192, 1.0, 0.05), (98304, 4.0, 0.0)])
+@pytest.mark.parametrize("budget,cap,split", [(32768, 2.0, 0.25), (8192, 1.0, 0.05), (98304, 4.0, 0.0),
+                                              (32768, 2.0, -1.0), (8192, 1.0, -1.0)])
 def test_planner_plans_and_split_tiles_match_oracle(wdb, name, budget, cap, split):
     """Planner plans in place of the autotuned ones, with the heaviest tiles split at batch
     boundaries over several CTAs (the last part to finish adds the parts' partial sums in
@@ -170,12 +171,16 @@ def test_planner_plans_and_split_tiles_match_oracle(wdb, name, budget, cap, spli
     rng = np.random.default_rng(15)
     case = build_case(psf, nr, nc, J, 30 * nr * nc, rng.standard_normal((nr, nc)))
     g = gpu_from_oracle(wdb, case, nr, nc, J)
-    g.replan(budget, cap, split)
+    if split < 0:   # grouped items instead of split tiles
+        g.replan(budget, cap, 0.0, grouped=True)
+        assert min(g.info.plan_groups) == J
+    else:
+        g.replan(budget, cap, split)
     info = g.info
     assert info.plan_tuned == 0
-    if split == 0.0:
+    if split <= 0.0:
         assert list(info.plan_split_tiles) == [0, 0]
-    if budget == 8192:
+    if budget == 8192 and split > 0:
         assert sum(info.plan_split_tiles) > 0   # small buffers: several batches per tile
     y = rng.standard_normal(nr * nc)
     out = torch.zeros(nr * nc, device="cuda")
@@ -189,7 +194,7 @@ def test_planner_plans_and_split_tiles_match_oracle(wdb, name, budget, cap, spli
         g.replan(98305, 2.0, 0.0)
 
 
-@pytest.mark.parametrize("plan", ["split", "super"])
+@pytest.mark.parametrize("plan", ["split", "super", "grouped"])
 def test_split_and_super_tiles_fista_trajectory_parity(wdb, plan):
     """Kernels 1 and 2 over plans with split tiles, or with super tiles (2 x 2 tiles staged
     together and computed one after the other): the FISTA trajectory of the oracle, and the
@@ -204,6 +209,15 @@ def test_split_and_super_tiles_fista_trajectory_parity(wdb, plan):
     if plan == "split":
         g.replan(8192, 1.0, 0.05)
         assert min(g.info.plan_split_tiles) > 0
+    elif plan == "grouped":
+        g.replan(grouped=True)
+        assert min(g.info.plan_groups) == J and list(g.info.plan_super_subbands) == [0, 0]
+        y = np.random.default_rng(17).standard_normal(n * n)
+        out = torch.zeros(n * n, device="cuda")
+        g.apply(dev(y), out)
+        assert rel_max(host(out), case.th.mat @ y) < 2e-6
+        g.apply(dev(y), out, transpose=True)
+        assert rel_max(host(out), case.th.matT @ y) < 2e-6
     else:
         g.replan(32768, 2.0, 0.0, super_tiles=True)
         assert min(g.info.plan_super_subbands) > 0 and list(g.info.plan_split_tiles) == [0, 0]

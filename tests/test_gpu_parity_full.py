@@ -102,6 +102,9 @@ def test_apply_parity_deep_levels_all_plans(wdb, name):
     check_apply(wdb, g, case.th.mat, case.th.matT, n * n, 2)           # super tiles where they fit
     g.replan()
     check_apply(wdb, g, case.th.mat, case.th.matT, n * n, 3)           # planner plan
+    g.replan(grouped=True)
+    assert min(g.info.plan_groups) == J
+    check_apply(wdb, g, case.th.mat, case.th.matT, n * n, 4)           # grouped items
     g.free()
 
 

@@ -1,8 +1,8 @@
 """Host logic of the tile planner (no GPU): plans of Theta_K and Theta_K^T built by libwdb for
 operators from the oracle, checked by wdb_tile_plan_check -- every output produced exactly
 once, staged regions and tap areas inside the staging buffer, every staged read inside its
-pair's region, and the conditions of split tiles, super tiles and 16-byte staging -- over
-the planner's parameter space."""
+pair's region, and the conditions of split tiles, super tiles, grouped items and 16-byte
+staging -- over the planner's parameter space."""
 import numpy as np
 import pytest
 
@@ -28,6 +28,10 @@ CONFIGS = [
     dict(esize=8),
     dict(esize=8, smem_budget=8192),
     dict(ctas=8, cap_share=1.0),
+    dict(grouped=True),
+    dict(grouped=True, smem_budget=49152, cap_share=4.0),
+    dict(grouped=True, smem_budget=8192, cap_share=1.0),
+    dict(grouped=True, esize=8),
 ]
 
 
@@ -58,6 +62,10 @@ def test_plans_keep_their_invariants(wdb, case, transpose):
             assert s["super_subbands"] == 0
         if not cfg.get("split_share"):
             assert s["split_tiles"] == 0
+        if cfg.get("grouped"):
+            assert s["groups"] == J and s["super_subbands"] == 0   # A_J with level J, then J - 1 levels
+        else:
+            assert s["groups"] == 0
     # the multiply-adds per application depend on the operator, not on the plan; they count
     # every kept entry once (up pairs are padded to their fullest phase)
     assert len(macs) == 1
