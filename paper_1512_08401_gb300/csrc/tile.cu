@@ -862,7 +862,9 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
         const int nmem = M == 1 ? 1 : P.nm;
         if (P.mode == kDown) {
             const T* __restrict__ Sb = S + (tm.ly + oy) * P.PC + tm.lx + ox + sh;
-            for (int mk = 0; mk < nmem; ++mk) {
+            #pragma unroll
+            for (int mk = 0; mk < M; ++mk) {
+                if (mk >= nmem) break;
                 const TapSrc<T> ts = stap + (M == 1 ? P.tap_begin : P.mtb[mk]);
                 const int ntap = M == 1 ? P.ntap : P.mnt[mk];
                 T (&ac)[4] = acc[mk];
@@ -903,7 +905,9 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                 const int ph = ((py & m) << lg) + (px & m);
                 const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
                 const int stepc = tm.lgsx - lg;   // log2 of the coarse column step
-                for (int mk = 0; mk < nmem; ++mk) {
+                #pragma unroll
+            for (int mk = 0; mk < M; ++mk) {
+                if (mk >= nmem) break;
                     const TapSrc<T> gts = gts0 + ((M == 1 ? P.tap_begin : P.mtb[mk]) + ph);
                     const int ntap = M == 1 ? P.ntap : P.mnt[mk];
                     if (stepc == 2) up_taps4<4, T>(gts, g, ntap, G, rr, Sb, acc[mk]);
@@ -917,7 +921,9 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                     const int ph = ((py & m) << lg) + (pxe & m);
                     const T* __restrict__ Sb = S + rowb + ((pxe >> lg) - (w.tx0 >> lg));
                     const int stp = G * rr;
-                    for (int mk = 0; mk < nmem; ++mk) {
+                    #pragma unroll
+            for (int mk = 0; mk < M; ++mk) {
+                if (mk >= nmem) break;
                         TapSrc<T> ts = gts0 + ((M == 1 ? P.tap_begin : P.mtb[mk]) + ph + g * rr);
                         const int ntap = M == 1 ? P.ntap : P.mnt[mk];
                         T a = 0;
@@ -935,7 +941,9 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                 const int ph = ((py & m) << lg) + (px & m);
                 const T* __restrict__ Sb = S + rowb + ((px >> lg) - (w.tx0 >> lg));
                 const int stp = G * rr;
-                for (int mk = 0; mk < nmem; ++mk) {
+                #pragma unroll
+            for (int mk = 0; mk < M; ++mk) {
+                if (mk >= nmem) break;
                     TapSrc<T> ts = gts0 + ((M == 1 ? P.tap_begin : P.mtb[mk]) + ph + g * rr);
                     const int ntap = M == 1 ? P.ntap : P.mnt[mk];
                     T a = 0;
@@ -964,7 +972,9 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                 const bool cols_ok = px0 + 3 * tm.sx < so.cols && bx0 + P.x0 >= 0 && bx0 + 3 * bstep + P.x0 + P.RC <= C;
                 if (rows_ok && cols_ok) {
                     const T* __restrict__ bp = src + (size_t)by * C + bx0;
-                    for (int mk = 0; mk < nmem; ++mk) {
+                    #pragma unroll
+            for (int mk = 0; mk < M; ++mk) {
+                if (mk >= nmem) break;
                         const int tb = M == 1 ? P.tap_begin : P.mtb[mk];
                         const int ntap = M == 1 ? P.ntap : P.mnt[mk];
                         const int* __restrict__ tl = plan.tap_lin + tb;
@@ -1007,7 +1017,9 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                 }
                 // interior: every tap of the pair lands inside the input subband, no wrap
                 const bool inside = by + P.y0 >= 0 && by + P.y0 + P.RR <= R && bx + P.x0 >= 0 && bx + P.x0 + P.RC <= C;
-                for (int mk = 0; mk < nmem; ++mk) {
+                #pragma unroll
+            for (int mk = 0; mk < M; ++mk) {
+                if (mk >= nmem) break;
                     const int tb = (M == 1 ? P.tap_begin : P.mtb[mk]) + pho;
                     const int ntap = M == 1 ? P.ntap : P.mnt[mk];
                     T a = 0;
