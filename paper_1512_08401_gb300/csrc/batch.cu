@@ -2,7 +2,10 @@
 // advanced together. Every iteration is two launches that cover the tiles of every running
 // problem (heaviest tiles first across all problems, persistent CTAs pulling from one
 // queue); a problem that meets its own stopping rule drops out of the queue. Chunks of
-// check_every iterations are captured in a CUDA graph and replayed until no problem runs.
+// check_every iterations are captured in a CUDA graph and replayed until no problem runs;
+// between chunks the host compacts the two work lists to the problems still running (the
+// kernels read the item counts from device memory, so the captured graph stays valid).
+// The tiles come from each operator's batch plans, whose tile sides are the autotuner's.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -144,6 +147,8 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
     BatchItem *d_fwd = nullptr, *d_adj = nullptr;
     TileQueue* d_q = nullptr;
     int* d_running = nullptr;
+    int* d_counts = nullptr;       // item counts of the two phases (compacted between chunks)
+    int* d_flags = nullptr;        // per problem: still running
     WDB_TRY(mem.alloc(&d_sums, 4 * (size_t)B));
     for (int b = 0; b < B; ++b) hp[b].sums = d_sums + 4 * b;
     const std::vector<BatchItem> fi = merge_items(th, 0), ai = merge_items(th, 1);
@@ -152,11 +157,15 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
     WDB_TRY(mem.alloc(&d_adj, ai.size()));
     WDB_TRY(mem.alloc(&d_q, 1));
     WDB_TRY(mem.alloc(&d_running, 1));
+    WDB_TRY(mem.alloc(&d_counts, 2));
+    WDB_TRY(mem.alloc(&d_flags, B));
     WDB_CK(cudaMemsetAsync(d_sums, 0, sizeof(double) * 4 * B, st));
     WDB_CK(cudaMemsetAsync(d_q, 0, sizeof(TileQueue), st));
     WDB_CK(cudaMemcpyAsync(d_probs, hp.data(), sizeof(BatchProblem) * B, cudaMemcpyHostToDevice, st));
     WDB_CK(cudaMemcpyAsync(d_fwd, fi.data(), sizeof(BatchItem) * fi.size(), cudaMemcpyHostToDevice, st));
     WDB_CK(cudaMemcpyAsync(d_adj, ai.data(), sizeof(BatchItem) * ai.size(), cudaMemcpyHostToDevice, st));
+    int h_counts[2] = {(int)fi.size(), (int)ai.size()};
+    WDB_CK(cudaMemcpyAsync(d_counts, h_counts, sizeof h_counts, cudaMemcpyHostToDevice, st));
     int* h_running = nullptr;
     WDB_CK(cudaMallocHost(&h_running, sizeof(int)));
     rejoin.pinned = h_running;
@@ -170,6 +179,9 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
     A.n_items = (int)ai.size();
     F.queue = A.queue = d_q;
     F.running = A.running = d_running;
+    F.run_flags = A.run_flags = d_flags;
+    F.n_items_dev = d_counts;
+    A.n_items_dev = d_counts + 1;
     F.buf_elems = A.buf_elems = buf_elems;
     F.smem_bytes = A.smem_bytes = 2 * buf_elems * (int)sizeof(float);
     F.grid = A.grid = std::max(1, tile_batch_grid(F.smem_bytes));
@@ -197,6 +209,11 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
     count_launch(-2LL * m);
     int max_it = 0;
     for (int b = 0; b < B; ++b) max_it = std::max(max_it, params[b].max_iters);
+    // between chunks the work lists are compacted to the problems still running, so that the
+    // launches of a long tail do not walk the tiles of finished problems
+    int prev_running = B;
+    std::vector<int> flags(B);
+    std::vector<BatchItem> cf, ca;
     for (int chunk = 0; s == WDB_OK; ++chunk) {
         ce = cudaGraphLaunch(ge, st);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
@@ -206,9 +223,40 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
         }
         count_launch(2LL * m);
         if (*h_running == 0 || (long long)(chunk + 1) * m >= max_it) break;
+        if (*h_running < prev_running) {
+            prev_running = *h_running;
+            ce = cudaMemcpy(flags.data(), d_flags, sizeof(int) * B, cudaMemcpyDeviceToHost);
+            if (ce != cudaSuccess) {
+                s = cuda_error(ce, "batch flags", __FILE__, __LINE__);
+                break;
+            }
+            cf.clear();
+            ca.clear();
+            for (const BatchItem& it : fi)
+                if (flags[it.p]) cf.push_back(it);
+            for (const BatchItem& it : ai)
+                if (flags[it.p]) ca.push_back(it);
+            const int hc[2] = {(int)cf.size(), (int)ca.size()};
+            ce = cudaMemcpyAsync(d_fwd, cf.data(), sizeof(BatchItem) * std::max<size_t>(cf.size(), 1),
+                                 cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(d_adj, ca.data(), sizeof(BatchItem) * std::max<size_t>(ca.size(), 1),
+                                     cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_counts, hc, sizeof hc, cudaMemcpyHostToDevice, st);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+            if (ce != cudaSuccess) {
+                s = cuda_error(ce, "batch compaction", __FILE__, __LINE__);
+                break;
+            }
+        }
     }
     if (ge) cudaGraphExecDestroy(ge);
-    // exact objective of every returned x
+    // exact objective of every returned x (the full work list again)
+    if (s == WDB_OK) {
+        ce = cudaMemcpyAsync(d_fwd, fi.data(), sizeof(BatchItem) * fi.size(), cudaMemcpyHostToDevice, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_counts, h_counts, sizeof h_counts, cudaMemcpyHostToDevice, st);
+        if (ce != cudaSuccess) s = cuda_error(ce, "batch list", __FILE__, __LINE__);
+    }
     if (s == WDB_OK) s = batch_objective(F, st);
     std::vector<double> sums(4 * B);
     std::vector<SolveState> states(B);

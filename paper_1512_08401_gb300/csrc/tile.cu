@@ -1345,13 +1345,14 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
     __shared__ double red_d[2 * kTileThreads / 32];
     __shared__ int s_next;
     const int t = threadIdx.x;
+    const int n_items = B.n_items_dev ? *B.n_items_dev : B.n_items;
     // next item whose problem is still running (thread 0), broadcast through shared memory
     auto fetch = [&]() {
         if (t == 0) {
             int i;
             for (;;) {
                 i = (int)atomicAdd(&B.queue->next, 1u);
-                if (i >= B.n_items) break;
+                if (i >= n_items) break;
                 if (EPI == kObj || !*(volatile int*)&B.probs[B.items[i].p].st->stop) break;
             }
             s_next = i;
@@ -1371,7 +1372,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
     __shared__ PairSm tab_buf[2][kMaxBatchPairs];
     PairSm* tab = tab_buf[0];
     PairSm* tab_next = tab_buf[1];
-    if (it < B.n_items) {
+    if (it < n_items) {
         const BatchItem bw = B.items[it];
         const TilePlanDev& pl = plan_of(bw.p);
         bi = pl.items[bw.item].batch_begin;
@@ -1380,7 +1381,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
     cp_async_commit();
     float acc[1][4] = {{0.f, 0.f, 0.f, 0.f}};
     Partials pt;
-    while (it < B.n_items) {
+    while (it < n_items) {
         const BatchItem bw = B.items[it];
         const BatchProblem& P = B.probs[bw.p];
         const TilePlanDev& pl = plan_of(bw.p);
@@ -1389,12 +1390,12 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         __syncthreads();
         if (nbi >= w.batch_end) {
             nit = fetch();
-            if (nit < B.n_items) {
+            if (nit < n_items) {
                 const BatchItem nb = B.items[nit];
                 nbi = plan_of(nb.p).items[nb.item].batch_begin;
             }
         }
-        if (nit < B.n_items) {
+        if (nit < n_items) {
             const BatchItem nb = B.items[nit];
             const TilePlanDev& npl = plan_of(nb.p);
             stage_batch<float>(npl, in_of(nb.p), npl.items[nb.item], nbi, Snext, tab_next);
@@ -1454,6 +1455,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
             }
             P.sums[0] = P.sums[1] = P.sums[2] = P.sums[3] = 0.0;
             running += st->stop ? 0 : 1;
+            if (B.run_flags) B.run_flags[p] = st->stop ? 0 : 1;
         }
         for (int off = 16; off > 0; off >>= 1) running += __shfl_down_sync(0xffffffffu, running, off);
         __shared__ int s_run[kTileThreads / 32];

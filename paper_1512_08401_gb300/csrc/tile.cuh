@@ -225,8 +225,11 @@ struct BatchArgs {
     int B;
     const BatchItem* items;        // all problems' tiles of this phase, heaviest first
     int n_items;
+    const int* n_items_dev;        // if set: the item count, read on the device (the host compacts
+                                   // the list to the running problems between graph chunks)
     TileQueue* queue;
     int* running;                  // written by the last CTA of the step kernel
+    int* run_flags;                // per problem: 1 while running (written with `running`)
     int grid;
     int buf_elems;                 // largest staging buffer of any problem's plan
     int smem_bytes;
