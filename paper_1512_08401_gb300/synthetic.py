@@ -23,6 +23,9 @@ PSFs:
     of 1/8 px, bilinearly splatted into an L x L grid, sum 1
   * the five families of the paper's Sec. 5 / Table 3 (paper_blur): Gaussian, skewed
     Gaussian, spline motion blur, Airy pattern, defocus disk
+  * varying_gaussian(n_rows, sigma0, sigma1, k): a spatially varying blur (Sec. 3.1, 3.5):
+    the input pixels of image row i spread with a Gaussian of sigma0 + (sigma1 - sigma0) i /
+    n_rows on a k x k support, sum 1 per row; blur_varying applies it by direct scatter
 """
 from __future__ import annotations
 
@@ -213,6 +216,24 @@ def blur_fft(u: np.ndarray, psf: np.ndarray) -> np.ndarray:
     return np.real(np.fft.ifft2(np.fft.fft2(u) * np.fft.fft2(pad)))
 
 
+def varying_gaussian(n_rows: int, sigma0: float, sigma1: float, k: int) -> np.ndarray:
+    """[n_rows, k, k]: the PSF with which the input pixels of each image row spread."""
+    sig = sigma0 + (sigma1 - sigma0) * np.arange(n_rows, dtype=np.float64) / n_rows
+    return np.stack([gaussian_psf(float(s), k) for s in sig])
+
+
+def blur_varying(u: np.ndarray, psfs: np.ndarray) -> np.ndarray:
+    """out[(i + a) mod R, (j + b) mod C] += psfs[i][a + kh//2, b + kw//2] u[i, j] (data
+    synthesis only)."""
+    n_rows, n_cols = u.shape
+    _, kh, kw = psfs.shape
+    out = np.zeros((n_rows, n_cols))
+    for a in range(kh):
+        for b in range(kw):
+            out += np.roll(psfs[:, a, b][:, None] * u, (a - kh // 2, b - kw // 2), axis=(0, 1))
+    return out
+
+
 @dataclass
 class Problem:
     u_clean: np.ndarray     # float64 (n_rows, n_cols)
@@ -256,6 +277,18 @@ def headline_problem(blur: str = "gaussian", instance: int = 0) -> Problem:
 def large_problem() -> Problem:
     """4096 x 4096, Gaussian sigma = 4 on 41 x 41 (db4, J = 6, K = 30 N)."""
     return make_problem(4096, gaussian_psf(4.0, 41), 1e-3, config_id=2, name="4096^2 gaussian s4")
+
+
+def varying_problem(n: int = 512, sigma0: float = 1.0, sigma1: float = 4.0, k: int = 25,
+                    lam: float = 1e-3, instance: int = 0, noise: float = 0.01) -> Problem:
+    """n x n, row-varying Gaussian (sigma from sigma0 at the top row to sigma1 at the bottom,
+    k x k support), noise 0.01, lambda = 1e-3 (db4, J = 5, K = 30 N). `psf` holds the
+    [n, k, k] stack of row PSFs."""
+    rng = rng_for(4, instance)
+    psfs = varying_gaussian(n, sigma0, sigma1, k)
+    u = clean_image(n, n, rng)
+    u0 = blur_varying(u, psfs) + noise * rng.standard_normal((n, n))
+    return Problem(u, u0, psfs, lam, f"{n}^2 varying gaussian s{sigma0:g}-{sigma1:g}")
 
 
 def batch_mix(count: int = 256, seed_config: int = 3):
