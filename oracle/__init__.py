@@ -19,6 +19,9 @@ solver    Preconditioned FISTA (Algorithm 3) on Theta_K, exact-operator FISTA
           (Algorithm 1 with the FFT-path gradient evaluated by direct convolution),
           objective, duality gap, KKT residuals, and a coordinate-descent Lasso solver
           used only to pin FISTA.
+varying   Row-varying blur (Sec. 3.1, 3.5): H by direct scatter, Theta from one probe per
+          subband row with horizontal circulant taps (Sec. 3.4), tap thresholding (Sec. 3.7)
+          and the preconditioner classes of that operator.
 rng       splitmix64 counter-based generator (Steele, Lea & Flood 2014) for the power
           iteration start vector.
 cnn       FP64 forward/backward of the warm-start U-Net (not a paper component).
