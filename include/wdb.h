@@ -61,6 +61,7 @@ typedef enum {
 
 typedef struct wdb_theta wdb_theta;   /* Theta_K and its preconditioners, library-owned */
 typedef struct wdb_fftop wdb_fftop;   /* exact operator H Psi for the FFT path, library-owned */
+typedef struct wdb_vtheta wdb_vtheta; /* Theta_K of a row-varying blur, library-owned */
 
 /* Summary of a Theta_K handle. */
 typedef struct {
@@ -282,6 +283,88 @@ wdb_status wdb_fftop_objective(wdb_fftop* op, const float* u_dev, const float* x
  * result->objective is the exact objective 1/2||H Psi x - u0||^2 + sum w|x|. */
 wdb_status wdb_solve_fft(wdb_fftop* op, const float* u_dev, float* x_dev,
                          const wdb_solve_params* params, void* stream, wdb_solve_result* result);
+
+/* ---- Spatially varying blur (Sec. 3.1, 3.4, 3.5) ----
+ * H spreads every input pixel of image row i with its own PSF psfs[i] (odd kh x kw, origin at
+ * (kh/2, kw/2)) on the torus: (H u)[(i+a) mod R][(j+b) mod C] += psfs[i][a+kh/2][b+kw/2] u[i][j].
+ * (One PSF for every row is the convolution of wdb_build_theta.) Such an H commutes with
+ * horizontal translations, so Theta = Psi* H Psi is circulant along the column axis inside
+ * every pair of subbands, and a tap is (a, py, b, qy, ox): output row py of subband a, input
+ * row qy of subband b, horizontal diagonal ox, with the entries
+ *   ((a, py, px), (b, qy, qx)) for px = ox + 2^{level(b)-level(a)} qx (mod C_a) when
+ *   level(a) <= level(b) (C_b entries), otherwise qx = ox + 2^{level(a)-level(b)} px
+ *   (mod C_b) (C_a entries).
+ * Construction (Sec. 3.4, one probe per subband row): H applied to the wavelet of (b, qy, 0)
+ * for every input row and H^T to the wavelet of (a, py, 0) for every output row of a subband
+ * above level 1, one FP64 forward DWT each, on the device. Thresholding (Sec. 3.7): whole taps
+ * by decreasing score |sigma_b v| (sigma_b = 2^{level(b)} or 1 as in wdb_build_theta), ties by
+ * (a, py, b, qy, ox) ascending, while the entry count stays <= K; |v| <= 1e-14 max|v| is never
+ * kept. Preconditioner classes: (b, qy, qx mod 2^{J - level(b)}), one table entry per class,
+ * subbands in planar order, then row-major in (qy, qx mod 2^{J - level(b)}) (info.n_classes).
+ * Limits: n_cols <= 2048 (WDB_EUNSUPPORTED above), n_rows, n_cols divisible by 2^levels,
+ * kh <= n_rows, kw <= n_cols. The build holds one FP64 candidate per coefficient window of
+ * every probe on the device (info.candidate_slots x 8 bytes) while it runs. */
+typedef struct {
+    int n_rows, n_cols, levels, n_subbands;
+    int rule;
+    long long K_requested;      /* K passed to wdb_vtheta_build */
+    long long K_eff;            /* nonzero entries of Theta_K (<= K_requested) */
+    long long n_taps;           /* kept taps */
+    long long n_candidates;     /* nonzero taps of the full Theta (0 for wdb_vtheta_from_taps) */
+    long long candidate_slots;  /* FP64 candidate values stored by the build */
+    int n_probes;               /* probes (column and row) of the build */
+    int n_classes;              /* length of the preconditioner tables */
+    int n_plan_rows;            /* output rows of one application (CTAs of a launch) */
+    long long plan_taps[2];     /* taps of the Theta_K and Theta_K^T row plans */
+    double theta_max_abs;       /* max |tap| of the full Theta */
+    double build_ms;            /* wall time of the build, device work included */
+} wdb_vtheta_info;
+
+/* psfs_host: n_rows x kh x kw FP64, row-major. K >= 0; rule WDB_RULE_*. WDB_EINVAL for bad
+ * sizes, an even PSF side, a non-finite PSF value, K < 0 or an unknown wavelet. Synchronises
+ * `stream`; on success *out owns device memory until wdb_vtheta_free. */
+wdb_status wdb_vtheta_build(const double* psfs_host, int kh, int kw, int n_rows, int n_cols,
+                            const char* wavelet, int levels, long long K, int rule, void* stream,
+                            wdb_vtheta** out);
+/* A handle from an explicit tap list (host arrays, n_taps each) in the convention above.
+ * Taps outside the subbands' sides, or a duplicate (a, py, b, qy, ox), are WDB_EINVAL. */
+wdb_status wdb_vtheta_from_taps(int n_rows, int n_cols, const char* wavelet, int levels, long long n_taps,
+                                const int* a_host, const int* py_host, const int* b_host, const int* qy_host,
+                                const int* ox_host, const double* v_host, void* stream, wdb_vtheta** out);
+wdb_status wdb_vtheta_info_get(const wdb_vtheta* op, wdb_vtheta_info* info);
+/* Kept taps to host arrays (capacity cap >= info.n_taps), sorted by (a, py, b, qy, ox). */
+wdb_status wdb_vtheta_export_taps(const wdb_vtheta* op, long long cap, int* a_host, int* py_host, int* b_host,
+                                  int* qy_host, int* ox_host, double* v_host);
+/* out = Theta_K in (transpose = 0) or Theta_K^T in (1); N floats each, device. */
+wdb_status wdb_vtheta_apply(const wdb_vtheta* op, const float* in_dev, float* out_dev, int transpose,
+                            void* stream);
+/* Preconditioner of kind `precond` (computed on first use, cached): P_host, Md_host, M2d_host
+ * receive info.n_classes values each (diag(M), diag(M^2) of M = Theta_K^T Theta_K per class,
+ * FP64 on the host from the taps); tau, L_hat as for wdb_theta_precond (FP64 power iteration on
+ * the device). Any output may be NULL. Synchronises `stream`. */
+wdb_status wdb_vtheta_precond(wdb_vtheta* op, int precond, double jacobi_eps, void* stream, double* P_host,
+                              double* Md_host, double* M2d_host, double* tau_host, double* L_hat_host);
+/* Override the table (info.n_classes values > 0) and step used for `precond`. */
+wdb_status wdb_vtheta_set_precond(wdb_vtheta* op, int precond, const double* P_host, double tau);
+/* Algorithm 3 on this Theta_K, as wdb_solve / wdb_solve_coeffs (params.kkt_check is ignored;
+ * the kkt_* and *64 result fields are NaN). */
+wdb_status wdb_vtheta_solve(wdb_vtheta* op, const float* u_dev, float* x_dev, const wdb_solve_params* params,
+                            void* stream, wdb_solve_result* result);
+wdb_status wdb_vtheta_solve_coeffs(wdb_vtheta* op, const float* x0_dev, float* x_dev,
+                                   const wdb_solve_params* params, void* stream, wdb_solve_result* result);
+/* E(x) = 1/2||Theta_K x - x0||^2 + sum w|x| in FP64 for device x, x0. */
+wdb_status wdb_vtheta_objective(wdb_vtheta* op, const float* x_dev, const float* x0_dev, double lambda,
+                                const double* w_subband_host, void* stream, double* E_host);
+void wdb_vtheta_free(wdb_vtheta* op);
+/* Host self-check of the row plans (no GPU): builds the plan of Theta_K (transpose = 0) or
+ * Theta_K^T (1) for a tap list in the convention above, runs one application on the host with
+ * the kernel's index arithmetic, checking every row, tap and access against the vector
+ * bounds, and writes y_host = Theta_K x_host (or the transpose) in FP64 (N values each).
+ * WDB_EPLAN: an invariant broke (wdb_last_error names it); WDB_EINVAL: bad sizes or taps. */
+wdb_status wdb_vtheta_plan_check(int n_rows, int n_cols, const char* wavelet, int levels, long long n_taps,
+                                 const int* a_host, const int* py_host, const int* b_host, const int* qy_host,
+                                 const int* ox_host, const double* v_host, int transpose, const double* x_host,
+                                 double* y_host);
 
 /* ---- Wavelet transforms (Sec. 2), FP32, device ---- */
 wdb_status wdb_dwt(const float* img_dev, float* coef_dev, int n_rows, int n_cols,

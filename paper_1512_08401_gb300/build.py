@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwdb.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["common.cpp", "dwt.cu", "subband_ops.cu", "tile.cu", "plan_check.cpp", "fftops.cu", "theta.cu", "solve.cu", "batch.cu", "kkt.cu", "noalloc.cu", "cnn.cu", "api.cpp"]
+SOURCES = ["common.cpp", "dwt.cu", "subband_ops.cu", "tile.cu", "plan_check.cpp", "fftops.cu", "theta.cu", "solve.cu", "batch.cu", "kkt.cu", "vtheta.cu", "noalloc.cu", "cnn.cu", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", *ARCH]
 

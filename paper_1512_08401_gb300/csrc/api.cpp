@@ -6,10 +6,12 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <tuple>
 
 #include "solve_impl.h"
 #include "plan_check.h"
 #include "theta_impl.h"
+#include "vtheta.h"
 #include "wdb_internal.h"
 
 namespace wdb {
@@ -469,6 +471,207 @@ wdb_status wdb_solve_fft(wdb_fftop* op, const float* u_dev, float* x_dev, const 
     std::memset(result, 0, sizeof *result);
     wdb_status s = fft_solve(op, u_dev, x_dev, params, static_cast<cudaStream_t>(stream), result);
     result->status = s;
+    return s;
+}
+
+// ---- row-varying operator ----
+wdb_status wdb_vtheta_build(const double* psfs_host, int kh, int kw, int n_rows, int n_cols, const char* wavelet,
+                            int levels, long long K, int rule, void* stream, wdb_vtheta** out) {
+    if (!out) return set_error(WDB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!psfs_host) return set_error(WDB_EINVAL, "psfs is NULL");
+    if (n_rows <= 0 || n_cols <= 0) return set_error(WDB_EINVAL, "bad image size %dx%d", n_rows, n_cols);
+    for (int i = 0; i < n_rows; ++i)
+        WDB_TRY(check_psf(psfs_host + (size_t)i * kh * kw, kh, kw, n_rows, n_cols));
+    if (K < 0) return set_error(WDB_EINVAL, "K must be >= 0");
+    if (rule != WDB_RULE_WEIGHTED && rule != WDB_RULE_NAIVE) return set_error(WDB_EINVAL, "unknown rule %d", rule);
+    wdb_vtheta* op = nullptr;
+    WDB_TRY(vtheta_new(n_rows, n_cols, wavelet, levels, &op));
+    wdb_status s = need_device();
+    const double t0 = now_ms();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    op->rule = rule;
+    op->K_requested = K;
+    if (s == WDB_OK) s = vtheta_build_device(op, psfs_host, kh, kw, K, rule, st);
+    if (s == WDB_OK) s = vtheta_finalize(op, st);
+    if (s != WDB_OK) {
+        vtheta_release(op);
+        return s;
+    }
+    op->build_ms = now_ms() - t0;
+    *out = op;
+    return WDB_OK;
+}
+
+wdb_status wdb_vtheta_from_taps(int n_rows, int n_cols, const char* wavelet, int levels, long long n_taps,
+                                const int* a, const int* py, const int* b, const int* qy, const int* ox,
+                                const double* v, void* stream, wdb_vtheta** out) {
+    if (!out) return set_error(WDB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_taps < 0) return set_error(WDB_EINVAL, "n_taps must be >= 0");
+    if (n_taps > 0 && (!a || !py || !b || !qy || !ox || !v)) return set_error(WDB_EINVAL, "tap array is NULL");
+    wdb_vtheta* op = nullptr;
+    WDB_TRY(vtheta_new(n_rows, n_cols, wavelet, levels, &op));
+    const Layout& L = op->lay;
+    op->taps.resize((size_t)n_taps);
+    for (long long i = 0; i < n_taps; ++i) {
+        if (a[i] < 0 || a[i] >= L.S || b[i] < 0 || b[i] >= L.S) {
+            vtheta_release(op);
+            return set_error(WDB_EINVAL, "tap %lld: subband out of range", i);
+        }
+        const SubbandDev &sa = L.sb[a[i]], &sb = L.sb[b[i]];
+        const int ocols = sa.level <= sb.level ? sa.cols : sb.cols;
+        if (py[i] < 0 || py[i] >= sa.rows || qy[i] < 0 || qy[i] >= sb.rows || ox[i] < 0 || ox[i] >= ocols ||
+            !std::isfinite(v[i])) {
+            vtheta_release(op);
+            return set_error(WDB_EINVAL, "tap %lld outside its subbands or not finite", i);
+        }
+        op->taps[i] = {a[i], py[i], b[i], qy[i], ox[i], v[i]};
+    }
+    auto key = [](const VTapH& t) { return std::tie(t.a, t.py, t.b, t.qy, t.ox); };
+    std::sort(op->taps.begin(), op->taps.end(), [&](const VTapH& x, const VTapH& y) { return key(x) < key(y); });
+    for (size_t i = 1; i < op->taps.size(); ++i)
+        if (key(op->taps[i]) == key(op->taps[i - 1])) {
+            vtheta_release(op);
+            return set_error(WDB_EINVAL, "duplicate tap");
+        }
+    double vmax = 0.0;
+    for (const VTapH& t : op->taps) vmax = std::max(vmax, std::fabs(t.v));
+    op->theta_max_abs = vmax;
+    op->K_requested = -1;
+    wdb_status s = need_device();
+    const double t0 = now_ms();
+    if (s == WDB_OK) s = vtheta_finalize(op, static_cast<cudaStream_t>(stream));
+    if (s != WDB_OK) {
+        vtheta_release(op);
+        return s;
+    }
+    op->K_requested = op->K_eff;
+    op->build_ms = now_ms() - t0;
+    *out = op;
+    return WDB_OK;
+}
+
+wdb_status wdb_vtheta_info_get(const wdb_vtheta* op, wdb_vtheta_info* info) {
+    if (!op || !info) return set_error(WDB_EINVAL, "NULL argument");
+    std::memset(info, 0, sizeof *info);
+    info->n_rows = op->lay.n_rows;
+    info->n_cols = op->lay.n_cols;
+    info->levels = op->lay.J;
+    info->n_subbands = op->lay.S;
+    info->rule = op->rule;
+    info->K_requested = op->K_requested;
+    info->K_eff = op->K_eff;
+    info->n_taps = (long long)op->taps.size();
+    info->n_candidates = op->n_candidates;
+    info->candidate_slots = op->n_cand_slots;
+    info->n_probes = op->n_probes;
+    info->n_classes = op->n_classes;
+    info->n_plan_rows = op->plan[0].n_rows;
+    info->plan_taps[0] = (long long)op->hplan[0].taps.size();
+    info->plan_taps[1] = (long long)op->hplan[1].taps.size();
+    info->theta_max_abs = op->theta_max_abs;
+    info->build_ms = op->build_ms;
+    return WDB_OK;
+}
+
+wdb_status wdb_vtheta_export_taps(const wdb_vtheta* op, long long cap, int* a, int* py, int* b, int* qy, int* ox,
+                                  double* v) {
+    if (!op || !a || !py || !b || !qy || !ox || !v) return set_error(WDB_EINVAL, "NULL argument");
+    if (cap < (long long)op->taps.size()) return set_error(WDB_EINVAL, "capacity %lld < %zu taps", cap, op->taps.size());
+    for (size_t i = 0; i < op->taps.size(); ++i) {
+        const VTapH& t = op->taps[i];
+        a[i] = t.a;
+        py[i] = t.py;
+        b[i] = t.b;
+        qy[i] = t.qy;
+        ox[i] = t.ox;
+        v[i] = t.v;
+    }
+    return WDB_OK;
+}
+
+wdb_status wdb_vtheta_apply(const wdb_vtheta* op, const float* in_dev, float* out_dev, int transpose, void* stream) {
+    if (!op || !in_dev || !out_dev) return set_error(WDB_EINVAL, "NULL argument");
+    return vtheta_apply(op, in_dev, out_dev, transpose != 0, static_cast<cudaStream_t>(stream));
+}
+
+wdb_status wdb_vtheta_precond(wdb_vtheta* op, int precond, double jacobi_eps, void* stream, double* P_host,
+                              double* Md_host, double* M2d_host, double* tau_host, double* L_hat_host) {
+    if (!op) return set_error(WDB_EINVAL, "NULL handle");
+    WDB_TRY(need_device());
+    WDB_TRY(vtheta_precond(op, precond, jacobi_eps, static_cast<cudaStream_t>(stream)));
+    const PrecondCache& pc = op->pc[precond];
+    if (P_host) std::copy(pc.P.begin(), pc.P.end(), P_host);
+    if (Md_host) std::copy(op->Md.begin(), op->Md.end(), Md_host);
+    if (M2d_host) std::copy(op->M2d.begin(), op->M2d.end(), M2d_host);
+    if (tau_host) *tau_host = pc.tau;
+    if (L_hat_host) *L_hat_host = pc.L_hat;
+    return WDB_OK;
+}
+
+wdb_status wdb_vtheta_set_precond(wdb_vtheta* op, int precond, const double* P_host, double tau) {
+    if (!op || !P_host) return set_error(WDB_EINVAL, "NULL argument");
+    if (precond < 0 || precond > 2) return set_error(WDB_EINVAL, "unknown preconditioner %d", precond);
+    if (!(tau > 0.0) || !std::isfinite(tau)) return set_error(WDB_EINVAL, "tau must be finite and > 0");
+    for (int i = 0; i < op->n_classes; ++i)
+        if (!(P_host[i] > 0.0) || !std::isfinite(P_host[i])) return set_error(WDB_EINVAL, "P[%d] must be > 0", i);
+    return vtheta_set_precond(op, precond, P_host, tau);
+}
+
+wdb_status wdb_vtheta_solve(wdb_vtheta* op, const float* u_dev, float* x_dev, const wdb_solve_params* params,
+                            void* stream, wdb_solve_result* result) {
+    if (!op || !u_dev || !x_dev || !params || !result) return set_error(WDB_EINVAL, "NULL argument");
+    std::memset(result, 0, sizeof *result);
+    wdb_status s = vtheta_solve(op, u_dev, true, x_dev, params, static_cast<cudaStream_t>(stream), result);
+    result->status = s;
+    return s;
+}
+
+wdb_status wdb_vtheta_solve_coeffs(wdb_vtheta* op, const float* x0_dev, float* x_dev, const wdb_solve_params* params,
+                                   void* stream, wdb_solve_result* result) {
+    if (!op || !x0_dev || !x_dev || !params || !result) return set_error(WDB_EINVAL, "NULL argument");
+    std::memset(result, 0, sizeof *result);
+    wdb_status s = vtheta_solve(op, x0_dev, false, x_dev, params, static_cast<cudaStream_t>(stream), result);
+    result->status = s;
+    return s;
+}
+
+wdb_status wdb_vtheta_objective(wdb_vtheta* op, const float* x_dev, const float* x0_dev, double lambda,
+                                const double* w_subband_host, void* stream, double* E_host) {
+    if (!op || !x_dev || !x0_dev || !E_host) return set_error(WDB_EINVAL, "NULL argument");
+    if (!w_subband_host && !(lambda >= 0.0 && std::isfinite(lambda)))
+        return set_error(WDB_EINVAL, "lambda must be finite and >= 0");
+    std::vector<double> w(op->lay.S);
+    for (int b = 0; b < op->lay.S; ++b) w[b] = w_subband_host ? w_subband_host[b] : lambda;
+    return vtheta_objective_public(op, x_dev, x0_dev, w.data(), static_cast<cudaStream_t>(stream), E_host);
+}
+
+void wdb_vtheta_free(wdb_vtheta* op) { vtheta_release(op); }
+
+wdb_status wdb_vtheta_plan_check(int n_rows, int n_cols, const char* wavelet, int levels, long long n_taps,
+                                 const int* a, const int* py, const int* b, const int* qy, const int* ox,
+                                 const double* v, int transpose, const double* x_host, double* y_host) {
+    if (!x_host || !y_host) return set_error(WDB_EINVAL, "NULL argument");
+    if (n_taps < 0 || (n_taps > 0 && (!a || !py || !b || !qy || !ox || !v)))
+        return set_error(WDB_EINVAL, "bad tap arrays");
+    wdb_vtheta* op = nullptr;
+    WDB_TRY(vtheta_new(n_rows, n_cols, wavelet, levels, &op));
+    const Layout& L = op->lay;
+    wdb_status s = WDB_OK;
+    for (long long i = 0; i < n_taps && s == WDB_OK; ++i) {
+        if (a[i] < 0 || a[i] >= L.S || b[i] < 0 || b[i] >= L.S) {
+            s = set_error(WDB_EINVAL, "tap %lld: subband out of range", i);
+            break;
+        }
+        const SubbandDev &sa = L.sb[a[i]], &sb = L.sb[b[i]];
+        const int ocols = sa.level <= sb.level ? sa.cols : sb.cols;
+        if (py[i] < 0 || py[i] >= sa.rows || qy[i] < 0 || qy[i] >= sb.rows || ox[i] < 0 || ox[i] >= ocols)
+            s = set_error(WDB_EINVAL, "tap %lld outside its subbands", i);
+        else op->taps.push_back({a[i], py[i], b[i], qy[i], ox[i], v[i]});
+    }
+    if (s == WDB_OK) s = vtheta_plan_emulate(op, transpose != 0, x_host, y_host);
+    vtheta_release(op);
     return s;
 }
 

@@ -1,6 +1,8 @@
 // Device helpers shared by the kernels of libwdb: compensated FP32 accumulation, the
 // deterministic grid-wide FP64 reduction, and subband / phase-class lookups.
 #pragma once
+#include <cfloat>
+
 #include "wdb_internal.h"
 
 namespace wdb {
@@ -75,6 +77,12 @@ __device__ bool grid_reduce(double (&v)[NV], unsigned maxmask, double* part, uns
     }
     if (threadIdx.x == 0) *counter = 0u;
     return true;
+}
+
+// |g| / w, the ratio of the dual bound (infinite for g != 0 where w = 0)
+__device__ __forceinline__ float gw_ratio(float g, float w) {
+    const float ag = fabsf(g);
+    return w > 0.f ? ag / w : (ag > 0.f ? FLT_MAX : 0.f);
 }
 
 __device__ __forceinline__ int find_subband(const int* __restrict__ vb_start, int S, int vb) {

@@ -173,6 +173,17 @@ static wdb_status record_ev(cudaEvent_t ev, cudaStream_t st) {
     return WDB_OK;
 }
 
+// The loop pieces above, for the other operator types (vtheta.cu).
+SolveState solve_init_state(const wdb_solve_params* p, int m) { return init_state(p, m); }
+wdb_status solve_check_params(const wdb_solve_params* p, int S) { return check_params(p, S); }
+std::vector<float> solve_weights(const wdb_solve_params* p, int S) { return weights(p, S); }
+double solve_now_ms() { return now_ms(); }
+wdb_status solve_run_loop(IterEngine& E, int m, bool use_graph, bool timed, long long kernels_per_chunk,
+                          cudaStream_t st) {
+    return run_loop(E, m, use_graph, timed, kernels_per_chunk, st);
+}
+wdb_status solve_record_ev(cudaEvent_t ev, cudaStream_t st) { return record_ev(ev, st); }
+
 wdb_status work_enter(cudaStream_t* work, cudaEvent_t* ev_in, cudaEvent_t* ev_out, cudaStream_t caller) {
     if (!*work) WDB_CK(cudaStreamCreateWithFlags(work, cudaStreamNonBlocking));
     if (!*ev_in) WDB_CK(cudaEventCreateWithFlags(ev_in, cudaEventDisableTiming));

@@ -57,4 +57,13 @@ wdb_status fft_objective_public(wdb_fftop* op, const float* u, const float* x, c
 wdb_status fft_solve(wdb_fftop* op, const float* u, float* x_out, const wdb_solve_params* p, cudaStream_t st,
                      wdb_solve_result* res);
 
+// Solve-loop pieces shared with the row-varying operator (defined in solve.cu).
+SolveState solve_init_state(const wdb_solve_params* p, int m);
+wdb_status solve_check_params(const wdb_solve_params* p, int S);
+std::vector<float> solve_weights(const wdb_solve_params* p, int S);
+double solve_now_ms();
+wdb_status solve_run_loop(IterEngine& E, int m, bool use_graph, bool timed, long long kernels_per_chunk,
+                          cudaStream_t st);
+wdb_status solve_record_ev(cudaEvent_t ev, cudaStream_t st);
+
 }  // namespace wdb

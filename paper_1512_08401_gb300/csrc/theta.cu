@@ -24,6 +24,7 @@
 #include "device_util.cuh"
 #include "fftops.cuh"
 #include "subband_ops.cuh"
+#include "select.cuh"
 #include "theta_impl.h"
 
 namespace wdb {
@@ -36,17 +37,6 @@ struct CandPair {
     long long base;        // global candidate index of element 0
     unsigned long long mult;
     double sigma;
-};
-
-struct SelState {
-    unsigned long long vmax_bits;
-    unsigned long long K;
-    unsigned long long before;     // weight of keys strictly below the current prefix range
-    unsigned long long prefix_hi, prefix_lo;
-    unsigned long long count;
-    int keep_all;
-    int pad;
-    unsigned long long hist[256];
 };
 
 __device__ __forceinline__ bool cand_key(const CandPair& P, int e, double thr, unsigned long long& hi,
@@ -101,34 +91,6 @@ __global__ void sel_hist_kernel(const CandPair* __restrict__ pairs, SelState* se
     __syncthreads();
     for (int i = threadIdx.x; i < 256; i += blockDim.x)
         if (h[i]) atomicAdd(&sel->hist[i], h[i]);
-}
-
-__global__ void sel_scan_kernel(SelState* sel, int pass) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    if (!sel->keep_all) {
-        unsigned long long excl = 0;
-        int dsel = -1;
-        for (int d = 0; d < 256; ++d) {
-            const unsigned long long hd = sel->hist[d];
-            if (sel->before + excl + hd > sel->K) {
-                dsel = d;
-                break;
-            }
-            excl += hd;
-        }
-        if (dsel < 0) {
-            sel->keep_all = 1;
-        } else {
-            sel->before += excl;
-            if (pass < 8) sel->prefix_hi = (sel->prefix_hi << 8) | (unsigned long long)dsel;
-            else sel->prefix_lo = (sel->prefix_lo << 8) | (unsigned long long)dsel;
-        }
-    }
-    for (int d = 0; d < 256; ++d) sel->hist[d] = 0ull;
-}
-
-__device__ __forceinline__ bool kept(const SelState& s, unsigned long long hi, unsigned long long lo) {
-    return s.keep_all || hi < s.prefix_hi || (hi == s.prefix_hi && lo < s.prefix_lo);
 }
 
 __global__ void sel_emit_kernel(const CandPair* __restrict__ pairs, SelState* sel, int* out_pair, int* out_e,

@@ -636,11 +636,6 @@ __device__ __forceinline__ int pos_mod(int v, int n) {
     return v;
 }
 
-__device__ __forceinline__ float gw_ratio(float g, float w) {
-    const float ag = fabsf(g);
-    return w > 0.f ? ag / w : (ag > 0.f ? FLT_MAX : 0.f);
-}
-
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 template <int B>
 __device__ __forceinline__ void cp_async_to(unsigned s, const void* gmem) {

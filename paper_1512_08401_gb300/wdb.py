@@ -44,6 +44,14 @@ class ThetaInfo(C.Structure):
                 ("plan_super_subbands", C.c_int * 2), ("plan_groups", C.c_int * 2)]
 
 
+class VThetaInfo(C.Structure):
+    _fields_ = [("n_rows", C.c_int), ("n_cols", C.c_int), ("levels", C.c_int), ("n_subbands", C.c_int),
+                ("rule", C.c_int), ("K_requested", C.c_longlong), ("K_eff", C.c_longlong), ("n_taps", C.c_longlong),
+                ("n_candidates", C.c_longlong), ("candidate_slots", C.c_longlong), ("n_probes", C.c_int),
+                ("n_classes", C.c_int), ("n_plan_rows", C.c_int), ("plan_taps", C.c_longlong * 2),
+                ("theta_max_abs", C.c_double), ("build_ms", C.c_double)]
+
+
 class SolveParams(C.Structure):
     _fields_ = [("lam", C.c_double), ("w_subband_host", C.POINTER(C.c_double)), ("max_iters", C.c_int),
                 ("tol", C.c_double), ("precond", C.c_int), ("jacobi_eps", C.c_double),
@@ -102,6 +110,18 @@ _SIGS = {
     "wdb_fftop_precond": (i32, [vp, i32, f64, vp, pd, pd, pd]),
     "wdb_fftop_set_precond": (i32, [vp, i32, pd, f64]),
     "wdb_solve_fft": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
+    "wdb_vtheta_build": (i32, [pd, i32, i32, i32, i32, C.c_char_p, i32, i64, i32, vp, C.POINTER(vp)]),
+    "wdb_vtheta_from_taps": (i32, [i32, i32, C.c_char_p, i32, i64, pi, pi, pi, pi, pi, pd, vp, C.POINTER(vp)]),
+    "wdb_vtheta_info_get": (i32, [vp, C.POINTER(VThetaInfo)]),
+    "wdb_vtheta_export_taps": (i32, [vp, i64, pi, pi, pi, pi, pi, pd]),
+    "wdb_vtheta_apply": (i32, [vp, vp, vp, i32, vp]),
+    "wdb_vtheta_precond": (i32, [vp, i32, f64, vp, pd, pd, pd, pd, pd]),
+    "wdb_vtheta_set_precond": (i32, [vp, i32, pd, f64]),
+    "wdb_vtheta_solve": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
+    "wdb_vtheta_solve_coeffs": (i32, [vp, vp, vp, C.POINTER(SolveParams), vp, C.POINTER(SolveResult)]),
+    "wdb_vtheta_objective": (i32, [vp, vp, vp, f64, pd, vp, pd]),
+    "wdb_vtheta_free": (None, [vp]),
+    "wdb_vtheta_plan_check": (i32, [i32, i32, C.c_char_p, i32, i64, pi, pi, pi, pi, pi, pd, i32, pd, pd]),
     "wdb_dwt": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
     "wdb_idwt": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
     "wdb_dwt_noalloc": (i32, [vp, vp, i32, i32, C.c_char_p, i32, vp]),
@@ -336,6 +356,104 @@ class Theta:
             pass
 
 
+class VTheta:
+    """Theta_K of a row-varying blur (wdb_vtheta_*): psfs[i] is the PSF of image row i."""
+
+    def __init__(self, handle):
+        self._h = C.c_void_p(handle)
+        self.info = self._info()
+
+    @classmethod
+    def build(cls, psfs, n_rows, n_cols, wavelet="db4", levels=4, K=None, rule="weighted", stream=None):
+        psfs, pp = _f64(psfs)
+        if psfs.ndim != 3 or psfs.shape[0] != n_rows:
+            raise ValueError("psfs must be [n_rows, kh, kw]")
+        _, kh, kw = psfs.shape
+        K = n_rows * n_cols * 30 if K is None else int(K)
+        out = C.c_void_p()
+        _check(lib().wdb_vtheta_build(pp, kh, kw, n_rows, n_cols, wavelet.encode(), levels, K,
+                                      RULE[rule] if isinstance(rule, str) else int(rule), _stream(stream),
+                                      C.byref(out)))
+        return cls(out.value)
+
+    @classmethod
+    def from_taps(cls, n_rows, n_cols, wavelet, levels, a, py, b, qy, ox, v, stream=None):
+        arrs = [_i32(z) for z in (a, py, b, qy, ox)]
+        v, pv = _f64(v)
+        out = C.c_void_p()
+        _check(lib().wdb_vtheta_from_taps(n_rows, n_cols, wavelet.encode(), levels, len(v), *[p for _, p in arrs],
+                                          pv, _stream(stream), C.byref(out)))
+        return cls(out.value)
+
+    def _info(self) -> VThetaInfo:
+        i = VThetaInfo()
+        _check(lib().wdb_vtheta_info_get(self._h, C.byref(i)))
+        return i
+
+    @property
+    def N(self) -> int:
+        return self.info.n_rows * self.info.n_cols
+
+    def export_taps(self):
+        n = self.info.n_taps
+        a, py, b, qy, ox = (np.zeros(n, np.int32) for _ in range(5))
+        v = np.zeros(n)
+        _check(lib().wdb_vtheta_export_taps(self._h, n, *[z.ctypes.data_as(pi) for z in (a, py, b, qy, ox)],
+                                            v.ctypes.data_as(pd)))
+        return a, py, b, qy, ox, v
+
+    def precond(self, kind="spai", jacobi_eps=0.0, stream=None):
+        n = self.info.n_classes
+        P, Md, M2d = np.zeros(n), np.zeros(n), np.zeros(n)
+        tau, L = C.c_double(), C.c_double()
+        _check(lib().wdb_vtheta_precond(self._h, PRECOND[kind], jacobi_eps, _stream(stream), P.ctypes.data_as(pd),
+                                        Md.ctypes.data_as(pd), M2d.ctypes.data_as(pd), C.byref(tau), C.byref(L)))
+        return {"P": P, "Md": Md, "M2d": M2d, "tau": tau.value, "L_hat": L.value}
+
+    def set_precond(self, kind, P, tau):
+        P, pp = _f64(P)
+        _check(lib().wdb_vtheta_set_precond(self._h, PRECOND[kind], pp, float(tau)))
+
+    def apply(self, x, out, transpose=False, stream=None):
+        _check(lib().wdb_vtheta_apply(self._h, _dev(x, self.N), _dev(out, self.N), 1 if transpose else 0,
+                                      _stream(stream)))
+        return out
+
+    def solve(self, u, x, stream=None, **kw):
+        p, _keep = make_params(**kw)
+        r = SolveResult()
+        _check(lib().wdb_vtheta_solve(self._h, _dev(u, self.N), _dev(x, self.N), C.byref(p), _stream(stream),
+                                      C.byref(r)))
+        return r.as_dict()
+
+    def solve_coeffs(self, x0, x, stream=None, **kw):
+        p, _keep = make_params(**kw)
+        r = SolveResult()
+        _check(lib().wdb_vtheta_solve_coeffs(self._h, _dev(x0, self.N), _dev(x, self.N), C.byref(p),
+                                             _stream(stream), C.byref(r)))
+        return r.as_dict()
+
+    def objective(self, x, x0, lam=1e-3, w_subband=None, stream=None):
+        E = C.c_double()
+        pw = None
+        if w_subband is not None:
+            w, pw = _f64(w_subband)
+        _check(lib().wdb_vtheta_objective(self._h, _dev(x, self.N), _dev(x0, self.N), float(lam), pw,
+                                          _stream(stream), C.byref(E)))
+        return E.value
+
+    def free(self):
+        if self._h:
+            lib().wdb_vtheta_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
 class FFTOp:
     """Exact operator H Psi for the FFT path."""
 
@@ -403,6 +521,17 @@ def tile_plan_check(n_rows, n_cols, levels, a, b, oy, ox, v, transpose=False, es
                                       esize, smem_budget, cap_share, split_share,
                                       2 if grouped else (1 if super_tiles else 0), ctas, C.byref(sm)))
     return {f: getattr(sm, f) for f, _ in PlanSummary._fields_}
+
+
+def vtheta_plan_check(n_rows, n_cols, wavelet, levels, a, py, b, qy, ox, v, x, transpose=False):
+    """Host emulation of one row-plan application (wdb_vtheta_plan_check): returns y (FP64)."""
+    arrs = [_i32(z) for z in (a, py, b, qy, ox)]
+    v, pv = _f64(v)
+    x, px = _f64(x)
+    y = np.zeros(n_rows * n_cols)
+    _check(lib().wdb_vtheta_plan_check(n_rows, n_cols, wavelet.encode(), levels, len(v), *[p for _, p in arrs], pv,
+                                       1 if transpose else 0, px, y.ctypes.data_as(pd)))
+    return y
 
 
 def dwt(img, coef, n_rows, n_cols, wavelet="db4", levels=4, stream=None):
