@@ -160,44 +160,63 @@ class VTaps:
         return VTaps(*(z[mask] for z in (self.a, self.py, self.b, self.qy, self.ox, self.v, self.m)))
 
 
-def all_taps(psfs: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels: int, pool=None) -> VTaps:
-    """Every tap of Theta: column probes give the pairs with s_a <= s_b, row probes the
-    pairs with s_a > s_b. `pool` (an executor) only spreads the independent probes."""
+def _probe_taps(kind: int, psfs, n_rows, n_cols, wavelet, levels, sub, row):
+    """The taps one probe gives, exact zeros dropped (they can never be kept):
+    kind 0: column probe of input row (sub, row) -> pairs (a, b = sub) with s_a <= s_b;
+    kind 1: row probe of output row (sub, row)   -> pairs (a = sub, b) with s_b < s_a."""
     lay = layout(n_rows, n_cols, levels)
-    cjobs = [(b.index, qy) for b in lay for qy in range(b.rows)]
-    rjobs = [(a.index, py) for a in lay if a.level > 1 for py in range(a.rows)]
+    fixed = lay[sub]
+    vec = (column_probe if kind == 0 else row_probe)(psfs, n_rows, n_cols, wavelet, levels, sub, row)
+    out = []
+    for o in lay:
+        if (kind == 0 and o.level > fixed.level) or (kind == 1 and o.level >= fixed.level):
+            continue
+        blk = vec[o.offset:o.offset + o.size].reshape(o.rows, o.cols)
+        r, c = np.nonzero(blk)
+        if len(r) == 0:
+            continue
+        n = len(r)
+        if kind == 0:       # output a = o, rows r; input (sub, row)
+            a, py, b, qy, m = np.full(n, o.index), r, np.full(n, sub), np.full(n, row), fixed.cols
+        else:               # output (sub, row); input b = o, rows r
+            a, py, b, qy, m = np.full(n, sub), np.full(n, row), np.full(n, o.index), r, fixed.cols
+        out.append((a, py, b, qy, c, blk[r, c], np.full(n, m, dtype=np.int64)))
+    if not out:
+        return tuple(np.zeros(0, dtype=np.int64) for _ in range(5)) + (np.zeros(0), np.zeros(0, dtype=np.int64))
+    return tuple(np.concatenate(z) for z in zip(*out))
+
+
+_WORKER_OP = None
+
+
+def _worker_init(psfs, n_rows, n_cols, wavelet, levels):
+    global _WORKER_OP
+    _WORKER_OP = (psfs, n_rows, n_cols, wavelet, levels)
+
+
+def _worker_probe(job):
+    kind, sub, row = job
+    return _probe_taps(kind, *_WORKER_OP, sub, row)
+
+
+def all_taps(psfs: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels: int, workers: int = 1) -> VTaps:
+    """Every nonzero tap of Theta: column probes give the pairs with s_a <= s_b, row probes
+    the pairs with s_a > s_b (multiplicity: the columns of the coarser subband). workers > 1
+    only spreads the independent probes over that many spawned processes."""
+    lay = layout(n_rows, n_cols, levels)
+    jobs = [(0, b.index, q) for b in lay for q in range(b.rows)]
+    jobs += [(1, a.index, q) for a in lay if a.level > 1 for q in range(a.rows)]
     common = (psfs, n_rows, n_cols, wavelet, levels)
-    if pool is None:
-        cres = [column_probe(*common, *j) for j in cjobs]
-        rres = [row_probe(*common, *j) for j in rjobs]
+    if workers <= 1:
+        res = [_probe_taps(k, *common, s, q) for k, s, q in jobs]
     else:
-        rep = [[c] * len(cjobs) for c in common]
-        cres = list(pool.map(column_probe, *rep, *zip(*cjobs))) if cjobs else []
-        rep = [[c] * len(rjobs) for c in common]
-        rres = list(pool.map(row_probe, *rep, *zip(*rjobs))) if rjobs else []
-    parts = []
-    for (bi, qy), col in zip(cjobs, cres):
-        b = lay[bi]
-        for a in lay:
-            if a.level <= b.level:
-                v = col[a.offset:a.offset + a.size].reshape(a.rows, a.cols)
-                py, ox = np.meshgrid(np.arange(a.rows), np.arange(a.cols), indexing="ij")
-                parts.append((a.index, py.ravel(), bi, np.full(v.size, qy), ox.ravel(), v.ravel(), b.cols))
-    for (ai, py), row in zip(rjobs, rres):
-        a = lay[ai]
-        for b in lay:
-            if a.level > b.level:
-                v = row[b.offset:b.offset + b.size].reshape(b.rows, b.cols)
-                qy, ox = np.meshgrid(np.arange(b.rows), np.arange(b.cols), indexing="ij")
-                parts.append((ai, np.full(v.size, py), b.index, qy.ravel(), ox.ravel(), v.ravel(), a.cols))
-    A = np.concatenate([np.full(len(p[5]), p[0]) for p in parts])
-    PY = np.concatenate([np.broadcast_to(p[1], len(p[5])) for p in parts])
-    B = np.concatenate([np.full(len(p[5]), p[2]) for p in parts])
-    QY = np.concatenate([np.broadcast_to(p[3], len(p[5])) for p in parts])
-    OX = np.concatenate([p[4] for p in parts])
-    V = np.concatenate([p[5] for p in parts])
-    M = np.concatenate([np.full(len(p[5]), p[6], dtype=np.int64) for p in parts])
-    return VTaps(A, PY, B, QY, OX, V, M)
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"),
+                                 initializer=_worker_init, initargs=common) as pool:
+            res = list(pool.map(_worker_probe, jobs, chunksize=16))
+    cols = [np.concatenate([r[i] for r in res]) for i in range(7)]
+    return VTaps(*cols)
 
 
 # ---------------------------------------------------------------------------------------
@@ -231,21 +250,26 @@ def select_taps(t: VTaps, lay: list, K: int, rule: str = "weighted") -> np.ndarr
 def tap_entries(t: VTaps, lay: list):
     """(rows, cols, vals) of every entry carried by the taps (the two forms above)."""
     rows, cols, vals = [], [], []
-    for i in range(len(t)):
-        a, b = lay[t.a[i]], lay[t.b[i]]
+    if len(t) == 0:
+        return np.zeros(0, int), np.zeros(0, int), np.zeros(0)
+    pairs = np.unique(np.stack([t.a, t.b], axis=1), axis=0)
+    for ai, bi in pairs:
+        a, b = lay[ai], lay[bi]
+        sel = (t.a == ai) & (t.b == bi)
+        py, qy, ox, v = t.py[sel], t.qy[sel], t.ox[sel], t.v[sel]
         if a.level <= b.level:
             r = 1 << (b.level - a.level)
-            qx = np.arange(b.cols)
-            px = (t.ox[i] + r * qx) % a.cols
+            qx = np.arange(b.cols)[None, :]
+            px = (ox[:, None] + r * qx) % a.cols
+            qx = np.broadcast_to(qx, px.shape)
         else:
             r = 1 << (a.level - b.level)
-            px = np.arange(a.cols)
-            qx = (t.ox[i] + r * px) % b.cols
-        rows.append(a.offset + t.py[i] * a.cols + px)
-        cols.append(b.offset + t.qy[i] * b.cols + qx)
-        vals.append(np.full(len(px), t.v[i]))
-    if not rows:
-        return np.zeros(0, int), np.zeros(0, int), np.zeros(0)
+            px = np.arange(a.cols)[None, :]
+            qx = (ox[:, None] + r * px) % b.cols
+            px = np.broadcast_to(px, qx.shape)
+        rows.append((a.offset + py[:, None] * a.cols + px).ravel())
+        cols.append((b.offset + qy[:, None] * b.cols + qx).ravel())
+        vals.append(np.broadcast_to(v[:, None], px.shape).ravel())
     return np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
 
 
@@ -270,11 +294,11 @@ class VThetaK:
 
 
 def build_varying_theta(psfs: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels: int,
-                        K: int, rule: str = "weighted", pool=None) -> VThetaK:
+                        K: int, rule: str = "weighted", workers: int = 1) -> VThetaK:
     """Probes (one per row of every subband) + Sec. 3.7 thresholding -> Theta_K."""
     if K < 0:
         raise ValueError("K must be >= 0")
-    t = all_taps(psfs, n_rows, n_cols, wavelet, levels, pool=pool)
+    t = all_taps(psfs, n_rows, n_cols, wavelet, levels, workers=workers)
     lay = layout(n_rows, n_cols, levels)
     keep = select_taps(t, lay, K, rule)
     kt = t.subset(keep)
