@@ -72,66 +72,86 @@ __device__ __forceinline__ T tap_value(const VPlanDev& P, int i) {
     else return P.v32[i];
 }
 
+// one register tap for the outputs c = lt + To e of this thread
+template <typename T>
+__device__ __forceinline__ void reg_tap(const VTap& tp, T v, const T* __restrict__ in, int lt, int To, int cols,
+                                        T (&acc)[4]) {
+    const T* __restrict__ src = in + tp.in_off;
+    if (tp.mode & kVTapU) {
+        // same level: ci = c - ox (mod cols)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = lt + To * e;
+            if (c < cols) {
+                int ci = c - tp.ox;
+                if (ci < 0) ci += cols;
+                acc[e] += v * src[ci];
+            }
+        }
+    } else {
+        // input finer (or same level, transposed): ci = ox + r c (mod r cols)
+        const int lgr = tp.mode & 255, cin = cols << lgr;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int c = lt + To * e;
+            if (c < cols) {
+                int ci = tp.ox + (c << lgr);
+                if (ci >= cin) ci -= cin;
+                acc[e] += v * src[ci];
+            }
+        }
+    }
+}
+
 template <typename T, int EPI>
 __global__ void __launch_bounds__(kVThreads) vrow_kernel(VPlanDev P, const T* __restrict__ in, T* __restrict__ out,
                                                         VEpi ep) {
     __shared__ T acc_s[kVMaxCols];
-    __shared__ T red[kVThreads];
+    __shared__ T red[4 * kVThreads];
     if (EPI == kVK1 || EPI == kVK2) {
         if (*(volatile int*)&ep.st->stop) return;
     }
     const int t = threadIdx.x;
     const VRow R = P.rows[P.order[blockIdx.x]];
     const int cols = R.cols;
-    // taps summed in registers: outputs c = lt + To e, G groups of threads split the taps
-    const int To = cols >= kVThreads ? kVThreads : ((cols + 31) & ~31);
+    // taps summed in registers: a thread owns the outputs c = lt + To e (e < 4), To = the
+    // row's columns / 4 rounded up to a warp (32 ... 256); the G = 256 / To groups of threads
+    // split the taps, two taps in flight per thread, and their sums are added in group order
+    const int q = (cols + 3) >> 2;
+    const int To = q <= 32 ? 32 : (q >= kVThreads ? kVThreads : ((q + 31) & ~31));
     const int G = kVThreads / To;
     const int grp = t / To, lt = t - grp * To;
     T acc[4] = {0, 0, 0, 0};
-    // (threads past the last whole group, when To does not divide 256, take no taps)
-    for (int i = R.t0 + grp; grp < G && i < R.t1; i += G) {
-        const VTap tp = P.taps[i];
-        const T v = tap_value<T>(P, i);
-        const T* __restrict__ src = in + tp.in_off;
-        if (tp.mode & kVTapU) {
-            // same level: ci = c - ox (mod cols)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int c = lt + To * e;
-                if (c < cols) {
-                    int ci = c - tp.ox;
-                    if (ci < 0) ci += cols;
-                    acc[e] += v * src[ci];
-                }
-            }
-        } else {
-            // input finer (or same level, transposed): ci = ox + r c (mod r cols)
-            const int lgr = tp.mode & 255, cin = cols << lgr;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int c = lt + To * e;
-                if (c < cols) {
-                    int ci = tp.ox + (c << lgr);
-                    if (ci >= cin) ci -= cin;
-                    acc[e] += v * src[ci];
-                }
-            }
+    if (grp < G) {   // (threads past the last whole group, when To does not divide 256, idle)
+        int i = R.t0 + grp;
+        for (; i + G < R.t1; i += 2 * G) {
+            const VTap t0 = P.taps[i], t1 = P.taps[i + G];
+            const T v0 = tap_value<T>(P, i), v1 = tap_value<T>(P, i + G);
+            reg_tap<T>(t0, v0, in, lt, To, cols, acc);
+            reg_tap<T>(t1, v1, in, lt, To, cols, acc);
         }
+        if (i < R.t1) reg_tap<T>(P.taps[i], tap_value<T>(P, i), in, lt, To, cols, acc);
     }
     if (G == 1) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int c = t + kVThreads * e;
+            const int c = lt + To * e;
             if (c < cols) acc_s[c] = acc[e];
         }
     } else {
-        // cols <= To: one output per thread; the groups' sums added in group order
-        red[t] = acc[0];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) red[e * kVThreads + t] = acc[e];
         __syncthreads();
-        if (t < cols) {
-            T s = 0;
-            for (int g = 0; g < G; ++g) s += red[g * To + t];
-            acc_s[t] = s;
+        if (t < To) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int c = t + To * e;
+                if (c < cols) {
+                    T s = 0;
+                    for (int g = 0; g < G; ++g) s += red[e * kVThreads + g * To + t];
+                    acc_s[c] = s;
+                }
+            }
         }
     }
     __syncthreads();
