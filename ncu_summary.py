@@ -5,7 +5,7 @@ total device time and share, split by NVTX range when ncu recorded one:
 
     python -m ncu_summary launches.csv
 
-Record the DRAM bytes per launch of the two FISTA kernels from a capture that holds
+Record the DRAM bytes per launch of the FISTA kernels (circulant or row-varying) from a capture that holds
 dram__bytes_read.sum and dram__bytes_write.sum (the first launch of each kernel), with the
 hash of the sources they were compiled from, in profiles/traffic.json (bench.py reports the
 record only while the sources still hash the same):
@@ -25,8 +25,13 @@ from collections import defaultdict
 
 CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1512_08401_gb300", "csrc")
 TILE_SOURCES = ["tile.cu", "tile.cuh", "device_util.cuh", "layout_types.h", "wdb_internal.h"]
-# name prefixes of the two FISTA kernels (tile_kernel<float, EPI[, SPLIT]>)
-FISTA_KERNELS = {"k1_residual": "tile_kernel<float, 2", "k2_step": "tile_kernel<float, 3"}
+VROW_SOURCES = ["vtheta.cu", "vtheta.h", "device_util.cuh", "layout_types.h", "wdb_internal.h"]
+# name prefixes of the FISTA kernels: tile_kernel<float, EPI, ...> (circulant Theta_K) and
+# vrow_kernel<float, EPI> (row-varying Theta_K)
+FISTA_KERNELS = {"k1_residual": "tile_kernel<float, 2", "k2_step": "tile_kernel<float, 3",
+                 "vk1_residual": "vrow_kernel<float, 1", "vk2_step": "vrow_kernel<float, 2"}
+KERNEL_SOURCES = {"k1_residual": TILE_SOURCES, "k2_step": TILE_SOURCES,
+                  "vk1_residual": VROW_SOURCES, "vk2_step": VROW_SOURCES}
 
 
 def kernel_sources_sha256(files) -> str:
@@ -129,14 +134,14 @@ def write_traffic(csv_path: str, workload: str, profile: str, record: str) -> di
     rec.setdefault("_about", "DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the "
                              "FISTA kernels from ncu captures; valid while the listed sources hash to "
                              "sources_sha256.")
-    sha = kernel_sources_sha256(TILE_SOURCES)
     ent = rec.setdefault(workload, {})
     for key, d in got.items():
         rd, wr = d.get("dram__bytes_read.sum", 0.0), d.get("dram__bytes_write.sum", 0.0)
+        src = KERNEL_SOURCES[key]
         ent[key] = {"kernel": d["kernel"], "dram_bytes_per_launch": int(round(rd + wr)),
                     "dram_read": int(round(rd)), "dram_write": int(round(wr)),
                     "duration_us_under_ncu": round(d.get("gpu__time_duration.sum", 0.0), 2),
-                    "sources": TILE_SOURCES, "sources_sha256": sha, "profile": profile}
+                    "sources": src, "sources_sha256": kernel_sources_sha256(src), "profile": profile}
     with open(record, "w") as fh:
         json.dump(rec, fh, indent=1)
         fh.write("\n")
