@@ -279,6 +279,22 @@ def large_problem() -> Problem:
     return make_problem(4096, gaussian_psf(4.0, 41), 1e-3, config_id=2, name="4096^2 gaussian s4")
 
 
+def blur_pool(count: int, config_id: int):
+    """`count` seeded blurs drawn like batch_mix's: a Gaussian of sigma ~ U[1, 4] on a
+    (2 ceil(3 sigma)+1)^2 support or a motion line of length U{9..21} (odd) at an angle
+    U[0, pi), probability 1/2 each. Returns [(psf, name)]."""
+    rng = rng_for(config_id, 998)
+    out = []
+    for _ in range(count):
+        if rng.uniform() < 0.5:
+            s = rng.uniform(1.0, 4.0)
+            out.append((gaussian_psf(s, 2 * int(np.ceil(3 * s)) + 1), f"gauss{s:.2f}"))
+        else:
+            L = int(rng.choice(np.arange(9, 22, 2)))
+            out.append((motion_line_psf(L, rng.uniform(0.0, np.pi)), f"motion{L}"))
+    return out
+
+
 def varying_problem(n: int = 512, sigma0: float = 1.0, sigma1: float = 4.0, k: int = 25,
                     lam: float = 1e-3, instance: int = 0, noise: float = 0.01) -> Problem:
     """n x n, row-varying Gaussian (sigma from sigma0 at the top row to sigma1 at the bottom,

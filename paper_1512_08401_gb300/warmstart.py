@@ -25,6 +25,49 @@ def observations(n: int, psf: np.ndarray, count: int, config_id: int, first: int
     return [synthetic.make_problem(n, psf, 0.0, config_id, first + i, noise=noise).u0 for i in range(count)]
 
 
+def _observation_job(args):
+    n, psf, config_id, instance, noise = args
+    return synthetic.make_problem(n, psf, 0.0, config_id, instance, noise=noise).u0.astype(np.float32)
+
+
+def observations_mixed(n: int, psfs, per_blur: int, config_id: int, noise: float = 0.01, workers: int = 1):
+    """per_blur seeded observations for each blur, blur-major (instance = blur index * per_blur
+    + image index), as a float32 array [len(psfs) * per_blur, n, n]; workers > 1 spreads the
+    synthesis over spawned processes."""
+    jobs = [(n, psf, config_id, k * per_blur + i, noise) for k, psf in enumerate(psfs) for i in range(per_blur)]
+    if workers <= 1:
+        return np.stack([_observation_job(j) for j in jobs])
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as pool:
+        return np.stack(list(pool.map(_observation_job, jobs, chunksize=64)))
+
+
+def solution_images_batched(thetas, U, lam: float, iters: int, tol: float = 0.0, precond: str = "spai",
+                            wavelet: str = "db4"):
+    """Targets Psi x* for observations U [len(thetas) * per_blur, n, n] (blur-major, problem
+    k * per_blur + i uses thetas[k]): x* from the batched solver (one problem per blur handle
+    per call, `iters` iterations or the relative gap `tol`), then one IDWT each."""
+    import torch
+    nb = len(thetas)
+    M = U.shape[0]
+    per = M // nb
+    n_rows, n_cols, J = thetas[0].info.n_rows, thetas[0].info.n_cols, thetas[0].info.levels
+    N = n_rows * n_cols
+    X = torch.zeros(nb, N, device="cuda")
+    T = torch.empty(M, n_rows, n_cols, device="cuda")
+    Uf = U.view(M, N)
+    params = [dict(lam=lam, max_iters=iters, tol=tol, precond=precond, check_every=20)] * nb
+    iters_run = []
+    for i in range(per):
+        X.zero_()
+        res = wdb.solve_batch(thetas, [Uf[k * per + i] for k in range(nb)], [X[k] for k in range(nb)], params)
+        iters_run += [r["iters"] for r in res]
+        for k in range(nb):
+            wdb.idwt(X[k], T[k * per + i].view(-1), n_rows, n_cols, wavelet, J)
+    return T, iters_run
+
+
 def _stack(arrs):
     import torch
     return torch.from_numpy(np.ascontiguousarray(np.stack(arrs), dtype=np.float32)).cuda()
