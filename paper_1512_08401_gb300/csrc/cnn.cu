@@ -14,9 +14,12 @@
 //
 // Convolution kernel: one CTA per 16 x 16 output tile of one image; the input tile with its
 // one-pixel periodic halo and the CTA's weights are staged in shared memory; every thread
-// accumulates all output channels of one pixel. The data gradient is the same kernel with
-// flipped, transposed weights. The weight gradient keeps a thread's 36 (c_out, c_in, tap)
-// sums in registers and slides along image rows held in registers.
+// accumulates all output channels of one pixel. The data gradient is a convolution of the
+// output gradient with flipped, transposed weights: on the tensor cores (the gradient rounded
+// to BF16) wherever both channel counts are 2 ... 32, else this kernel. The weight gradient is
+// on the tensor cores under the same condition (wgrad_mma_kernel, the gradient rounded to
+// BF16 as it is staged); the layers with one channel (input, output) use wgrad_kernel, which
+// keeps a thread's 36 (c_out, c_in, tap) sums in registers and slides along image rows.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -340,6 +343,115 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const TIN* __restrict__ in, 
     }
 }
 
+// Tensor-core weight gradient (2 <= C_in, C_out <= 32): dW[co][ci][tap] += sum over pixels of
+// g[co][p] x[ci][p + offset(tap)], an implicit GEMM per 16 x 16 tile with M = C_out (two
+// m-tiles of 16), N = C_in per tap (four n-tiles of 8) and K = the tile's 256 pixels, one
+// tile row of 16 per k-step. The FP32 output gradient is rounded to BF16 as it is staged
+// ([32 c_out][kGP], pixels contiguous: A fragments by ldmatrix), the input tile with its
+// periodic halo channels-last ([18 x 18][kCP]: B fragments by ldmatrix.trans). Warp w owns
+// the output tile (m, n) = (w / 4, w % 4) for all nine taps, so one A fragment serves nine
+// mma per k-step; the persistent CTAs accumulate over their tiles in registers and add the
+// result to dW with FP32 atomics. db is summed from the FP32 gradient.
+constexpr int kGP = 264;   // pixel pitch of the staged gradient tile (528-byte rows)
+constexpr size_t kWgSmem = sizeof(bf16) * (kMmaHalo + 32 * kGP);
+
+__device__ __forceinline__ void ldsm_x2_trans(unsigned addr, unsigned& r0, unsigned& r1) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0, %1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+__global__ void __launch_bounds__(256) wgrad_mma_kernel(const bf16* __restrict__ in, int CI, int CO, int H, int W,
+                                                        int B, const float* __restrict__ dout, float* dW, float* db) {
+    extern __shared__ __align__(16) unsigned char cnn_smem[];
+    bf16* halo = reinterpret_cast<bf16*>(cnn_smem);   // [18*18][kCP]
+    bf16* gs = halo + kMmaHalo;                        // [32][kGP]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int m = warp >> 2, nt = warp & 3;
+    float acc[9][4];
+#pragma unroll
+    for (int k = 0; k < 9; ++k)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[k][e] = 0.f;
+    float bs[32];       // db partials: thread t sums pixel t of every tile, per c_out
+#pragma unroll
+    for (int j = 0; j < 32; ++j) bs[j] = 0.f;
+    __shared__ float s_db[32];
+    if (t < 32) s_db[t] = 0.f;
+    const int tx = (W + kT - 1) / kT, ty = (H + kT - 1) / kT;
+    const int tiles = B * tx * ty;
+    const size_t plane = (size_t)H * W;
+    const unsigned hb = (unsigned)__cvta_generic_to_shared(halo), gb = (unsigned)__cvta_generic_to_shared(gs);
+    const int a_row = lane & 15, a_k = (lane >> 4) * 8;        // A: c_out rows, pixel halves
+    const int b_k = (lane & 7) + ((lane >> 3) & 1) * 8;         // B (trans): pixel rows of the two 8 x 8 halves
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int b = tile / (tx * ty), r = tile - b * tx * ty;
+        const int ty0 = (r / tx) * kT, tx0 = (r % tx) * kT;
+        __syncthreads();   // the previous tile's fragments are read
+        const bf16* inb = in + (size_t)b * CI * plane;
+        for (int q = t; q < kHalo * kHalo; q += 256) {
+            const int y = q / kHalo, x = q - y * kHalo;
+            int gy = ty0 + y - 1, gx = tx0 + x - 1;
+            while (gy < 0) gy += H;
+            while (gy >= H) gy -= H;
+            while (gx < 0) gx += W;
+            while (gx >= W) gx -= W;
+            const bf16* src = inb + (size_t)gy * W + gx;
+            unsigned packed[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const unsigned short lo = (2 * c < CI) ? __bfloat16_as_ushort(src[(size_t)(2 * c) * plane]) : 0;
+                const unsigned short hi = (2 * c + 1 < CI) ? __bfloat16_as_ushort(src[(size_t)(2 * c + 1) * plane]) : 0;
+                packed[c] = (unsigned)lo | ((unsigned)hi << 16);
+            }
+            uint4* dst = reinterpret_cast<uint4*>(halo + q * kCP);
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                dst[c] = make_uint4(packed[4 * c], packed[4 * c + 1], packed[4 * c + 2], packed[4 * c + 3]);
+        }
+        const float* gbase = dout + (size_t)b * CO * plane;
+        {
+            const int oy = ty0 + (t >> 4), ox = tx0 + (t & 15);
+            const bool inside = oy < H && ox < W;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float v = (j < CO && inside) ? gbase[(size_t)j * plane + (size_t)oy * W + ox] : 0.f;
+                gs[j * kGP + t] = __float2bfloat16(v);
+                bs[j] += v;
+            }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int kr = 0; kr < kT; ++kr) {
+            unsigned a0, a1, a2, a3;
+            ldsm_x4(gb + 2u * (unsigned)((m * 16 + a_row) * kGP + kr * 16 + a_k), a0, a1, a2, a3);
+#pragma unroll
+            for (int tap = 0; tap < 9; ++tap) {
+                const int ky = tap / 3, kx = tap - ky * 3;
+                unsigned b0, b1;
+                ldsm_x2_trans(hb + 2u * (unsigned)(((kr + ky) * kHalo + b_k + kx) * kCP + nt * 8), b0, b1);
+                mma_bf16(acc[tap], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // D fragment: rows (c_out) m*16 + lane/4 (+8), columns (c_in) nt*8 + 2 (lane % 4) (+1)
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int co = m * 16 + (lane >> 2) + ((e >> 1) << 3);
+            const int ci = nt * 8 + (lane & 3) * 2 + (e & 1);
+            if (co < CO && ci < CI) atomicAdd(&dW[((size_t)co * CI + ci) * 9 + tap], acc[tap][e]);
+        }
+    // db: per c_out, the threads' pixel sums reduced by warp, then across warps in shared memory
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        float v = bs[j];
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) atomicAdd(&s_db[j], v);
+    }
+    __syncthreads();
+    if (t < CO) atomicAdd(&db[t], s_db[t]);
+}
+
 // Wt[ci][co][8-k] = W[co][ci][k] (data gradient weights)
 __global__ void flip_transpose_kernel(const bf16* __restrict__ w, bf16* __restrict__ wt, int CO, int CI) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -488,6 +600,8 @@ struct wdb_cnn {
     float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // FP32 master, grad, Adam moments
     bf16 *pb = nullptr, *wt = nullptr;                              // BF16 weights, flipped copy
     bf16* wlay = nullptr;                                           // per layer: [tap][32][kCP] for the MMA path
+    bf16* wlay_t = nullptr;                                         // flipped copy in the MMA layout (data gradient)
+    bf16* gb16 = nullptr;                                           // data-gradient input rounded to BF16
     // activations (BF16) per level: inp (l > 0), a, e; decoder s, a, d
     std::vector<bf16*> e_inp, e_a, e_e, d_s, d_a, d_d;
     std::vector<float*> g_enc;          // gradient accumulators of e_l (FP32)
@@ -543,6 +657,33 @@ wdb_status conv(const wdb_cnn* n, int layer, const TIN* in, int B, int l, int ou
     }
     const float* bias = flipped ? nullptr : n->p + cl.b_off;
     dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT, B);
+    if constexpr (std::is_same<TIN, float>::value) {
+        if (flipped && CI >= 2 && CO >= 2 && CI <= kCMax && CO <= kCMax) {
+            // data gradient on the tensor cores: the FP32 gradient rounded to BF16 (as the
+            // feature maps are stored), the flipped weights in the MMA layout
+            const long long cnt = (long long)B * CI * H * W;
+            to_bf16_kernel<<<ew(cnt), 256, 0, st>>>(in, n->gb16, cnt);
+            relayout_weights_kernel<<<(kMmaW + 255) / 256, 256, 0, st>>>(w, n->wlay_t, CO, CI);
+            count_launch(2);
+            static unsigned long long attr_t = 0ull;
+            if (!done_on_device(&attr_t)) {
+                WDB_CK(cudaFuncSetAttribute(conv3x3_mma_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kMmaSmem));
+                WDB_CK(cudaFuncSetAttribute(conv3x3_mma_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kMmaSmem));
+                mark_on_device(&attr_t);
+            }
+            if (CI <= 16)
+                conv3x3_mma_kernel<16><<<grid, 256, kMmaSmem, st>>>(n->gb16, CI, CO, H, W, n->wlay_t, nullptr, out_mode,
+                                                                    out, relu, mask, residual);
+            else
+                conv3x3_mma_kernel<32><<<grid, 256, kMmaSmem, st>>>(n->gb16, CI, CO, H, W, n->wlay_t, nullptr, out_mode,
+                                                                    out, relu, mask, residual);
+            count_launch();
+            WDB_CK(cudaGetLastError());
+            return WDB_OK;
+        }
+    }
     if constexpr (std::is_same<TIN, bf16>::value) {
         if (!flipped && CI >= 2 && CO >= 2 && CI <= kCMax && CO <= kCMax) {   // BF16 feature maps: tensor cores
             const bf16* wl = n->wlay + (size_t)layer * kMmaW;
@@ -601,6 +742,21 @@ wdb_status wgrad(const wdb_cnn* n, int layer, const TIN* in, const float* dout, 
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int grid = std::max(1, std::min(tiles, 2 * std::max(sms, 1)));
+    if constexpr (std::is_same<TIN, bf16>::value) {
+        if (cl.ci >= 2 && cl.co >= 2 && cl.ci <= kCMax && cl.co <= kCMax) {   // tensor cores
+            static unsigned long long attr_m = 0ull;
+            if (!done_on_device(&attr_m)) {
+                WDB_CK(cudaFuncSetAttribute(wgrad_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kWgSmem));
+                mark_on_device(&attr_m);
+            }
+            wgrad_mma_kernel<<<grid, 256, kWgSmem, st>>>(in, cl.ci, cl.co, H, W, B, dout, n->g + cl.w_off,
+                                                         n->g + cl.b_off);
+            count_launch();
+            WDB_CK(cudaGetLastError());
+            return WDB_OK;
+        }
+    }
     wgrad_kernel<TIN><<<grid, 256, smem, st>>>(in, cl.ci, cl.co, H, W, B, dout, n->g + cl.w_off, n->g + cl.b_off);
     count_launch();
     WDB_CK(cudaGetLastError());
@@ -819,6 +975,7 @@ wdb_status wdb_cnn_create(int levels, int channels, int height, int width, int m
     A(&n->pb, n->n_params);
     A(&n->wt, (size_t)C * C * 9);
     A(&n->wlay, (size_t)kMmaW * n->convs.size());
+    A(&n->wlay_t, (size_t)kMmaW);
     const size_t B = (size_t)max_batch;
     n->e_inp.assign(levels, nullptr);
     n->e_a.assign(levels, nullptr);
@@ -840,6 +997,7 @@ wdb_status wdb_cnn_create(int levels, int channels, int height, int width, int m
         A(&n->g_enc[l], cnt);
     }
     const size_t full = B * C * (size_t)height * width;
+    A(&n->gb16, full);
     A(&n->g0, full);
     A(&n->g1, full);
     A(&n->g2, full);

@@ -8,7 +8,9 @@ FP32 accumulation and FP32 gradients. Two comparisons:
     2e-2 relative and the forward correction v - u within 5e-2 (the correction is about 10x
     smaller than the feature maps at initialisation, so their 2^-9 rounding shows up 10x);
   * against the oracle evaluated with every stored feature map rounded to BF16 (its `store`
-    hook), so that both sides take the ReLU decisions on the same values: every gradient
+    hook), so that both sides take the ReLU decisions on the same values, and with the
+    gradient rounded to BF16 where the library's tensor-core data-gradient convolutions read
+    it (its `gstore` hook): every gradient
     tensor within `tol` relative (2-norm). What is left is FP32 against FP64 accumulation,
     which moves a value across a BF16 rounding boundary with probability about
     (accumulation error / BF16 spacing), near 3e-4 per value for 288-term sums. With a few
@@ -90,7 +92,7 @@ def compare(wdb, levels, channels, u, t, seed, tol):
     loss, g = net.loss_grad(U, T)
     v_ref = ocnn.forward(p, u, levels)[0]
     l_ref = ocnn.loss_and_grads(p, u, t, levels)[0]
-    l_bf, g_bf, v_bf = ocnn.loss_and_grads(p, u, t, levels, store=bf16_round)
+    l_bf, g_bf, v_bf = ocnn.loss_and_grads(p, u, t, levels, store=bf16_round, gstore=bf16_round)
     errs = {"v-u (fp64)": rel(V.cpu().numpy() - u, v_ref - u), "loss (fp64)": abs(loss - l_ref) / l_ref,
             "v-u (bf16 maps)": rel(V.cpu().numpy() - u, v_bf - u), "loss (bf16 maps)": abs(loss - l_bf) / l_bf}
     gg = ocnn.unflatten(g.astype(np.float64), levels, channels)
