@@ -80,9 +80,20 @@ def test_kkt_and_gap_fp64_against_oracle(wdb, small, iters):
         assert abs(a_ - b_) <= 1e-12 * max(1.0, abs(b_))
     assert abs(k["objective"] - pr) <= 1e-12 * pr and k["support"] == int(np.count_nonzero(xg))
     if iters == 3000:
-        # at convergence the conditions hold up to the FP32 rounding of the iterate (about
-        # 4e-4 of w for coefficients of size ~10 on this problem)
-        assert off <= 2e-3 and on <= 2e-3
+        # at convergence the conditions hold up to the resolution of the FP32 iteration, two
+        # terms (relative to w):
+        #  * the step: an iterate stops moving once (tau / P)(g + w sign x) is below half an
+        #    ulp of x, so g can stay ulp(x) P / (2 tau) away; twice that is taken (FISTA's
+        #    momentum does not settle exactly);
+        #  * the residual: kernel 1 forms r = Theta_K x - x0 in FP32 from terms of size
+        #    |x0| (cancellation), so r carries about ulp(max|x0|) per entry and the
+        #    library's g differs from the FP64 g by up to ulp(max|x0|) times the largest
+        #    column sum of |Theta_K|
+        ulp_x = float(np.max(np.spacing(np.abs(xg).astype(np.float32))))
+        ulp_x0 = float(np.spacing(np.float32(np.abs(x0f).max())))
+        colsum = float(np.asarray(abs(case.th.mat).sum(axis=0)).max())
+        floor = (ulp_x * float(np.max(P)) / tau + ulp_x0 * colsum) / lam
+        assert off <= floor and on <= floor, (off, on, floor)
     g.free()
 
 
