@@ -59,14 +59,18 @@ def summarise(path: str) -> str:
     vi = head.index("Metric Value")
     ui = head.index("Metric Unit")
     ri = next((i for i, h in enumerate(head) if h.startswith("NVTX") or h == "thread_domain:push_pop_ranges"), None)
+    mi = head.index("Metric Name") if "Metric Name" in head else None
     tot = defaultdict(float)
     cnt = defaultdict(int)
     for r in rows[1:]:
         if len(r) <= max(ki, vi):
             continue
+        if mi is not None and r[mi] != "gpu__time_duration.sum":
+            continue   # other metrics of the same launch
         v = float(r[vi].replace(",", ""))
         unit = r[ui]
-        ns = v * {"nsecond": 1, "usecond": 1e3, "msecond": 1e6, "second": 1e9}.get(unit, 1)
+        ns = v * {"nsecond": 1, "ns": 1, "usecond": 1e3, "us": 1e3, "msecond": 1e6, "ms": 1e6, "second": 1e9,
+                  "s": 1e9}.get(unit, 1)
         rng = r[ri] if ri is not None else ""
         key = (rng, short(r[ki]))
         tot[key] += ns

@@ -44,6 +44,18 @@ def test_fista_dram_first_launch_and_units(tmp_path):
     assert got["k1_residual"]["kernel"] == "tile_kernel<float, 2, 0>"
 
 
+def test_launch_summary_counts_time_rows_only(tmp_path):
+    # a metrics log with three metrics per launch: launches and shares come from the
+    # duration rows alone, in their own units
+    p = tmp_path / "log.csv"
+    _metrics_log(p)
+    out = ns.summarise(str(p))
+    assert "5 launches" in out
+    shares = sorted(float(ln.split()[-1].rstrip("%")) for ln in out.splitlines()[2:])
+    total = 1000 + 45009 + 68500          # ns: K4 1 us, K1 45000 + 9 ns, K2 59.5 + 9 us
+    assert shares == pytest.approx(sorted([100 * 1000 / total, 100 * 45009 / total, 100 * 68500 / total]), abs=0.05)
+
+
 def test_fista_dram_raw_page(tmp_path):
     p = tmp_path / "raw.csv"
     head = ["ID", "Kernel Name", "dram__bytes_read.sum", "dram__bytes_write.sum", "gpu__time_duration.sum"]
