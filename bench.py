@@ -507,9 +507,20 @@ def run_batch(args):
     build.build()
     wdb.lib()
     probs = synthetic.batch_mix(args.problems)
+    if args.profile:
+        # the program of the batch kernel's ncu captures: the 256^2 problems of the mix, a
+        # few fixed iterations of one batched solve
+        probs = [p for p in probs if p.u0.shape[0] == 256]
     t0 = time.perf_counter()
     th = [wdb.Theta.build(p.psf, p.u0.shape[0], p.u0.shape[1], "db4", 5, K=30 * p.u0.size) for p in probs]
     build_s = time.perf_counter() - t0
+    if args.profile:
+        us = [torch.from_numpy(p.u0.astype(np.float32).ravel()).cuda() for p in probs]
+        xs = [torch.zeros(t.N, device="cuda") for t in th]
+        wdb.solve_batch(th, us, xs, [dict(lam=p.lam, max_iters=3, tol=0.0, precond=PRECOND) for p in probs])
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": "ok", "problems": len(probs)}))
+        return 0
     us = [torch.from_numpy(p.u0.astype(np.float32).ravel()).cuda() for p in probs]
     xs = [torch.zeros(t.N, device="cuda") for t in th]
     # E* of every problem (long untimed batched run), targets at 1e-4 relative

@@ -5,7 +5,8 @@
 // check_every iterations are captured in a CUDA graph and replayed until no problem runs;
 // between chunks the host compacts the two work lists to the problems still running (the
 // kernels read the item counts from device memory, so the captured graph stays valid).
-// The tiles come from each operator's batch plans, whose tile sides are the autotuner's.
+// The tiles come from each operator's batch plans, whose tile sides are the autotuner's and
+// whose items are grouped (one item per level and tile covers every subband of the level).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -184,7 +185,10 @@ wdb_status solve_batch(int B, wdb_theta* const* ths, const float* const* u, floa
     A.n_items_dev = d_counts + 1;
     F.buf_elems = A.buf_elems = buf_elems;
     F.smem_bytes = A.smem_bytes = 2 * buf_elems * (int)sizeof(float);
-    F.grid = A.grid = std::max(1, tile_batch_grid(F.smem_bytes));
+    bool grouped = false;
+    for (int b = 0; b < B; ++b) grouped = grouped || hp[b].fwd.n_grp > 0 || hp[b].adj.n_grp > 0;
+    F.grouped = A.grouped = grouped ? 1 : 0;
+    F.grid = A.grid = std::max(1, tile_batch_grid(F.smem_bytes, grouped));
     // chunks of m iterations in a CUDA graph, replayed until no problem is running
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;

@@ -453,7 +453,10 @@ wdb_status theta_batch_plans(wdb_theta* th, cudaStream_t st) {
     for (int op = 0; op < 2; ++op) {
         const std::vector<TileTune>* tune =
             (int)th->tune_levels[op].size() == th->lay.S ? &th->tune_levels[op] : nullptr;
-        th->bplan[op] = make_tile_plan(th->lay, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, tune, 0, 16.0);
+        // grouped items: one item per (level, tile) computes every subband of the level, so
+        // the per-item set-up and staging of the many small items of a batch are shared
+        th->bplan[op] = make_tile_plan(th->lay, th->tent[op], 4, kTileSmemBudget, th->plan_ctas, tune, 0, 16.0, 0.0,
+                                       false, true);
         WDB_TRY(upload_plan(th, th->bplan[op], th->bargs[op], st));
     }
     th->bplan_ok = true;

@@ -1331,8 +1331,12 @@ __device__ __forceinline__ void flush_partials(Partials& pt, double* sums, doubl
     pt = Partials();
 }
 
-template <int EPI>
-__global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B) {
+// GRP: the plans have grouped items (one item computes the tile of every subband of a level,
+// one accumulator set and one epilogue per member subband), as in tile_kernel; that instance
+// runs two CTAs per SM so that its four accumulator sets stay in registers
+template <int EPI, bool GRP>
+__global__ void __launch_bounds__(kTileThreads, GRP ? 2 : 3) tile_batch_kernel(BatchArgs B) {
+    constexpr int M = GRP ? 4 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* const buf0 = reinterpret_cast<float*>(smem_raw);
     float* const buf1 = buf0 + B.buf_elems;
@@ -1374,7 +1378,11 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         stage_batch<float>(pl, in_of(bw.p), pl.items[bw.item], bi, S, tab);
     }
     cp_async_commit();
-    float acc[1][4] = {{0.f, 0.f, 0.f, 0.f}};
+    float acc[M][4];
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[k][e] = 0.f;
     Partials pt;
     while (it < n_items) {
         const BatchItem bw = B.items[it];
@@ -1400,9 +1408,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
         __syncthreads();
         const SubbandDev so = P.sb[w.o];
         const ThreadMap tm = thread_map(w);
-        compute_batch<float, 1>(pl, in_of(bw.p), w, so, bi, S, tab, tm, acc);
+        compute_batch<float, M>(pl, in_of(bw.p), w, so, bi, S, tab, tm, acc);
         if (bi + 1 == w.batch_end) {
-            group_reduce<float>(tm, acc[0], red_buf);
             EpiArgs ep{};
             ep.x0 = P.x0;
             ep.y = P.y;
@@ -1414,10 +1421,27 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_batch_kernel(BatchArgs B
                 const int k = P.st->k;
                 beta = P.st->ista ? 0.f : (float)(k - 1) / (float)(k + 2);
             }
-            epilogue<float, EPI>(w, so, tm, acc[0], (EPI == kK1) ? P.r : nullptr, ep, beta, pt);
+            if (!GRP) {
+                group_reduce<float>(tm, acc[0], red_buf);
+                epilogue<float, EPI>(w, so, tm, acc[0], (EPI == kK1) ? P.r : nullptr, ep, beta, pt);
+            } else {
+                // one epilogue per member subband of the group (same geometry)
+                const int nm = w.nm() > 0 ? w.nm() : 1;
+#pragma unroll
+                for (int k = 0; k < M; ++k) {
+                    if (k >= nm) break;
+                    if (k > 0 && tm.G > 1) __syncthreads();   // red_buf reused
+                    group_reduce<float>(tm, acc[k], red_buf);
+                    TileItem wk = w;
+                    wk.o = w.o + k;
+                    epilogue<float, EPI>(wk, P.sb[wk.o], tm, acc[k], (EPI == kK1) ? P.r : nullptr, ep, beta, pt);
+                }
+            }
             flush_partials<EPI>(pt, P.sums, red_d);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) acc[0][e] = 0.f;
+            for (int k = 0; k < M; ++k)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[k][e] = 0.f;
         }
         it = nit;
         bi = nbi;
@@ -1508,17 +1532,23 @@ wdb_status launch_tile(const TileArgs& A, const T* in, T* out, const EpiArgs& ep
     return launch_tile_as<T, EPI, false, false, false>(A, in, out, ep, st, pdl);
 }
 
-template <int EPI>
-wdb_status launch_batch(const BatchArgs& B, cudaStream_t st) {
+template <int EPI, bool GRP>
+wdb_status launch_batch_as(const BatchArgs& B, cudaStream_t st) {
     static unsigned long long attr = 0ull;
     if (!done_on_device(&attr)) {
-        WDB_CK(cudaFuncSetAttribute(tile_batch_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        WDB_CK(cudaFuncSetAttribute(tile_batch_kernel<EPI, GRP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    200 * 1024));
         mark_on_device(&attr);
     }
-    tile_batch_kernel<EPI><<<B.grid, kTileThreads, B.smem_bytes, st>>>(B);
+    tile_batch_kernel<EPI, GRP><<<B.grid, kTileThreads, B.smem_bytes, st>>>(B);
     count_launch();
     WDB_CK(cudaGetLastError());
     return WDB_OK;
+}
+
+template <int EPI>
+wdb_status launch_batch(const BatchArgs& B, cudaStream_t st) {
+    return B.grouped ? launch_batch_as<EPI, true>(B, st) : launch_batch_as<EPI, false>(B, st);
 }
 
 }  // namespace
@@ -1536,12 +1566,17 @@ int tile_grid(int smem_bytes) {
     return sms * per;
 }
 
-int tile_batch_grid(int smem_bytes) {
+int tile_batch_grid(int smem_bytes, bool grouped) {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(tile_batch_kernel<kK2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_batch_kernel<kK2>, kTileThreads, smem_bytes);
+    if (grouped) {
+        cudaFuncSetAttribute(tile_batch_kernel<kK2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_batch_kernel<kK2, true>, kTileThreads, smem_bytes);
+    } else {
+        cudaFuncSetAttribute(tile_batch_kernel<kK2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tile_batch_kernel<kK2, false>, kTileThreads, smem_bytes);
+    }
     if (sms <= 0) sms = 1;
     if (per <= 0) per = 1;
     return sms * per;

@@ -233,9 +233,10 @@ struct BatchArgs {
     int grid;
     int buf_elems;                 // largest staging buffer of any problem's plan
     int smem_bytes;
+    int grouped;                   // some problem's plans have grouped items (kernel instance)
 };
 
-int tile_batch_grid(int smem_bytes);
+int tile_batch_grid(int smem_bytes, bool grouped);
 wdb_status batch_k1(const BatchArgs& B, cudaStream_t st);
 wdb_status batch_k2(const BatchArgs& B, cudaStream_t st);
 // x -> sums[0] = ||Theta_K x - x0||^2, sums[1] = sum w|x| for every problem
