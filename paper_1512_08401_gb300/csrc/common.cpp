@@ -4,6 +4,9 @@
 #include <complex>
 #include <cstdarg>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "wdb_internal.h"
 
@@ -309,8 +312,7 @@ static wdb_status symlet(int p, Filters* f) {
     return WDB_OK;
 }
 
-wdb_status wavelet_filters(const char* name, Filters* out) {
-    if (!name) return set_error(WDB_EINVAL, "wavelet name is NULL");
+static wdb_status derive_filters(const char* name, Filters* out) {
     const bool db = std::strncmp(name, "db", 2) == 0, sym = std::strncmp(name, "sym", 3) == 0;
     if (!db && !sym) return set_error(WDB_EINVAL, "unknown wavelet '%s'", name);
     const char* num = name + (db ? 2 : 3);
@@ -318,6 +320,28 @@ wdb_status wavelet_filters(const char* name, Filters* out) {
     long p = std::strtol(num, &end, 10);
     if (end == num || *end != '\0') return set_error(WDB_EINVAL, "unknown wavelet '%s'", name);
     return db ? daubechies((int)p, out) : symlet((int)p, out);
+}
+
+// The spectral factorisation runs once per wavelet name per process (the result depends on
+// the name only); later calls copy the cached filters.
+wdb_status wavelet_filters(const char* name, Filters* out) {
+    if (!name) return set_error(WDB_EINVAL, "wavelet name is NULL");
+    static std::mutex mu;
+    static std::map<std::string, Filters> cache;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(name);
+        if (it != cache.end()) {
+            *out = it->second;
+            return WDB_OK;
+        }
+    }
+    Filters f;
+    WDB_TRY(derive_filters(name, &f));
+    std::lock_guard<std::mutex> lock(mu);
+    cache.emplace(name, f);
+    *out = f;
+    return WDB_OK;
 }
 
 }  // namespace wdb
