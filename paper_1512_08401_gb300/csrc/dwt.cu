@@ -188,19 +188,21 @@ __global__ void __launch_bounds__(256) dwt_level_fast(const float* __restrict__ 
     __shared__ float s_lo[IY][kFT], s_hi[IY][kFT];
     const int oy0 = blockIdx.y * kFT, ox0 = blockIdx.x * kFT;
     const int R2 = R >> 1, C2 = C >> 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // load: one warp per input row, one column pair per lane (C even: a pair never wraps)
-    for (int iy = warp; iy < IY; iy += 8) {
+    // load: one column pair per thread and step over the flattened (row, pair) range,
+    // consecutive pairs of a row on consecutive lanes (C even: a pair never wraps); fully
+    // unrolled over the thread's steps, so that all its loads are in flight together
+#pragma unroll
+    for (int k = 0; k < (IY * PX + 255) / 256; ++k) {
+        const int q = threadIdx.x + 256 * k;
+        if (q >= IY * PX) break;
+        const int iy = q / PX, c = q - iy * PX;
         int gy = 2 * oy0 + iy;
         while (gy >= R) gy -= R;
-        const float* __restrict__ row = in + (size_t)gy * C;
-        for (int c = lane; c < PX; c += 32) {
-            int gx = 2 * (ox0 + c);
-            while (gx >= C) gx -= C;
-            const float2 v = *reinterpret_cast<const float2*>(row + gx);
-            s_ev[iy][c] = v.x;
-            s_od[iy][c] = v.y;
-        }
+        int gx = 2 * (ox0 + c);
+        while (gx >= C) gx -= C;
+        const float2 v = __ldg(reinterpret_cast<const float2*>(in + (size_t)gy * C + gx));
+        s_ev[iy][c] = v.x;
+        s_od[iy][c] = v.y;
     }
     __syncthreads();
     // along x: lo/hi[iy][j] = sum_k h/g[k] in[iy][2j + k]
@@ -251,21 +253,23 @@ __global__ void __launch_bounds__(256) idwt_level_fast(const float* __restrict__
     __shared__ float sLL[CY][CX], sLH[CY][CX], sHL[CY][CX], sHH[CY][CX];
     __shared__ float sLx[2 * kFT][CX], sHx[2 * kFT][CX];
     const int cy0 = blockIdx.y * kFT, cx0 = blockIdx.x * kFT;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int iy = warp; iy < CY; iy += 8) {
+    // load: flattened (row, column) range, fully unrolled over the thread's steps
+#pragma unroll
+    for (int k = 0; k < (CY * CX + 255) / 256; ++k) {
+        const int q = threadIdx.x + 256 * k;
+        if (q >= CY * CX) break;
+        const int iy = q / CX, ix = q - iy * CX;
         int gy = cy0 - H2 + 1 + iy;
         while (gy < 0) gy += R2;
         while (gy >= R2) gy -= R2;
-        const size_t r = (size_t)gy * C2;
-        for (int ix = lane; ix < CX; ix += 32) {
-            int gx = cx0 - H2 + 1 + ix;
-            while (gx < 0) gx += C2;
-            while (gx >= C2) gx -= C2;
-            sLL[iy][ix] = cA[r + gx];
-            sLH[iy][ix] = c01[r + gx];
-            sHL[iy][ix] = c10[r + gx];
-            sHH[iy][ix] = c11[r + gx];
-        }
+        int gx = cx0 - H2 + 1 + ix;
+        while (gx < 0) gx += C2;
+        while (gx >= C2) gx -= C2;
+        const size_t o = (size_t)gy * C2 + gx;
+        sLL[iy][ix] = __ldg(cA + o);
+        sLH[iy][ix] = __ldg(c01 + o);
+        sHL[iy][ix] = __ldg(c10 + o);
+        sHH[iy][ix] = __ldg(c11 + o);
     }
     __syncthreads();
     // along y: rows 2i and 2i + 1 from coefficient rows i - m, m < L/2:
