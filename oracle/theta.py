@@ -35,7 +35,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from .blur import conv_adjoint, conv_matrix, conv_periodic
-from .wavelet import Subband, dwt2, dwt_matrix, idwt2, layout
+from .wavelet import Subband, dwt2, dwt_matrix, idwt2, layout, synthesis_1d, wavelet_filters
 
 ZERO_REL = 1e-14
 
@@ -265,3 +265,41 @@ def build_theta(psf: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels:
     mat = theta_sparse(kt, pr.lay, N)
     return ThetaK(n_rows, n_cols, wavelet, levels, pr.lay, kt, int(K), int(kt.m.sum()),
                   mat, mat.T.tocsr())
+
+
+# ---------------------------------------------------------------------------------------
+# Single entries at any size (separable wavelets)
+# ---------------------------------------------------------------------------------------
+
+def wavelet_1d(n: int, level: int, high: bool, pos: int, wavelet: str) -> np.ndarray:
+    """The 1-D periodic synthesis function of length n of the coefficient `pos` at `level`:
+    a unit coefficient synthesised once with g (high) or h, then with h down to level 0
+    (the axis factor of a 2-D wavelet of oracle.wavelet's separable transform)."""
+    h, g = wavelet_filters(wavelet)
+    c = np.zeros(n >> level)
+    c[pos] = 1.0
+    for s in range(level, 0, -1):
+        c = synthesis_1d(c[None, :], g if (s == level and high) else h, axis=1)[0]
+    return c
+
+
+def theta_entry(psf: np.ndarray, n_rows: int, n_cols: int, wavelet: str, levels: int,
+                a: int, p: tuple, b: int, q: tuple) -> float:
+    """Theta[(a, p), (b, q)] = <psi_{a,p}, H psi_{b,q}> (Eq. matrixH) for one entry.
+
+    Both wavelets are outer products of 1-D functions, psi(y) = f_v(y_r) f_h(y_c), so with
+    (H u)[i] = sum_d psf[d] u[i - d]:
+        <psi_a, H psi_b> = sum_d psf[d] C_v(d_r) C_h(d_c),
+        C(d) = sum_j f_a(j + d) f_b(j)   (periodic),
+    a sum over the PSF support of products of two 1-D correlations."""
+    lay = layout(n_rows, n_cols, levels)
+    sa, sb = lay[a], lay[b]
+    fav = wavelet_1d(n_rows, sa.level, sa.e[0] == 1, p[0], wavelet)
+    fah = wavelet_1d(n_cols, sa.level, sa.e[1] == 1, p[1], wavelet)
+    fbv = wavelet_1d(n_rows, sb.level, sb.e[0] == 1, q[0], wavelet)
+    fbh = wavelet_1d(n_cols, sb.level, sb.e[1] == 1, q[1], wavelet)
+    kh, kw = psf.shape
+    # np.roll(f, -d)[j] = f[(j + d) mod n]
+    Cv = np.array([np.dot(np.roll(fav, -d), fbv) for d in range(-(kh // 2), kh // 2 + 1)])
+    Ch = np.array([np.dot(np.roll(fah, -d), fbh) for d in range(-(kw // 2), kw // 2 + 1)])
+    return float(Cv @ psf @ Ch)

@@ -535,3 +535,39 @@ def test_ista_hand_derived_trajectory():
     for k, xk in _golden_rows("ista_diag.txt"):
         res = solver.fista(lambda v: A * v, lambda v: A * v, b, w, P, 0.5, max_iters=k, momentum=False)
         assert np.array_equal(res.x, np.array(xk)), (k, res.x, xk)
+
+
+@pytest.mark.parametrize("shape,wname,J", [((16, 16), "db2", 2), ((16, 32), "db3", 2), ((32, 32), "sym4", 2)])
+def test_theta_entry_equals_the_dense_definition(shape, wname, J):
+    """theta.theta_entry (one entry from the separable 1-D factors, any size) against
+    D H D^T built from unit vectors, on a non-symmetric PSF (a dropped transpose or a sign
+    of the correlation shift changes the entries)."""
+    R, C = shape
+    psf = synthetic.motion_line_psf(5, 0.7)
+    T = theta.theta_dense(R, C, psf, wname, J)
+    lay = wavelet.layout(R, C, J)
+    rng = np.random.default_rng(4)
+    for _ in range(200):
+        a, b = int(rng.integers(len(lay))), int(rng.integers(len(lay)))
+        sa, sb = lay[a], lay[b]
+        p = (int(rng.integers(sa.rows)), int(rng.integers(sa.cols)))
+        q = (int(rng.integers(sb.rows)), int(rng.integers(sb.cols)))
+        v = theta.theta_entry(psf, R, C, wname, J, a, p, b, q)
+        ref = T[sa.offset + p[0] * sa.cols + p[1], sb.offset + q[0] * sb.cols + q[1]]
+        assert abs(v - ref) <= 1e-14
+
+
+def test_theta_entry_equals_the_probe_construction():
+    n, J = 64, 3
+    psf = synthetic.gaussian_psf(1.5, 9)
+    th = theta.build_theta(psf, n, n, "db4", J, K=10**12)
+    lay = th.lay
+    A = th.mat.tocsr()
+    rng = np.random.default_rng(5)
+    for _ in range(100):
+        a, b = int(rng.integers(len(lay))), int(rng.integers(len(lay)))
+        sa, sb = lay[a], lay[b]
+        p = (int(rng.integers(sa.rows)), int(rng.integers(sa.cols)))
+        q = (int(rng.integers(sb.rows)), int(rng.integers(sb.cols)))
+        ref = A[sa.offset + p[0] * sa.cols + p[1], sb.offset + q[0] * sb.cols + q[1]]
+        assert abs(theta.theta_entry(psf, n, n, "db4", J, a, p, b, q) - ref) <= 1e-13
