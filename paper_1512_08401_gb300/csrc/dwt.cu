@@ -10,6 +10,9 @@
 // in shared memory with coalesced loads, the x pass goes to shared memory, the y pass
 // writes the four outputs (coalesced). HBM-bound: each level reads its input once and
 // writes its outputs once.
+#include <algorithm>
+#include <cstdint>
+
 #include "wdb_internal.h"
 
 namespace wdb {
@@ -308,9 +311,128 @@ __global__ void __launch_bounds__(256) idwt_level_fast(const float* __restrict__
     }
 }
 
+// Persistent, double-buffered form of dwt_level_fast for 16-byte aligned inputs whose width
+// is a multiple of 4: each CTA walks tiles tile += gridDim.x and, while it filters one tile,
+// cp.async brings the next tile's raw input rows (16-byte chunks; a row segment starts at a
+// multiple of 64 columns, chunks past the right edge wrap to column 0) into the other buffer.
+// The x pass reads the raw rows as column pairs (float2), the y pass is dwt_level_fast's.
+template <int L>
+struct PipeGeom {
+    static constexpr int IY = 2 * kFT + L - 2;        // input rows of a tile
+    static constexpr int NCH = (2 * kFT + L - 2 + 3) / 4;   // 16-byte chunks per row
+    static constexpr int RP = 4 * NCH;                // row pitch (floats)
+    static constexpr size_t smem = sizeof(float) * (size_t)(2 * IY * RP + 2 * IY * kFT);
+};
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+template <int L>
+__global__ void __launch_bounds__(256) dwt_level_pipe(const float* __restrict__ in, int R, int C,
+                                                      float* __restrict__ outA, float* __restrict__ d01,
+                                                      float* __restrict__ d10, float* __restrict__ d11,
+                                                      FiltT<float> f) {
+    using G = PipeGeom<L>;
+    extern __shared__ __align__(16) float pipe_smem[];
+    float* const raw0 = pipe_smem;
+    float* const raw1 = raw0 + G::IY * G::RP;
+    float (*s_lo)[kFT] = reinterpret_cast<float (*)[kFT]>(raw1 + G::IY * G::RP);
+    float (*s_hi)[kFT] = s_lo + G::IY;
+    const int R2 = R >> 1, C2 = C >> 1;
+    const int ntx = (C2 + kFT - 1) / kFT, nty = (R2 + kFT - 1) / kFT, nt = ntx * nty;
+    auto stage = [&](int tile, float* buf) {
+        const int oy0 = (tile / ntx) * kFT, ox0 = (tile % ntx) * kFT;
+        for (int q = threadIdx.x; q < G::IY * G::NCH; q += 256) {
+            const int iy = q / G::NCH, k = q - iy * G::NCH;
+            int gy = 2 * oy0 + iy;
+            while (gy >= R) gy -= R;
+            int col = 2 * ox0 + 4 * k;
+            while (col >= C) col -= C;
+            cp_async16(buf + iy * G::RP + 4 * k, in + (size_t)gy * C + col);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    int tile = blockIdx.x;
+    if (tile < nt) stage(tile, raw0);
+    float* cur = raw0;
+    float* nxt = raw1;
+    for (; tile < nt; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        if (next < nt) stage(next, nxt);
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+        // along x from the raw rows: column pair j + m of the tile is float2 (2(j + m), +1)
+        const float2* rows2 = reinterpret_cast<const float2*>(cur);
+        for (int t = threadIdx.x; t < G::IY * kFT; t += 256) {
+            const int iy = t >> 5, j = t & 31;
+            float lo = 0.f, hi = 0.f;
+#pragma unroll
+            for (int m = 0; m < L / 2; ++m) {
+                const float2 v = rows2[iy * (G::RP / 2) + j + m];
+                lo = fmaf(f.h[2 * m], v.x, lo);
+                lo = fmaf(f.h[2 * m + 1], v.y, lo);
+                hi = fmaf(f.g[2 * m], v.x, hi);
+                hi = fmaf(f.g[2 * m + 1], v.y, hi);
+            }
+            s_lo[iy][j] = lo;
+            s_hi[iy][j] = hi;
+        }
+        __syncthreads();
+        const int oy0 = (tile / ntx) * kFT, ox0 = (tile % ntx) * kFT;
+        for (int t = threadIdx.x; t < kFT * kFT; t += 256) {
+            const int i = t >> 5, j = t & 31;
+            const int oy = oy0 + i, ox = ox0 + j;
+            float ll = 0.f, lh = 0.f, hl = 0.f, hh = 0.f;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                const float lo = s_lo[2 * i + k][j], hi = s_hi[2 * i + k][j];
+                ll = fmaf(f.h[k], lo, ll);
+                hl = fmaf(f.g[k], lo, hl);
+                lh = fmaf(f.h[k], hi, lh);
+                hh = fmaf(f.g[k], hi, hh);
+            }
+            if (oy < R2 && ox < C2) {
+                const size_t o = (size_t)oy * C2 + ox;
+                outA[o] = ll;
+                d01[o] = lh;
+                d10[o] = hl;
+                d11[o] = hh;
+            }
+        }
+        // the next iteration writes s_lo / s_hi and stages into this iteration's buffer only
+        // after its wait and barrier
+        float* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int L>
 void dwt_fast_launch(const float* src, int R, int C, float* a, float* d01, float* d10, float* d11,
                      const FiltT<float>& f, cudaStream_t st) {
+    const int tiles = ((C / 2 + kFT - 1) / kFT) * ((R / 2 + kFT - 1) / kFT);
+    if ((C & 3) == 0 && C >= 8 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+        static unsigned long long attr = 0ull;
+        static int grid_per_sm = 0;
+        if (!done_on_device(&attr)) {
+            cudaFuncSetAttribute(dwt_level_pipe<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)PipeGeom<L>::smem);
+            int per = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, dwt_level_pipe<L>, 256, PipeGeom<L>::smem);
+            grid_per_sm = per > 0 ? per : 1;
+            mark_on_device(&attr);
+        }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int grid = std::max(1, std::min(tiles, std::max(sms, 1) * grid_per_sm));
+        dwt_level_pipe<L><<<grid, 256, PipeGeom<L>::smem, st>>>(src, R, C, a, d01, d10, d11, f);
+        return;
+    }
     dim3 grid((C / 2 + kFT - 1) / kFT, (R / 2 + kFT - 1) / kFT);
     dwt_level_fast<L><<<grid, 256, 0, st>>>(src, R, C, a, d01, d10, d11, f);
 }
