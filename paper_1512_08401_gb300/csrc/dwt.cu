@@ -411,6 +411,108 @@ __global__ void __launch_bounds__(256) dwt_level_pipe(const float* __restrict__ 
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Persistent, double-buffered form of idwt_level_fast for 16-byte aligned coefficient arrays
+// whose width is a multiple of 4. A tile needs coefficient columns cx0 - (L/2 - 1) ... cx0 + 31;
+// the staged segment starts HP >= L/2 - 1 columns before cx0 (HP a multiple of 4) so that
+// every 16-byte chunk is aligned, and wraps periodically in whole chunks.
+template <int L>
+struct IPipeGeom {
+    static constexpr int H2 = L / 2;
+    static constexpr int CY = kFT + H2 - 1;            // coefficient rows of a tile
+    static constexpr int CX = kFT + H2 - 1;            // coefficient columns used
+    static constexpr int HP = (H2 - 1 + 3) / 4 * 4;    // staged columns left of the tile
+    static constexpr int OFF = HP - (H2 - 1);          // first used column within a staged row
+    static constexpr int NCH = (HP + kFT) / 4;         // 16-byte chunks per staged row
+    static constexpr int RP = 4 * NCH;                 // row pitch (floats)
+    static constexpr int BUF = 4 * CY * RP;            // one buffer: four subbands
+    static constexpr size_t smem = sizeof(float) * (size_t)(2 * BUF + 2 * 2 * kFT * CX);
+};
+
+template <int L>
+__global__ void __launch_bounds__(256) idwt_level_pipe(const float* __restrict__ cA, const float* __restrict__ c01,
+                                                       const float* __restrict__ c10, const float* __restrict__ c11,
+                                                       int R2, int C2, float* __restrict__ out, FiltT<float> f) {
+    using G = IPipeGeom<L>;
+    constexpr int H2 = G::H2, CX = G::CX;
+    extern __shared__ __align__(16) float ipipe_smem[];
+    float* const buf0 = ipipe_smem;
+    float* const buf1 = buf0 + G::BUF;
+    float (*sLx)[CX] = reinterpret_cast<float (*)[CX]>(buf1 + G::BUF);
+    float (*sHx)[CX] = sLx + 2 * kFT;
+    const int ntx = (C2 + kFT - 1) / kFT, nty = (R2 + kFT - 1) / kFT, nt = ntx * nty;
+    // subband s of a buffer: rows of RP floats, s = 0..3 for cA, c01, c10, c11
+    auto stage = [&](int tile, float* buf) {
+        const int cy0 = (tile / ntx) * kFT, cx0 = (tile % ntx) * kFT;
+        for (int q = threadIdx.x; q < 4 * G::CY * G::NCH; q += 256) {
+            const int sb = q / (G::CY * G::NCH);
+            const int r = q - sb * (G::CY * G::NCH);
+            const int iy = r / G::NCH, k = r - iy * G::NCH;
+            int gy = cy0 - H2 + 1 + iy;
+            while (gy < 0) gy += R2;
+            while (gy >= R2) gy -= R2;
+            int col = cx0 - G::HP + 4 * k;
+            while (col < 0) col += C2;
+            while (col >= C2) col -= C2;
+            const float* src = sb == 0 ? cA : sb == 1 ? c01 : sb == 2 ? c10 : c11;
+            cp_async16(buf + (sb * G::CY + iy) * G::RP + 4 * k, src + (size_t)gy * C2 + col);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    const int R = 2 * R2, C = 2 * C2;
+    int tile = blockIdx.x;
+    if (tile < nt) stage(tile, buf0);
+    float* cur = buf0;
+    float* nxt = buf1;
+    for (; tile < nt; tile += gridDim.x) {
+        const int next = tile + gridDim.x;
+        if (next < nt) stage(next, nxt);
+        else asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+        const float* sLL = cur;
+        const float* sLH = cur + G::CY * G::RP;
+        const float* sHL = cur + 2 * G::CY * G::RP;
+        const float* sHH = cur + 3 * G::CY * G::RP;
+        // along y, as in idwt_level_fast
+        for (int t = threadIdx.x; t < kFT * CX; t += 256) {
+            const int i = t / CX, cx = t - i * CX;
+            float l0 = 0.f, l1 = 0.f, h0 = 0.f, h1 = 0.f;
+#pragma unroll
+            for (int m = 0; m < H2; ++m) {
+                const int o = (i - m + H2 - 1) * G::RP + cx + G::OFF;
+                const float ll = sLL[o], hl = sHL[o], lh = sLH[o], hh = sHH[o];
+                l0 = fmaf(f.h[2 * m], ll, fmaf(f.g[2 * m], hl, l0));
+                l1 = fmaf(f.h[2 * m + 1], ll, fmaf(f.g[2 * m + 1], hl, l1));
+                h0 = fmaf(f.h[2 * m], lh, fmaf(f.g[2 * m], hh, h0));
+                h1 = fmaf(f.h[2 * m + 1], lh, fmaf(f.g[2 * m + 1], hh, h1));
+            }
+            sLx[2 * i][cx] = l0;
+            sLx[2 * i + 1][cx] = l1;
+            sHx[2 * i][cx] = h0;
+            sHx[2 * i + 1][cx] = h1;
+        }
+        __syncthreads();
+        const int cy0 = (tile / ntx) * kFT, cx0 = (tile % ntx) * kFT;
+        for (int t = threadIdx.x; t < 2 * kFT * kFT; t += 256) {
+            const int yl = t >> 5, c = t & 31;
+            const int y = 2 * cy0 + yl, xc = cx0 + c;
+            float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+            for (int m = 0; m < H2; ++m) {
+                const float lx = sLx[yl][c - m + H2 - 1], hx = sHx[yl][c - m + H2 - 1];
+                o0 = fmaf(f.h[2 * m], lx, fmaf(f.g[2 * m], hx, o0));
+                o1 = fmaf(f.h[2 * m + 1], lx, fmaf(f.g[2 * m + 1], hx, o1));
+            }
+            if (y < R && xc < C2) *reinterpret_cast<float2*>(out + (size_t)y * C + 2 * xc) = make_float2(o0, o1);
+        }
+        // sLx / sHx are rewritten, and this buffer restaged, only after the next wait and barrier
+        float* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int L>
 void dwt_fast_launch(const float* src, int R, int C, float* a, float* d01, float* d10, float* d11,
                      const FiltT<float>& f, cudaStream_t st) {
@@ -440,6 +542,33 @@ void dwt_fast_launch(const float* src, int R, int C, float* a, float* d01, float
 template <int L>
 void idwt_fast_launch(const float* a, const float* d01, const float* d10, const float* d11, int R2, int C2,
                       float* out, const FiltT<float>& f, cudaStream_t st) {
+    // The persistent form wins while each CTA has a few tiles (4096^2 level 2: 2.2 per CTA,
+    // 16.3 against 17.1 us; the coarse levels) and loses with many (level 1: 9 per CTA, 52.9
+    // against 44.7 us): its three resident CTAs per SM keep fewer loads in flight than the
+    // one-tile CTAs of idwt_level_fast.
+    const auto aligned = [](const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    if ((C2 & 3) == 0 && aligned(a) && aligned(d01) && aligned(d10) && aligned(d11)) {
+        static unsigned long long attr = 0ull;
+        static int grid_per_sm = 0;
+        if (!done_on_device(&attr)) {
+            cudaFuncSetAttribute(idwt_level_pipe<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)IPipeGeom<L>::smem);
+            int per = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, idwt_level_pipe<L>, 256, IPipeGeom<L>::smem);
+            grid_per_sm = per > 0 ? per : 1;
+            mark_on_device(&attr);
+        }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int tiles = ((C2 + kFT - 1) / kFT) * ((R2 + kFT - 1) / kFT);
+        const int resident = std::max(sms, 1) * grid_per_sm;
+        if (tiles <= 3 * resident) {
+            const int grid = std::max(1, std::min(tiles, resident));
+            idwt_level_pipe<L><<<grid, 256, IPipeGeom<L>::smem, st>>>(a, d01, d10, d11, R2, C2, out, f);
+            return;
+        }
+    }
     dim3 grid((C2 + kFT - 1) / kFT, (R2 + kFT - 1) / kFT);
     idwt_level_fast<L><<<grid, 256, 0, st>>>(a, d01, d10, d11, R2, C2, out, f);
 }
