@@ -571,3 +571,21 @@ def test_theta_entry_equals_the_probe_construction():
         q = (int(rng.integers(sb.rows)), int(rng.integers(sb.cols)))
         ref = A[sa.offset + p[0] * sa.cols + p[1], sb.offset + q[0] * sb.cols + q[1]]
         assert abs(theta.theta_entry(psf, n, n, "db4", J, a, p, b, q) - ref) <= 1e-13
+
+
+@pytest.mark.parametrize("shape,wname,J", [((16, 16), "db2", 2), ((32, 32), "db4", 3)])
+def test_theta_of_the_autocorrelation_is_the_normal_operator(shape, wname, J):
+    """HᵀH is the periodic convolution with the PSF's autocorrelation, so Algorithm 2 run on
+    that PSF (unthresholded) must give ΘᵀΘ. Row and column taps of the probe construction
+    meet in the product, so a transposed block, a flipped probe or a wrong row/column rule
+    for coarser outputs breaks the identity. The PSF is a seeded random 5 x 5 array without
+    point symmetry, so the self-convolution h * h (a plausible slip for h~ * h) fails too."""
+    from scipy.signal import correlate2d
+    R, C = shape
+    psf = np.random.default_rng(8).random((5, 5))
+    psf /= psf.sum()
+    auto = correlate2d(psf, psf, mode="full")
+    th = theta.build_theta(psf, R, C, wname, J, K=10**12)
+    hess = theta.build_theta(auto, R, C, wname, J, K=10**12)
+    normal = (th.matT @ th.mat).toarray()
+    assert np.abs(hess.mat.toarray() - normal).max() <= 1e-13 * np.abs(normal).max()
