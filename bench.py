@@ -391,7 +391,8 @@ def run_ours(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD, "global_batch": d.world, "parallelism": "replicas",
                       "l2": "flushed between steps (256 MiB write)", "K_eff": th.info.K_eff,
-                      "n_taps": th.info.n_taps, "tau": pc["tau"], "L_hat": pc["L_hat"]},
+                      "n_taps": th.info.n_taps, "tau": pc["tau"], "L_hat": pc["L_hat"],
+                      "plans": plan_summary(th.info)},
            "iters_to_gap": it_theta, "fista_iters_per_s": it_theta / (ms_theta * 1e-3),
            "protocol": ("paper Sec. 5.4: N_it from an untimed run with the objective target E*(1 + 1e-4), then "
                         "N_it iterations timed as one CUDA-graph chunk (no checks), each path with its own E*"),
@@ -442,6 +443,13 @@ def run_ours(args):
     return 0
 
 
+def plan_summary(info):
+    """The FP32 tile plans the autotuner kept for Theta_K and Theta_K^T."""
+    return {"items": list(info.plan_items), "smem_bytes": list(info.plan_smem_bytes), "grid": list(info.plan_grid),
+            "groups": list(info.plan_groups), "super_subbands": list(info.plan_super_subbands),
+            "split_tiles": list(info.plan_split_tiles)}
+
+
 def large_study(wdb, torch, peak, peak_src):
     """4096 x 4096 (Gaussian sigma = 4 on 41 x 41, J = 6, K = 30 N, SPAI): per-launch time of
     the two FISTA kernels over 200 iterations, against the HBM roofline."""
@@ -466,7 +474,7 @@ def large_study(wdb, torch, peak, peak_src):
                          "frac": (b1 + b2) / ((r["ms_k1"] + r["ms_k2"]) * 1e-3) / 1e9 / peak,
                          "wall_ms_per_iter": it_ms},
            "peak": peak, "unit": "GB/s", "peak_source": peak_src, "K_eff": th.info.K_eff,
-           "n_taps": T, "build_ms": th.info.build_ms}
+           "n_taps": T, "build_ms": th.info.build_ms, "plans": plan_summary(th.info)}
     # both paths to a 1e-4 relative gap of their own optimum (paper protocol: N_it from an
     # untimed run with the objective target, then N_it iterations as one graph chunk)
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

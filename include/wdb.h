@@ -80,6 +80,8 @@ typedef struct {
     int plan_split_tiles[2];    /* tiles of those plans split over several CTAs */
     int plan_super_subbands[2]; /* subbands of those plans worked in 2 x 2 super tiles */
     int plan_groups[2];         /* groups of subbands worked together by those plans' items */
+    int plan_smem_bytes[2];     /* dynamic shared memory per CTA of those plans (two staging buffers) */
+    int plan_grid[2];           /* persistent CTAs those plans launch (SMs x resident CTAs per SM) */
 } wdb_theta_info;
 
 /* Parameters of one solve. Zero-initialise and set what you need. */

@@ -180,6 +180,8 @@ wdb_status wdb_theta_info_get(const wdb_theta* th, wdb_theta_info* info) {
         info->plan_split_tiles[op] = th->tplan[op][0].n_split;
         info->plan_super_subbands[op] = th->tplan[op][0].n_sup;
         info->plan_groups[op] = th->tplan[op][0].n_grp;
+        info->plan_smem_bytes[op] = th->tplan[op][0].smem_bytes;
+        info->plan_grid[op] = th->targs[op][0].grid;
     }
     return WDB_OK;
 }

@@ -41,7 +41,8 @@ class ThetaInfo(C.Structure):
                 ("K_eff", C.c_longlong), ("n_taps", C.c_longlong), ("n_candidates", C.c_longlong),
                 ("theta_max_abs", C.c_double), ("phase_table_len", C.c_int), ("build_ms", C.c_double),
                 ("plan_tuned", C.c_int), ("plan_items", C.c_int * 2), ("plan_split_tiles", C.c_int * 2),
-                ("plan_super_subbands", C.c_int * 2), ("plan_groups", C.c_int * 2)]
+                ("plan_super_subbands", C.c_int * 2), ("plan_groups", C.c_int * 2),
+                ("plan_smem_bytes", C.c_int * 2), ("plan_grid", C.c_int * 2)]
 
 
 class VThetaInfo(C.Structure):
