@@ -513,6 +513,73 @@ __global__ void __launch_bounds__(256) idwt_level_pipe(const float* __restrict__
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
+// One tile per CTA, staged like idwt_level_pipe (16-byte cp.async chunks from 4 or 8 columns
+// left of the tile) into a single buffer: for levels with many tiles, where more resident
+// CTAs (38 KB of shared memory for db4) hide the staging better than a persistent pipeline.
+template <int L>
+__global__ void __launch_bounds__(256) idwt_level_async(const float* __restrict__ cA, const float* __restrict__ c01,
+                                                        const float* __restrict__ c10, const float* __restrict__ c11,
+                                                        int R2, int C2, float* __restrict__ out, FiltT<float> f) {
+    using G = IPipeGeom<L>;
+    constexpr int H2 = G::H2, CX = G::CX;
+    extern __shared__ __align__(16) float iasync_smem[];
+    float* const buf = iasync_smem;
+    float (*sLx)[CX] = reinterpret_cast<float (*)[CX]>(buf + G::BUF);
+    float (*sHx)[CX] = sLx + 2 * kFT;
+    const int cy0 = blockIdx.y * kFT, cx0 = blockIdx.x * kFT;
+    for (int q = threadIdx.x; q < 4 * G::CY * G::NCH; q += 256) {
+        const int sb = q / (G::CY * G::NCH);
+        const int r = q - sb * (G::CY * G::NCH);
+        const int iy = r / G::NCH, k = r - iy * G::NCH;
+        int gy = cy0 - H2 + 1 + iy;
+        while (gy < 0) gy += R2;
+        while (gy >= R2) gy -= R2;
+        int col = cx0 - G::HP + 4 * k;
+        while (col < 0) col += C2;
+        while (col >= C2) col -= C2;
+        const float* src = sb == 0 ? cA : sb == 1 ? c01 : sb == 2 ? c10 : c11;
+        cp_async16(buf + (sb * G::CY + iy) * G::RP + 4 * k, src + (size_t)gy * C2 + col);
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
+    const float* sLL = buf;
+    const float* sLH = buf + G::CY * G::RP;
+    const float* sHL = buf + 2 * G::CY * G::RP;
+    const float* sHH = buf + 3 * G::CY * G::RP;
+    for (int t = threadIdx.x; t < kFT * CX; t += 256) {
+        const int i = t / CX, cx = t - i * CX;
+        float l0 = 0.f, l1 = 0.f, h0 = 0.f, h1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < H2; ++m) {
+            const int o = (i - m + H2 - 1) * G::RP + cx + G::OFF;
+            const float ll = sLL[o], hl = sHL[o], lh = sLH[o], hh = sHH[o];
+            l0 = fmaf(f.h[2 * m], ll, fmaf(f.g[2 * m], hl, l0));
+            l1 = fmaf(f.h[2 * m + 1], ll, fmaf(f.g[2 * m + 1], hl, l1));
+            h0 = fmaf(f.h[2 * m], lh, fmaf(f.g[2 * m], hh, h0));
+            h1 = fmaf(f.h[2 * m + 1], lh, fmaf(f.g[2 * m + 1], hh, h1));
+        }
+        sLx[2 * i][cx] = l0;
+        sLx[2 * i + 1][cx] = l1;
+        sHx[2 * i][cx] = h0;
+        sHx[2 * i + 1][cx] = h1;
+    }
+    __syncthreads();
+    const int R = 2 * R2, C = 2 * C2;
+    for (int t = threadIdx.x; t < 2 * kFT * kFT; t += 256) {
+        const int yl = t >> 5, c = t & 31;
+        const int y = 2 * cy0 + yl, xc = cx0 + c;
+        float o0 = 0.f, o1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < H2; ++m) {
+            const float lx = sLx[yl][c - m + H2 - 1], hx = sHx[yl][c - m + H2 - 1];
+            o0 = fmaf(f.h[2 * m], lx, fmaf(f.g[2 * m], hx, o0));
+            o1 = fmaf(f.h[2 * m + 1], lx, fmaf(f.g[2 * m + 1], hx, o1));
+        }
+        if (y < R && xc < C2) *reinterpret_cast<float2*>(out + (size_t)y * C + 2 * xc) = make_float2(o0, o1);
+    }
+}
+
 template <int L>
 void dwt_fast_launch(const float* src, int R, int C, float* a, float* d01, float* d10, float* d11,
                      const FiltT<float>& f, cudaStream_t st) {
@@ -568,6 +635,15 @@ void idwt_fast_launch(const float* a, const float* d01, const float* d10, const 
             idwt_level_pipe<L><<<grid, 256, IPipeGeom<L>::smem, st>>>(a, d01, d10, d11, R2, C2, out, f);
             return;
         }
+        constexpr size_t smem1 = sizeof(float) * (size_t)(IPipeGeom<L>::BUF + 2 * 2 * kFT * IPipeGeom<L>::CX);
+        static unsigned long long attr1 = 0ull;
+        if (!done_on_device(&attr1)) {
+            cudaFuncSetAttribute(idwt_level_async<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+            mark_on_device(&attr1);
+        }
+        dim3 grid1((C2 + kFT - 1) / kFT, (R2 + kFT - 1) / kFT);
+        idwt_level_async<L><<<grid1, 256, smem1, st>>>(a, d01, d10, d11, R2, C2, out, f);
+        return;
     }
     dim3 grid((C2 + kFT - 1) / kFT, (R2 + kFT - 1) / kFT);
     idwt_level_fast<L><<<grid, 256, 0, st>>>(a, d01, d10, d11, R2, C2, out, f);

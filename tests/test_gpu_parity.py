@@ -52,10 +52,11 @@ def rel_max(a, b):
 @pytest.mark.parametrize("n_rows,n_cols,J,wname", [(64, 64, 3, "db4"), (48, 80, 3, "db4"), (128, 128, 4, "db4"),
                                                     (16, 16, 4, "db4"), (32, 64, 5, "db4"), (256, 256, 6, "sym6"),
                                                     (64, 128, 4, "sym6"), (2048, 1024, 3, "db4"),
-                                                    (2048, 2048, 2, "sym6")])
+                                                    (2048, 2048, 2, "sym6"), (4096, 2048, 2, "db4")])
 def test_dwt_idwt_parity(wdb, n_rows, n_cols, J, wname):
-    # (the 2048-row cases have more level-1 tiles than the persistent transform kernel has
-    # CTAs, so its double-buffered tile loop runs several tiles per CTA)
+    # (the 2048-row cases have more level-1 tiles than the persistent transform kernels have
+    # CTAs, so their double-buffered tile loops run several tiles per CTA; at 4096 x 2048 the
+    # inverse level 1 has more than 3 tiles per resident CTA and runs one tile per CTA)
     rng = np.random.default_rng(11)
     u = rng.standard_normal((n_rows, n_cols))
     c = torch.zeros(n_rows * n_cols, device="cuda")
