@@ -103,6 +103,12 @@ typedef struct {
                                    (wdb_theta_kkt; the kkt_* and *64 fields of the result) */
     int ista;                   /* 1: drop the momentum step, y^(k+1) = x^(k) (ISTA, the baseline
                                    of the paper's Sec. 5.3 comparison); 0: Algorithm 3 */
+    int fused;                  /* 1: run each chunk of check_every iterations as one cooperative
+                                   launch of the resident CTAs (kernel 1 and kernel 2 of every
+                                   iteration separated by grid barriers); falls back to two
+                                   launches per iteration for plans with split tiles */
+    long long spin_limit;       /* fused loop: polls a grid barrier's wait makes before giving up
+                                   with WDB_ETIMEOUT (<= 0: 2^23, well over a second) */
 } wdb_solve_params;
 
 typedef struct {

@@ -81,6 +81,8 @@ struct SolveState {
     int hit_k;              // first k with primal <= target
     int ista;               // 1: no momentum step (y^(k+1) = x^(k)): ISTA
     double scratch[8];      // free slots for one-off reductions
+    unsigned int bar_count, bar_gen;   // grid barrier of the fused loop (arrivals, generation)
+    int timeout;            // 1: a bounded wait of the fused loop gave up
 };
 
 }  // namespace wdb

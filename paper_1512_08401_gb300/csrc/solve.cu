@@ -279,14 +279,24 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     E.d_state = th->d_state;
     E.h_state = th->h_state;
     const float* step = pc.d_step;
-    E.enqueue = [=](int iters) -> wdb_status {
-        for (int i = 0; i < iters; ++i) {
-            // each kernel after the first is a programmatic dependent of the one before it
-            WDB_TRY(tile_k1(F, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st, i > 0));
-            WDB_TRY(tile_k2(A, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st, true));
-        }
-        return WDB_OK;
-    };
+    const bool fused = p->fused != 0 && tile_fused_supported(F, A);
+    const long long spin = p->spin_limit;
+    if (fused) {
+        // one cooperative launch per chunk (no graph needed)
+        E.enqueue = [=](int iters) -> wdb_status {
+            return tile_fused(F, A, th->d_y, th->d_x0, th->d_r, th->d_xs, step, th->d_w, th->d_part, th->d_state, iters,
+                              spin, 2 * th->part_len, st);
+        };
+    } else {
+        E.enqueue = [=](int iters) -> wdb_status {
+            for (int i = 0; i < iters; ++i) {
+                // each kernel after the first is a programmatic dependent of the one before it
+                WDB_TRY(tile_k1(F, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st, i > 0));
+                WDB_TRY(tile_k2(A, th->d_r, th->d_y, th->d_xs, step, th->d_w, th->d_part, th->d_state, st, true));
+            }
+            return WDB_OK;
+        };
+    }
     E.enqueue_timed = [=](cudaEvent_t* ev) -> wdb_status {
         WDB_TRY(record_ev(ev[0], st));
         WDB_TRY(tile_k1(F, th->d_y, th->d_x0, th->d_r, th->d_part, th->d_state, st));
@@ -295,8 +305,13 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
         WDB_TRY(record_ev(ev[2], st));
         return WDB_OK;
     };
-    WDB_TRY(run_loop(E, m, !p->no_graph, p->time_kernels != 0, 2LL * m, st));
+    WDB_TRY(run_loop(E, m, !p->no_graph && !fused, p->time_kernels != 0, 2LL * m, st));
     SolveState hs = *th->h_state;
+    if (hs.timeout) {
+        // a pass that ran without its full grid left its work queue unreset
+        WDB_CK(cudaMemsetAsync(F.queue, 0, sizeof(TileQueue), st));
+        WDB_CK(cudaMemsetAsync(A.queue, 0, sizeof(TileQueue), st));
+    }
     double Eobj = 0.0;
     long long sup = 0;
     WDB_TRY(theta_objective_dev(th, th->d_xs, th->d_x0, th->d_w, st, &Eobj, &sup));
@@ -326,7 +341,10 @@ wdb_status theta_solve(wdb_theta* th, const float* in, bool is_image, float* x_o
     res->gap64 = kk.gap;
     res->rel_gap64 = kk.rel_gap;
     res->status = WDB_OK;
-    if (hs.nan_flag || !std::isfinite(Eobj)) res->status = set_error(WDB_ENAN, "NaN/Inf in the objective");
+    if (hs.timeout)
+        res->status = set_error(WDB_ETIMEOUT, "a grid barrier of the fused loop gave up after %lld polls",
+                                p->spin_limit > 0 ? p->spin_limit : (1LL << 23));
+    else if (hs.nan_flag || !std::isfinite(Eobj)) res->status = set_error(WDB_ENAN, "NaN/Inf in the objective");
     else if (hs.diverged)
         res->status = set_error(WDB_EDIVERGED, "objective %g at iteration %d, above 1e6 x its first value %g",
                                 hs.primal, hs.iters_done, hs.first_primal);

@@ -835,12 +835,21 @@ __device__ __forceinline__ void up_taps4(TapSrc<T> ts, int j0, int n, int G, int
     }
 }
 
+// A load of the operator's input vector in the global-gather paths: through the read-only
+// cache in kernels that run one pass (the input is not written during the launch), and
+// through L2 (COH) in the fused loop, where the other pass of the same launch writes it.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_in(const T* p) {
+    if constexpr (COH) return __ldcg(p);
+    else return __ldg(p);
+}
+
 // Accumulate the pairs of batch `bi` of tile `w` (staged in S) into acc.
 // (oy, ox): offset of the computed tile inside the staged one (a super tile's quarter; 0, 0
 // for ordinary tiles)
 // M: accumulator sets (1, or 4 for grouped items, whose pairs hold one tap list per member
 // output subband; the region and the per-thread set-up of a pair serve every member).
-template <typename T, int M>
+template <typename T, int M, bool COH = false>
 __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* __restrict__ in, const TileItem& w,
                                               const SubbandDev& so, int bi, const T* __restrict__ S,
                                               const PairSm* __restrict__ tab, const ThreadMap& tm, T (&acc)[M][4],
@@ -980,10 +989,10 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                             const int l = __ldg(tl + j);
                             const T v = __ldg(tv + j);
                             const T* __restrict__ q = bp + l;
-                            a0 = fma(v, __ldg(q), a0);
-                            a1 = fma(v, __ldg(q + bstep), a1);
-                            a2 = fma(v, __ldg(q + 2 * bstep), a2);
-                            a3 = fma(v, __ldg(q + 3 * bstep), a3);
+                            a0 = fma(v, ld_in<COH>(q), a0);
+                            a1 = fma(v, ld_in<COH>(q + bstep), a1);
+                            a2 = fma(v, ld_in<COH>(q + 2 * bstep), a2);
+                            a3 = fma(v, ld_in<COH>(q + 3 * bstep), a3);
                         }
                         acc[mk][0] += a0;
                         acc[mk][1] += a1;
@@ -1030,12 +1039,12 @@ __device__ __forceinline__ void compute_batch(const TilePlanDev& plan, const T* 
                             const int l2 = __ldg(tl + (j + 2 * G) * step), l3 = __ldg(tl + (j + 3 * G) * step);
                             const T v0 = __ldg(tv + j * step), v1 = __ldg(tv + (j + G) * step);
                             const T v2 = __ldg(tv + (j + 2 * G) * step), v3 = __ldg(tv + (j + 3 * G) * step);
-                            a = fma(v0, __ldg(bp + l0), a);
-                            a1 = fma(v1, __ldg(bp + l1), a1);
-                            a2 = fma(v2, __ldg(bp + l2), a2);
-                            a3 = fma(v3, __ldg(bp + l3), a3);
+                            a = fma(v0, ld_in<COH>(bp + l0), a);
+                            a1 = fma(v1, ld_in<COH>(bp + l1), a1);
+                            a2 = fma(v2, ld_in<COH>(bp + l2), a2);
+                            a3 = fma(v3, ld_in<COH>(bp + l3), a3);
                         }
-                        for (; j < ntap; j += G) a = fma(__ldg(tv + j * step), __ldg(bp + __ldg(tl + j * step)), a);
+                        for (; j < ntap; j += G) a = fma(__ldg(tv + j * step), ld_in<COH>(bp + __ldg(tl + j * step)), a);
                         a += (a1 + a2) + a3;
                     } else {
                         for (int j = g; j < ntap; j += G) {
@@ -1158,24 +1167,26 @@ __device__ __forceinline__ void epilogue(const TileItem& w, const SubbandDev& so
 // ---------------------------------------------------------------------------------------
 // Single problem: persistent CTAs, heaviest tiles first, (tile, batch) double buffering
 // ---------------------------------------------------------------------------------------
-// SPLIT: the plan has split tiles (a separate instance, so that plans without them run code
-// that carries none of the combining step)
-// SUP: the plan has super tiles (likewise a separate instance)
-// GRP: the plan has grouped items (the tile of up to four subbands per item; likewise)
-template <typename T, int EPI, bool SPLIT, bool SUP, bool GRP>
-__global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const T* __restrict__ in,
-                                                            T* __restrict__ out, EpiArgs ep) {
+// Shared memory of one pass, declared by the kernel that runs it (so that a kernel running
+// two passes holds one copy).
+template <typename T>
+struct PassSmem {
+    unsigned char* raw;                       // the two staging buffers (dynamic)
+    T* red_buf;                               // 4 x kTileThreads
+    PairSm (*tab_buf)[kMaxBatchPairs];        // [2][kMaxBatchPairs]
+    int* s_next;
+};
+
+// One application of a plan by the persistent CTAs of the launch: items from the queue,
+// (tile, batch) double buffering, the epilogue, and the grid-wide FP64 reduction whose last
+// CTA finishes the pass (COH: see ld_in).
+template <typename T, int EPI, bool SPLIT, bool SUP, bool GRP, bool COH>
+__device__ __forceinline__ void tile_pass(const TileArgs& A, const T* __restrict__ in, T* __restrict__ out,
+                                          const EpiArgs& ep, const PassSmem<T>& sm) {
     constexpr int M = GRP ? 4 : 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* const buf0 = reinterpret_cast<T*>(smem_raw);
+    T* const buf0 = reinterpret_cast<T*>(sm.raw);
     T* const buf1 = buf0 + A.plan.buf_elems;
-    __shared__ T red_buf[4 * kTileThreads];
-    // launched as a programmatic dependent of the previous FISTA kernel: nothing it wrote is
-    // read before that grid has completed (a no-op for ordinary launches)
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    if (EPI == kK1 || EPI == kK2) {
-        if (*(volatile int*)&ep.st->stop) return;
-    }
+    T* const red_buf = sm.red_buf;
     const TilePlanDev& plan = A.plan;
     const int t = threadIdx.x;
     Partials pt;
@@ -1185,7 +1196,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
         beta = ep.st->ista ? 0.f : (float)(k - 1) / (float)(k + 2);
     }
     // work items come from a queue, heaviest first
-    __shared__ int s_next;
+    int& s_next = *sm.s_next;
     if (t == 0) s_next = (int)atomicAdd(&A.queue->next, 1u);
     __syncthreads();
     int it = s_next;
@@ -1193,9 +1204,8 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
     int bi = w.batch_begin;
     T* S = buf0;
     T* Snext = buf1;
-    __shared__ PairSm tab_buf[2][kMaxBatchPairs];
-    PairSm* tab = tab_buf[0];
-    PairSm* tab_next = tab_buf[1];
+    PairSm* tab = sm.tab_buf[0];
+    PairSm* tab_next = sm.tab_buf[1];
     if (it < plan.n_items) stage_batch<T>(plan, in, w, bi, S, tab);
     cp_async_commit();
     T acc[M][4];
@@ -1228,7 +1238,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
             for (int q = 0; q < 4; ++q) {
                 const int oy = (q >> 1) << w.lgTS(), ox = (q & 1) << w.lgTS();
                 if (w.ty0 + oy >= so.rows || w.tx0 + ox >= so.cols) continue;
-                compute_batch<T, M>(plan, in, w, so, bi, S, tab, tm, acc, oy, ox);
+                compute_batch<T, M, COH>(plan, in, w, so, bi, S, tab, tm, acc, oy, ox);
                 TileItem wq = w;
                 wq.ty0 += oy;
                 wq.tx0 += ox;
@@ -1237,7 +1247,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
                 for (int e = 0; e < 4; ++e) acc[0][e] = 0;
             }
         } else {
-            compute_batch<T, M>(plan, in, w, so, bi, S, tab, tm, acc);
+            compute_batch<T, M, COH>(plan, in, w, so, bi, S, tab, tm, acc);
             if (bi + 1 == w.batch_end) {
                 if (!GRP) {
                     group_reduce<T>(tm, acc[0], red_buf);
@@ -1290,6 +1300,26 @@ __global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const
             }
         }
     }
+}
+
+// SPLIT: the plan has split tiles (a separate instance, so that plans without them run code
+// that carries none of the combining step)
+// SUP: the plan has super tiles (likewise a separate instance)
+// GRP: the plan has grouped items (the tile of up to four subbands per item; likewise)
+template <typename T, int EPI, bool SPLIT, bool SUP, bool GRP>
+__global__ void __launch_bounds__(kTileThreads, 3) tile_kernel(TileArgs A, const T* __restrict__ in,
+                                                            T* __restrict__ out, EpiArgs ep) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ T red_buf[4 * kTileThreads];
+    __shared__ PairSm tab_buf[2][kMaxBatchPairs];
+    __shared__ int s_next;
+    // launched as a programmatic dependent of the previous FISTA kernel: nothing it wrote is
+    // read before that grid has completed (a no-op for ordinary launches)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if (EPI == kK1 || EPI == kK2) {
+        if (*(volatile int*)&ep.st->stop) return;
+    }
+    tile_pass<T, EPI, SPLIT, SUP, GRP, false>(A, in, out, ep, PassSmem<T>{smem_raw, red_buf, tab_buf, &s_next});
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1492,7 +1522,119 @@ __global__ void __launch_bounds__(kTileThreads, GRP ? 2 : 3) tile_batch_kernel(B
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Fused FISTA loop: kernel 1 and kernel 2 of several iterations in one cooperative launch
+// ---------------------------------------------------------------------------------------
+// Grid-wide barrier between the passes (every CTA of a cooperative launch is resident). One
+// thread per CTA reads the generation, makes the CTA's writes visible and arrives; the last
+// arrival resets the count and advances the generation, the others poll it at most
+// spin_limit times. A poll that runs out records the timeout (and stops the solve); a poll
+// that sees another CTA's timeout returns false as well, so no CTA waits unboundedly. A CTA
+// released after others gave up may run one more pass alone and then leaves at the next
+// barrier; that pass's queue counters stay unreset, which the host resets after a timeout
+// (WDB_ETIMEOUT).
+__device__ __forceinline__ bool fused_barrier(SolveState* st, long long spin_limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned int* vgen = &st->bar_gen;
+        const unsigned int g = *vgen;
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&st->bar_gen, 1u);
+        } else {
+            long long n = 0;
+            while (*vgen == g) {
+                if (*(volatile int*)&st->timeout) {
+                    ok = 0;
+                    break;
+                }
+                if (++n > spin_limit) {
+                    atomicExch(&st->timeout, 1);
+                    atomicExch(&st->stop, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct FusedArgs {
+    TileArgs A1, A2;        // plans of Theta_K (kernel 1) and Theta_K^T (kernel 2)
+    const float* y;
+    float* r;
+    EpiArgs e1, e2;
+    int iters;
+    long long spin_limit;
+};
+
+// SUPn / GRPn: the pass of plan n has super tiles / grouped items (as in tile_kernel; plans
+// with split tiles run the two-launch loop instead)
+template <bool SUP1, bool GRP1, bool SUP2, bool GRP2>
+__global__ void __launch_bounds__(kTileThreads, 3) fista_fused_kernel(FusedArgs F) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ float red_buf[4 * kTileThreads];
+    __shared__ PairSm tab_buf[2][kMaxBatchPairs];
+    __shared__ int s_next;
+    const PassSmem<float> sm{smem_raw, red_buf, tab_buf, &s_next};
+    SolveState* const st = F.e1.st;
+    for (int i = 0; i < F.iters; ++i) {
+        // every CTA reads the flag after the same barrier, so all leave together
+        if (*(volatile int*)&st->stop || *(volatile int*)&st->timeout) break;
+        tile_pass<float, kK1, false, SUP1, GRP1, true>(F.A1, F.y, F.r, F.e1, sm);
+        if (!fused_barrier(st, F.spin_limit)) break;
+        tile_pass<float, kK2, false, SUP2, GRP2, true>(F.A2, F.r, nullptr, F.e2, sm);
+        if (!fused_barrier(st, F.spin_limit)) break;
+    }
+}
+
+template <bool SUP1, bool GRP1, bool SUP2, bool GRP2>
+wdb_status launch_fused_as(const FusedArgs& F, int smem, int max_ctas, cudaStream_t st) {
+    auto* kern = fista_fused_kernel<SUP1, GRP1, SUP2, GRP2>;
+    static unsigned long long attr = 0ull;
+    if (!done_on_device(&attr)) {
+        WDB_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        mark_on_device(&attr);
+    }
+    int dev = 0, sms = 0, per = 0;
+    WDB_CK(cudaGetDevice(&dev));
+    WDB_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    WDB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kTileThreads, smem));
+    if (per <= 0 || sms <= 0) return set_error(WDB_EINVAL, "fused loop: no resident CTA for %d bytes", smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)std::max(1, std::min(sms * per, max_ctas)));
+    cfg.blockDim = dim3(kTileThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    WDB_CK(cudaLaunchKernelEx(&cfg, kern, F));
+    count_launch();
+    WDB_CK(cudaGetLastError());
+    return WDB_OK;
+}
+
+template <bool SUP1, bool GRP1>
+wdb_status launch_fused_2(const FusedArgs& F, int mode2, int smem, int max_ctas, cudaStream_t st) {
+    if (mode2 == 1) return launch_fused_as<SUP1, GRP1, true, false>(F, smem, max_ctas, st);
+    if (mode2 == 2) return launch_fused_as<SUP1, GRP1, false, true>(F, smem, max_ctas, st);
+    return launch_fused_as<SUP1, GRP1, false, false>(F, smem, max_ctas, st);
+}
+
 // pdl: programmatic dependent launch, so that this grid's CTAs are scheduled while the
+// previous kernel of the stream drains// pdl: programmatic dependent launch, so that this grid's CTAs are scheduled while the
 // previous kernel of the stream drains (the kernel waits for that grid before its work)
 template <typename T, int EPI, bool SPLIT, bool SUP, bool GRP>
 wdb_status launch_tile_as(const TileArgs& A, const T* in, T* out, const EpiArgs& ep, cudaStream_t st, bool pdl) {
@@ -1612,6 +1754,36 @@ wdb_status tile_k2(const TileArgs& A, const float* r, float* y, float* x, const 
     ep.part = part;
     ep.st = s;
     return launch_tile<float, kK2>(A, r, nullptr, ep, st, pdl);
+}
+
+bool tile_fused_supported(const TileArgs& F, const TileArgs& A) { return !F.plan.split_ctr && !A.plan.split_ctr; }
+
+wdb_status tile_fused(const TileArgs& F, const TileArgs& A, float* y, const float* x0, float* r, float* x,
+                      const float* step_tab, const float* w_sb, double* part, SolveState* s, int iters,
+                      long long spin_limit, int max_ctas, cudaStream_t st) {
+    if (!tile_fused_supported(F, A)) return set_error(WDB_EINVAL, "fused loop: plans with split tiles");
+    FusedArgs fa{};
+    fa.A1 = F;
+    fa.A2 = A;
+    fa.y = y;
+    fa.r = r;
+    fa.e1.x0 = x0;
+    fa.e1.part = part;
+    fa.e1.st = s;
+    fa.e2.y = y;
+    fa.e2.x = x;
+    fa.e2.step_tab = step_tab;
+    fa.e2.w_sb = w_sb;
+    fa.e2.part = part;
+    fa.e2.st = s;
+    fa.iters = iters;
+    fa.spin_limit = spin_limit > 0 ? spin_limit : (1LL << 23);
+    const int smem = std::max(F.plan.smem_bytes, A.plan.smem_bytes);
+    const int mode1 = F.plan.n_sup > 0 ? 1 : F.plan.n_grp > 0 ? 2 : 0;
+    const int mode2 = A.plan.n_sup > 0 ? 1 : A.plan.n_grp > 0 ? 2 : 0;
+    if (mode1 == 1) return launch_fused_2<true, false>(fa, mode2, smem, max_ctas, st);
+    if (mode1 == 2) return launch_fused_2<false, true>(fa, mode2, smem, max_ctas, st);
+    return launch_fused_2<false, false>(fa, mode2, smem, max_ctas, st);
 }
 
 wdb_status tile_resnorm(const TileArgs& A, const float* x, const float* x0, float* r, double* out, double* part,

@@ -253,6 +253,15 @@ wdb_status tile_k2(const TileArgs& A, const float* r, float* y, float* x, const 
                    const float* w_sb, double* part, SolveState* s, cudaStream_t st, bool pdl = false);
 wdb_status tile_resnorm(const TileArgs& A, const float* x, const float* x0, float* r, double* out, double* part,
                         cudaStream_t st);
+// Fused FISTA loop: `iters` iterations of kernel 1 (plan F) and kernel 2 (plan A) in one
+// cooperative launch of the resident CTAs (at most max_ctas: `part` holds 2 doubles per CTA),
+// the passes separated by grid barriers whose waits poll at most spin_limit times (<= 0:
+// 2^23) before recording a timeout in the state. Stops early when the state says stop. Plans
+// with split tiles are not supported (WDB_EINVAL).
+bool tile_fused_supported(const TileArgs& F, const TileArgs& A);
+wdb_status tile_fused(const TileArgs& F, const TileArgs& A, float* y, const float* x0, float* r, float* x,
+                      const float* step_tab, const float* w_sb, double* part, SolveState* s, int iters,
+                      long long spin_limit, int max_ctas, cudaStream_t st);
 int tile_grid(int smem_bytes);
 
 }  // namespace wdb

@@ -58,7 +58,7 @@ class SolveParams(C.Structure):
                 ("tol", C.c_double), ("precond", C.c_int), ("jacobi_eps", C.c_double),
                 ("check_every", C.c_int), ("x_init_dev", C.c_void_p), ("no_graph", C.c_int),
                 ("target_objective", C.c_double), ("time_kernels", C.c_int), ("kkt_check", C.c_int),
-                ("ista", C.c_int)]
+                ("ista", C.c_int), ("fused", C.c_int), ("spin_limit", C.c_longlong)]
 
 
 class SolveResult(C.Structure):
@@ -210,7 +210,7 @@ def wavelet_filters(name: str = "db4"):
 
 def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0, check_every=10, x_init=None,
                 w_subband=None, no_graph=False, target_objective=0.0, time_kernels=False, kkt_check=False,
-                ista=False):
+                ista=False, fused=False, spin_limit=0):
     p = SolveParams()
     p.lam = float(lam)
     keep = None
@@ -228,6 +228,8 @@ def make_params(lam=1e-3, max_iters=200, tol=0.0, precond="spai", jacobi_eps=0.0
     p.time_kernels = 1 if time_kernels else 0
     p.kkt_check = 1 if kkt_check else 0
     p.ista = 1 if ista else 0
+    p.fused = 1 if fused else 0
+    p.spin_limit = int(spin_limit)
     return p, keep
 
 
