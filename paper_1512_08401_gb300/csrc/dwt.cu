@@ -185,6 +185,9 @@ __global__ void __launch_bounds__(256) dwt_level_fast(const float* __restrict__ 
                                                       float* __restrict__ outA, float* __restrict__ d01,
                                                       float* __restrict__ d10, float* __restrict__ d11,
                                                       FiltT<float> f) {
+    // a programmatic dependent of the previous level: nothing it wrote is read before that
+    // grid has completed (a no-op for ordinary launches)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     constexpr int IY = 2 * kFT + L - 2;       // input rows of the tile (with halo)
     constexpr int PX = kFT + L / 2 - 1;       // column pairs of the tile (with halo)
     __shared__ float s_ev[IY][PX + 1], s_od[IY][PX + 1];   // even / odd input columns
@@ -251,6 +254,9 @@ template <int L>
 __global__ void __launch_bounds__(256) idwt_level_fast(const float* __restrict__ cA, const float* __restrict__ c01,
                                                        const float* __restrict__ c10, const float* __restrict__ c11,
                                                        int R2, int C2, float* __restrict__ out, FiltT<float> f) {
+    // a programmatic dependent of the previous level: nothing it wrote is read before that
+    // grid has completed (a no-op for ordinary launches)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     constexpr int H2 = L / 2;
     constexpr int CY = kFT + H2 - 1, CX = kFT + H2 - 1;   // coefficient rows / cols with halo
     __shared__ float sLL[CY][CX], sLH[CY][CX], sHL[CY][CX], sHH[CY][CX];
@@ -324,6 +330,23 @@ struct PipeGeom {
     static constexpr size_t smem = sizeof(float) * (size_t)(2 * IY * RP + 2 * IY * kFT);
 };
 
+// Launch as a programmatic dependent of the previous kernel in the stream, so that the next
+// level's launch overlaps the tail of the previous one (the kernels wait for it first).
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);   // errors surface through cudaGetLastError
+}
+
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
@@ -334,6 +357,9 @@ __global__ void __launch_bounds__(256) dwt_level_pipe(const float* __restrict__ 
                                                       float* __restrict__ outA, float* __restrict__ d01,
                                                       float* __restrict__ d10, float* __restrict__ d11,
                                                       FiltT<float> f) {
+    // a programmatic dependent of the previous level: nothing it wrote is read before that
+    // grid has completed (a no-op for ordinary launches)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     using G = PipeGeom<L>;
     extern __shared__ __align__(16) float pipe_smem[];
     float* const raw0 = pipe_smem;
@@ -408,6 +434,7 @@ __global__ void __launch_bounds__(256) dwt_level_pipe(const float* __restrict__ 
         cur = nxt;
         nxt = tmp;
     }
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
@@ -432,6 +459,9 @@ template <int L>
 __global__ void __launch_bounds__(256) idwt_level_pipe(const float* __restrict__ cA, const float* __restrict__ c01,
                                                        const float* __restrict__ c10, const float* __restrict__ c11,
                                                        int R2, int C2, float* __restrict__ out, FiltT<float> f) {
+    // a programmatic dependent of the previous level: nothing it wrote is read before that
+    // grid has completed (a no-op for ordinary launches)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     using G = IPipeGeom<L>;
     constexpr int H2 = G::H2, CX = G::CX;
     extern __shared__ __align__(16) float ipipe_smem[];
@@ -510,6 +540,7 @@ __global__ void __launch_bounds__(256) idwt_level_pipe(const float* __restrict__
         cur = nxt;
         nxt = tmp;
     }
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
 
@@ -520,6 +551,9 @@ template <int L>
 __global__ void __launch_bounds__(256) idwt_level_async(const float* __restrict__ cA, const float* __restrict__ c01,
                                                         const float* __restrict__ c10, const float* __restrict__ c11,
                                                         int R2, int C2, float* __restrict__ out, FiltT<float> f) {
+    // a programmatic dependent of the previous level: nothing it wrote is read before that
+    // grid has completed (a no-op for ordinary launches)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     using G = IPipeGeom<L>;
     constexpr int H2 = G::H2, CX = G::CX;
     extern __shared__ __align__(16) float iasync_smem[];
@@ -599,11 +633,11 @@ void dwt_fast_launch(const float* src, int R, int C, float* a, float* d01, float
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int grid = std::max(1, std::min(tiles, std::max(sms, 1) * grid_per_sm));
-        dwt_level_pipe<L><<<grid, 256, PipeGeom<L>::smem, st>>>(src, R, C, a, d01, d10, d11, f);
+        launch_pdl(dwt_level_pipe<L>, dim3(grid), PipeGeom<L>::smem, st, src, R, C, a, d01, d10, d11, f);
         return;
     }
     dim3 grid((C / 2 + kFT - 1) / kFT, (R / 2 + kFT - 1) / kFT);
-    dwt_level_fast<L><<<grid, 256, 0, st>>>(src, R, C, a, d01, d10, d11, f);
+    launch_pdl(dwt_level_fast<L>, grid, 0, st, src, R, C, a, d01, d10, d11, f);
 }
 
 template <int L>
@@ -632,7 +666,7 @@ void idwt_fast_launch(const float* a, const float* d01, const float* d10, const 
         const int resident = std::max(sms, 1) * grid_per_sm;
         if (tiles <= 3 * resident) {
             const int grid = std::max(1, std::min(tiles, resident));
-            idwt_level_pipe<L><<<grid, 256, IPipeGeom<L>::smem, st>>>(a, d01, d10, d11, R2, C2, out, f);
+            launch_pdl(idwt_level_pipe<L>, dim3(grid), IPipeGeom<L>::smem, st, a, d01, d10, d11, R2, C2, out, f);
             return;
         }
         constexpr size_t smem1 = sizeof(float) * (size_t)(IPipeGeom<L>::BUF + 2 * 2 * kFT * IPipeGeom<L>::CX);
@@ -642,11 +676,11 @@ void idwt_fast_launch(const float* a, const float* d01, const float* d10, const 
             mark_on_device(&attr1);
         }
         dim3 grid1((C2 + kFT - 1) / kFT, (R2 + kFT - 1) / kFT);
-        idwt_level_async<L><<<grid1, 256, smem1, st>>>(a, d01, d10, d11, R2, C2, out, f);
+        launch_pdl(idwt_level_async<L>, grid1, smem1, st, a, d01, d10, d11, R2, C2, out, f);
         return;
     }
     dim3 grid((C2 + kFT - 1) / kFT, (R2 + kFT - 1) / kFT);
-    idwt_level_fast<L><<<grid, 256, 0, st>>>(a, d01, d10, d11, R2, C2, out, f);
+    launch_pdl(idwt_level_fast<L>, grid, 0, st, a, d01, d10, d11, R2, C2, out, f);
 }
 
 // FP32 level through the fast kernels (true) or not available for this filter length (false)
