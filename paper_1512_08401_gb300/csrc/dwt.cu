@@ -648,7 +648,7 @@ void idwt_fast_launch(const float* a, const float* d01, const float* d10, const 
     // against 44.7 us): its three resident CTAs per SM keep fewer loads in flight than the
     // one-tile CTAs of idwt_level_fast.
     const auto aligned = [](const float* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-    if ((C2 & 3) == 0 && aligned(a) && aligned(d01) && aligned(d10) && aligned(d11)) {
+    if ((C2 & 3) == 0 && aligned(a) && aligned(d01) && aligned(d10) && aligned(d11) && aligned(out)) {
         static unsigned long long attr = 0ull;
         static int grid_per_sm = 0;
         if (!done_on_device(&attr)) {
@@ -686,6 +686,9 @@ void idwt_fast_launch(const float* a, const float* d01, const float* d10, const 
 // FP32 level through the fast kernels (true) or not available for this filter length (false)
 bool dwt_level_f32(const float* src, int R, int C, float* a, float* d01, float* d10, float* d11,
                    const FiltT<float>& f, cudaStream_t st) {
+    // the fast kernels read the input in column pairs (8-byte loads); an input that is only
+    // 4-byte aligned (a caller's view at an odd offset) takes the generic kernel
+    if (reinterpret_cast<uintptr_t>(src) & 7) return false;
     switch (f.L) {
         case 2: dwt_fast_launch<2>(src, R, C, a, d01, d10, d11, f, st); return true;
         case 4: dwt_fast_launch<4>(src, R, C, a, d01, d10, d11, f, st); return true;
@@ -699,6 +702,9 @@ bool dwt_level_f32(const float* src, int R, int C, float* a, float* d01, float* 
 
 bool idwt_level_f32(const float* a, const float* d01, const float* d10, const float* d11, int R2, int C2,
                     float* out, const FiltT<float>& f, cudaStream_t st) {
+    // the fast kernels store pixel pairs (8 bytes); an output that is only 4-byte aligned
+    // takes the generic kernel
+    if (reinterpret_cast<uintptr_t>(out) & 7) return false;
     switch (f.L) {
         case 2: idwt_fast_launch<2>(a, d01, d10, d11, R2, C2, out, f, st); return true;
         case 4: idwt_fast_launch<4>(a, d01, d10, d11, R2, C2, out, f, st); return true;
