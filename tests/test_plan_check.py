@@ -97,3 +97,26 @@ def test_bad_arguments(wdb, case):
         wdb.tile_plan_check(nr, nc, J, bad, b, oy, ox, v)
     with pytest.raises(wdb.WdbError):
         wdb.tile_plan_check(nr + 1, nc, J, a, b, oy, ox, v)   # not divisible by 2^J
+
+
+@pytest.mark.parametrize("blur", ["gaussian", "motion"])
+@pytest.mark.parametrize("transpose", [False, True])
+def test_headline_operator_plans_keep_their_invariants(wdb, blur, transpose):
+    """The two 1024^2 operators the headline bench runs (J = 5, K = 30N; taps from the oracle's
+    records) under every planner configuration: the same invariants, and the same
+    multiply-adds per application whatever the plan."""
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    d = np.load(os.path.join(root, "oracle", "data", f"theta_1024_{blur}_k30.npz"))
+    n, J = int(d["n"]), int(d["levels"])
+    taps = (d["a"].astype(np.int32), d["b"].astype(np.int32), d["oy"].astype(np.int32), d["ox"].astype(np.int32),
+            d["v"].astype(np.float64))
+    macs = set()
+    for cfg in CONFIGS:
+        s = wdb.tile_plan_check(n, n, J, *taps, transpose=transpose, **cfg)
+        assert s["items"] > 0 and s["batches"] >= 1
+        if cfg.get("grouped"):
+            assert s["groups"] == J
+        macs.add(s["macs"])
+    assert len(macs) == 1
+    assert int(d["K_eff"]) <= macs.pop() <= 2 * int(d["K_eff"])
