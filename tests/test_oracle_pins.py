@@ -303,6 +303,27 @@ def test_selection_is_topK_of_dense_entries(rule):
         assert K - th.K_eff < n * n or th.K_eff == np.count_nonzero(np.abs(dense) > 1e-14 * np.abs(dense).max())
 
 
+def test_weighted_rule_restores_better_than_naive_at_equal_K():
+    """Sec. 5.1 (Fig. 5): at the same number of kept entries, the weighted rule (Eq.
+    cleverthreshold) restores better than the naive one (Eq. naivethresholding). Two blurs x
+    three seeded 64^2 problems, K = 5N, 300 iterations of Algorithm 3 with SPAI: the weighted
+    operator's pSNR is higher in every case (by 0.4-3.3 dB). Weights inverted to favour finer
+    inputs (sigma = 2^-level) lose in two of the six, so the direction of sigma is pinned."""
+    from oracle_cases import build_case, fista, precond_and_step
+    n, J = 64, 3
+    for psf in (synthetic.gaussian_psf(1.5, 9), synthetic.motion_line_psf(7, 0.9)):
+        for inst in range(3):
+            prob = synthetic.make_problem(n, psf, 1e-3, config_id=77, instance=inst)
+            snr = {}
+            for rule in ("weighted", "naive"):
+                case = build_case(psf, n, n, J, 5 * n * n, prob.u0, rule=rule)
+                _, P, tau, _ = precond_and_step(case, "spai")
+                x = fista(case, 1e-3, P, tau, 300).x
+                img = wavelet.idwt2(x, n, n, "db4", J).reshape(n, n)
+                snr[rule] = 10 * np.log10(1.0 / np.mean((img - prob.u_clean) ** 2))
+            assert snr["weighted"] > snr["naive"], (inst, snr)
+
+
 def test_selection_weighted_differs_from_naive():
     n, J = 32, 3
     psf = synthetic.gaussian_psf(1.5, 7)
